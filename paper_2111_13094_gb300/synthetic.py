@@ -1,0 +1,242 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+This module only draws data: it holds none of the fitting or query
+arithmetic and imports neither the CUDA library nor the oracle, so both can
+be fed the same arrays.  Random numbers that the method itself consumes
+(initialisation seeds, sampling uniforms) are generated here and passed in as
+inputs.
+
+Ground-truth mixtures follow the synthetic recipe of the workloads:
+  * K components, weights ~ Dirichlet(1);
+  * spatial means uniform in [0.1, 0.9]^3 of the region's cell, isotropic
+    spatial std U(0.05, 0.2) x cell size;
+  * directional means uniform on the sphere; tangent-plane lobes with per-axis
+    angular std U(0.05, 0.5) rad and a random in-plane rotation;
+  * optional "parallax": a random position/direction cross-covariance;
+  * sample weights log-normal(0, 1.5).
+Directions are drawn by walking a geodesic of length |nu| from the lobe
+centre along the tangent direction (nu_1 e1 + nu_2 e2)/|nu|, where (e1, e2)
+is a frame the generator picks by Gram-Schmidt; draws with |nu| >= pi are
+redrawn.  The frame is reported so that tests can express the ground truth
+without reference to any chart convention.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+FIELDS = ("px", "py", "pz", "ox", "oy", "oz", "w")
+
+
+@dataclass
+class GroundTruth:
+    """Frame-free description of R regions x K components (FP64)."""
+    pi: np.ndarray        # (R, K)
+    mu_x: np.ndarray      # (R, K, 3)
+    mu_w: np.ndarray      # (R, K, 3) unit
+    e1: np.ndarray        # (R, K, 3) tangent frame used for the lobe
+    e2: np.ndarray        # (R, K, 3)
+    cov: np.ndarray       # (R, K, 5, 5) joint covariance of (x, nu) in frame (e1, e2)
+
+    @property
+    def R(self):
+        return self.pi.shape[0]
+
+    @property
+    def K(self):
+        return self.pi.shape[1]
+
+
+def _unit(rng, n):
+    v = rng.normal(size=(n, 3))
+    return v / np.linalg.norm(v, axis=1, keepdims=True)
+
+
+def _frame(rng, mu):
+    """Gram-Schmidt tangent frame at each unit vector in mu (n, 3)."""
+    a = rng.normal(size=mu.shape)
+    e1 = a - np.sum(a * mu, axis=1, keepdims=True) * mu
+    e1 /= np.linalg.norm(e1, axis=1, keepdims=True)
+    e2 = np.cross(mu, e1)
+    return e1, e2
+
+
+def ground_truth(rng, R, K, cell_lo=None, cell_size=None, parallax=False) -> GroundTruth:
+    cell_lo = np.zeros((R, 3)) if cell_lo is None else np.asarray(cell_lo, float).reshape(R, 3)
+    h = np.ones(R) if cell_size is None else np.broadcast_to(np.asarray(cell_size, float), (R,))
+    pi = rng.dirichlet(np.ones(K), size=R)
+    mu_x = cell_lo[:, None, :] + h[:, None, None] * rng.uniform(0.1, 0.9, size=(R, K, 3))
+    sx = h[:, None] * rng.uniform(0.05, 0.2, size=(R, K))
+    mu_w = _unit(rng, R * K)
+    e1, e2 = _frame(rng, mu_w)
+    sig = rng.uniform(0.05, 0.5, size=(R * K, 2))
+    ang = rng.uniform(0.0, math.pi, size=R * K)
+    c, s = np.cos(ang), np.sin(ang)
+    rot = np.stack([np.stack([c, -s], -1), np.stack([s, c], -1)], -2)      # (RK, 2, 2)
+    cnu = rot @ (sig[:, :, None] ** 2 * np.eye(2)) @ np.swapaxes(rot, 1, 2)
+    cov = np.zeros((R * K, 5, 5))
+    cov[:, :3, :3] = (sx.reshape(-1) ** 2)[:, None, None] * np.eye(3)
+    cov[:, 3:, 3:] = cnu
+    if parallax:
+        # cross-covariance with correlation coefficients up to 0.6 in magnitude
+        rho = rng.uniform(-0.6, 0.6, size=(R * K, 3, 2)) / math.sqrt(3.0)
+        sdx = sx.reshape(-1)[:, None, None]
+        sdn = np.sqrt(np.diagonal(cnu, axis1=1, axis2=2))[:, None, :]
+        cov[:, :3, 3:] = rho * sdx * sdn
+        cov[:, 3:, :3] = np.swapaxes(cov[:, :3, 3:], 1, 2)
+    return GroundTruth(pi=pi, mu_x=mu_x, mu_w=mu_w.reshape(R, K, 3),
+                       e1=e1.reshape(R, K, 3), e2=e2.reshape(R, K, 3),
+                       cov=cov.reshape(R, K, 5, 5))
+
+
+def draw(rng, gt: GroundTruth, counts) -> np.ndarray:
+    """Samples of every region, concatenated region by region: (7, N) float32."""
+    counts = np.asarray(counts, dtype=np.int64)
+    R, K = gt.R, gt.K
+    N = int(counts.sum())
+    reg = np.repeat(np.arange(R), counts)
+    # component by inverse CDF on each region's weights
+    cum = np.cumsum(gt.pi, axis=1)
+    cum[:, -1] = 1.0
+    glob = (cum + np.arange(R)[:, None]).reshape(-1)
+    k = np.searchsorted(glob, reg + rng.random(N), side="right") - reg * K
+    k = np.minimum(k, K - 1)
+    rk = reg * K + k
+    chol = np.linalg.cholesky(gt.cov.reshape(R * K, 5, 5))
+    out = np.empty((7, N), dtype=np.float32)
+    x = np.empty((N, 3))
+    nu = np.empty((N, 2))
+    todo = np.arange(N)
+    while todo.size:
+        z = rng.normal(size=(todo.size, 5))
+        v = np.einsum("nij,nj->ni", chol[rk[todo]], z)
+        x[todo] = gt.mu_x.reshape(-1, 3)[rk[todo]] + v[:, :3]
+        nu[todo] = v[:, 3:]
+        todo = todo[np.linalg.norm(nu[todo], axis=1) >= math.pi]
+    r = np.linalg.norm(nu, axis=1)
+    safe = np.where(r > 0, r, 1.0)
+    e1 = gt.e1.reshape(-1, 3)[rk]
+    e2 = gt.e2.reshape(-1, 3)[rk]
+    t = (nu[:, :1] * e1 + nu[:, 1:] * e2) / safe[:, None]
+    mu = gt.mu_w.reshape(-1, 3)[rk]
+    d = np.cos(r)[:, None] * mu + np.sin(r)[:, None] * t
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    out[0:3] = x.T
+    out[3:6] = d.T
+    out[6] = rng.lognormal(0.0, 1.5, size=N)
+    return out
+
+
+def offsets_from_counts(counts) -> np.ndarray:
+    counts = np.asarray(counts, dtype=np.int64)
+    off = np.zeros(counts.size + 1, dtype=np.int64)
+    np.cumsum(counts, out=off[1:])
+    return off
+
+
+@dataclass
+class Batch:
+    samples: np.ndarray    # (7, N) float32: px, py, pz, ox, oy, oz, w
+    offsets: np.ndarray    # (R + 1,) int64
+    extent: np.ndarray     # (R,) longest side of each region's cell
+    truth: GroundTruth
+
+    @property
+    def R(self):
+        return self.offsets.size - 1
+
+    @property
+    def N(self):
+        return int(self.offsets[-1])
+
+
+def single_region(seed=0, N=65536, K=16, parallax=False) -> Batch:
+    """One region on the unit cube, N samples from a K-component truth."""
+    rng = np.random.default_rng([seed, 0])
+    gt = ground_truth(rng, 1, K, parallax=parallax)
+    s = draw(rng, gt, [N])
+    return Batch(s, offsets_from_counts([N]), np.ones(1), gt)
+
+
+def region_grid(R):
+    """Cells of a near-cubic grid of R regions over the unit cube."""
+    n = round(R ** (1.0 / 3.0))
+    dims = None
+    for a in range(max(1, n - 2), n + 3):
+        for b in range(a, n + 3):
+            if R % (a * b) == 0:
+                c = R // (a * b)
+                cand = sorted((a, b, c), reverse=True)
+                if dims is None or max(cand) - min(cand) < max(dims) - min(dims):
+                    dims = tuple(cand)
+    if dims is None:
+        dims = (R, 1, 1)
+    idx = np.arange(R)
+    ijk = np.stack([idx % dims[0], (idx // dims[0]) % dims[1], idx // (dims[0] * dims[1])], 1)
+    size = 1.0 / np.array(dims, float)
+    return ijk * size, np.broadcast_to(size.max(), (R,)).copy(), dims
+
+
+def region_counts(seed, R, m_lo=256, m_hi=65536):
+    """Per-region sample counts, log-uniform in [m_lo, m_hi]."""
+    rng = np.random.default_rng([seed, 1])
+    return np.floor(np.exp(rng.uniform(math.log(m_lo), math.log(m_hi), size=R))).astype(np.int64)
+
+
+def batched_truth(seed, R, K=16, parallax=False) -> GroundTruth:
+    rng = np.random.default_rng([seed, 2])
+    lo, h, _ = region_grid(R)
+    return ground_truth(rng, R, K, cell_lo=lo, cell_size=h, parallax=parallax)
+
+
+def batched_round(seed, R, counts, round_index, truth: GroundTruth) -> Batch:
+    """A fresh batch of every region's samples for one stepwise-EM round."""
+    rng = np.random.default_rng([seed, 3, round_index])
+    s = draw(rng, truth, counts)
+    _, h, _ = region_grid(R)
+    return Batch(s, offsets_from_counts(counts), h, truth)
+
+
+def init_uniforms(seed, R, per_region):
+    """Uniforms consumed by the k-means++ seeding of the initialisation."""
+    return np.random.default_rng([seed, 4]).random((R, per_region))
+
+
+def random_mixtures(seed, dims=(64, 32, 32), K=16):
+    """Per-cell K-component 5-D mixtures for the query workload.
+
+    Returns (pi, mu_x, mu_w, L) with L a random lower-triangular factor in the
+    (x, nu) order: position block with std U(0.05, 0.2) x cell size, direction
+    block with std U(0.05, 0.5) rad, and random cross terms.
+    """
+    rng = np.random.default_rng([seed, 5])
+    R = int(np.prod(dims))
+    idx = np.arange(R)
+    ijk = np.stack([idx % dims[0], (idx // dims[0]) % dims[1], idx // (dims[0] * dims[1])], 1)
+    h = 1.0 / np.array(dims, float)
+    lo = ijk * h
+    pi = rng.dirichlet(np.ones(K), size=R)
+    mu_x = lo[:, None, :] + h[None, None, :] * rng.uniform(0.1, 0.9, size=(R, K, 3))
+    mu_w = _unit(rng, R * K).reshape(R, K, 3)
+    L = np.zeros((R, K, 15))
+    sx = h.max() * rng.uniform(0.05, 0.2, size=(R, K, 3))
+    sd = rng.uniform(0.05, 0.5, size=(R, K, 2))
+    diag = np.concatenate([sx, sd], axis=2)
+    for i in range(5):
+        L[:, :, i * (i + 1) // 2 + i] = diag[:, :, i]
+        for j in range(i):
+            L[:, :, i * (i + 1) // 2 + j] = 0.3 * rng.normal(size=(R, K)) * diag[:, :, i]
+    return pi, mu_x, mu_w, L
+
+
+def query_points(seed, Q):
+    return np.random.default_rng([seed, 6]).random((Q, 3), dtype=np.float32)
+
+
+def grid_region(qx, dims):
+    """Cell index of each position on a uniform grid over the unit cube."""
+    d = np.asarray(dims)
+    ijk = np.clip(np.floor(np.asarray(qx, np.float64) * d).astype(np.int64), 0, d - 1)
+    return (ijk[:, 0] + d[0] * (ijk[:, 1] + d[1] * ijk[:, 2])).astype(np.int32)
