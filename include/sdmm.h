@@ -1,0 +1,351 @@
+/*
+ * sdmm.h -- C ABI of the GB300 (sm_103a) library for spatio-directional
+ * Gaussian mixtures, after Dodik, Papas, Oztireli, Mueller, "Path Guiding
+ * Using Spatio-Directional Mixture Models".
+ *
+ * The library fits, per spatial region, a K-component 5-D Gaussian mixture
+ * over position x (3-D, Euclidean) and direction w (unit 3-vector, mapped to
+ * the 2-D tangent plane at each component's mean by the azimuthal equidistant
+ * log map of Sec. 3.1), by weighted, Robbins-Monro averaged MAP-EM
+ * (Sec. 3.2, 3.4, 4.2, 4.3).  On the query side it conditions a region's
+ * mixture on a shading position, samples a direction and evaluates the
+ * solid-angle pdf (Sec. 3.1, 3.3).
+ *
+ * Conventions shared by every entry point
+ *  - Pointers are DEVICE memory allocated and owned by the caller, unless a
+ *    parameter says "host".  Configuration structs are host memory and are
+ *    read during the call only.  The library keeps no pointer after a call
+ *    returns, except inside an sdmm_fit_plan (which binds the workspace and
+ *    the state it was created with).
+ *  - Calls are asynchronous on `stream`.  Argument errors are detected on the
+ *    host before any launch and return SDMM_ERR_INVALID_ARG; nothing is
+ *    launched then.  Launch failures return SDMM_ERR_CUDA.  A call never
+ *    synchronises the stream, except sdmm_autotune and sdmm_fit_plan_timing.
+ *  - Inputs (const pointers) are never modified.  sdmm_state is in/out.
+ *  - The library allocates no device memory: all scratch is the caller's
+ *    workspace, whose size sdmm_*_workspace_size reports.
+ *  - Sample streams are structure-of-arrays FP32, sorted by region: region r
+ *    owns samples [offsets[r], offsets[r+1]) (offsets: int64, R+1 entries,
+ *    device).  Stream pointers need FP32 (4-byte) alignment.
+ *  - Mixture arrays are indexed by rk = r*K + k.  The 5-D tangent vector is
+ *    ordered (x0, x1, x2, nu0, nu1): position first.  Lower-triangular 5x5
+ *    matrices are packed row by row, entry (i, j <= i) at i*(i+1)/2 + j.
+ *  - The chart at a unit mean mu rotates mu to +z with R_mu whose rows are
+ *    (t, b, mu); (t, b) is the orthonormal basis of Duff et al. (JCGT 2017).
+ *    The paper leaves the azimuth of R_mu free; covariances are defined
+ *    relative to this choice.
+ *  - Errors: the return value; sdmm_last_error() gives a message for the
+ *    calling thread.  Per-region outcomes of a fit go to state.status.
+ */
+#ifndef SDMM_H
+#define SDMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t; NULL is the legacy default stream. */
+typedef struct CUstream_st *sdmm_stream;
+
+typedef enum {
+    SDMM_OK = 0,
+    SDMM_ERR_INVALID_ARG = 1,   /* bad size, pointer, alignment or config      */
+    SDMM_ERR_CUDA = 2,          /* a CUDA call failed (message in last_error)  */
+    SDMM_ERR_UNSUPPORTED = 4,   /* valid but not implemented (e.g. K > 32)     */
+    SDMM_ERR_WORKSPACE = 5      /* workspace smaller than reported size        */
+} sdmm_status;
+
+/* Per-region outcome of sdmm_fit_regions / sdmm_init_regions (state.status). */
+enum {
+    SDMM_REGION_OK = 0,
+    SDMM_REGION_SKIPPED = 1,     /* fewer than min_samples samples (Sec. 4.2)   */
+    SDMM_REGION_NUMERIC = 2,     /* a covariance was not positive definite; the
+                                    failing step left the region unchanged      */
+    SDMM_REGION_NONFINITE = 3,   /* non-finite weights or statistics            */
+    SDMM_REGION_ZERO_WEIGHT = 4, /* all sample weights are zero                 */
+    SDMM_REGION_BAD_OFFSETS = 5  /* offsets decrease or exceed N                */
+};
+
+enum { SDMM_ETA_ROBBINS_MONRO = 0, SDMM_ETA_ONE = 1 };
+enum { SDMM_DENSITY_TANGENT = 0, SDMM_DENSITY_SOLID_ANGLE = 1 };
+enum { SDMM_PRIOR_SCALE_SEEN = 0, SDMM_PRIOR_SCALE_ARRAY = 1 };
+enum { SDMM_PREC_FP32 = 0, SDMM_PREC_TC_3XBF16 = 1, SDMM_PREC_TC_TF32 = 2 };
+
+#define SDMM_MAX_K 32
+/* Floats per component in the derived FP32 tables (see sdmm_state). */
+#define SDMM_ETAB_FLOATS 36
+#define SDMM_QTAB_FLOATS 36
+
+typedef struct sdmm_config {
+    int32_t K;                 /* components per region, 1..32                */
+    int32_t min_samples;       /* smaller regions are skipped; paper: 16      */
+    int32_t eta_mode;          /* SDMM_ETA_*: Robbins-Monro step sizes
+                                  eta_j = (eta_beta j + 1)^-eta_alpha
+                                  (Sec. 4.3 Eq. robbins-monroe), or eta = 1
+                                  (plain EM on a fixed batch)                 */
+    int32_t estep_density;     /* SDMM_DENSITY_*: responsibilities from the
+                                  tangent density p^t (paper, Eq. em-ss-
+                                  computation) or the solid-angle density     */
+    int32_t prior_scale_mode;  /* SDMM_PRIOR_SCALE_*: beta = 1/n_seen, or the
+                                  caller's per-region array                   */
+    int32_t precision;         /* SDMM_PREC_*: E-step arithmetic              */
+    int32_t chunk;             /* samples per work unit of the fit kernels;
+                                  0 = library heuristic; else a multiple of
+                                  256 in [256, 65536]                        */
+    int32_t ctas_per_sm;       /* resident CTAs per SM of the persistent fit
+                                  kernels; 0 = library default, else 1..4     */
+    double eta_alpha;          /* 0.5 (Sec. 4.3)                              */
+    double eta_beta;           /* 0.1 (Sec. 4.3)                              */
+    double prior_q;            /* Dirichlet prior q = prior_q / K; paper 1    */
+    double prior_a;            /* Wishart prior a = prior_a / K; paper 5      */
+    double prior_B_pos;        /* B = a diag(pos, pos, pos, dir, dir);        */
+    double prior_B_dir;        /*   paper pos 1e-4, dir 1e-5 (Sec. 4.3)       */
+} sdmm_config;
+
+/*
+ * Mixture state of R regions x K components.  All device pointers, caller-
+ * owned, sized as noted (rk = r*K + k).
+ *   pi[RK]          weights                                   (FP64)
+ *   mu_x[RK*3]      spatial means                             (FP64)
+ *   mu_w[RK*3]      directional means, unit vectors           (FP64)
+ *   L[RK*15]        Cholesky factor of the 5-D covariance in the mu_w chart,
+ *                   packed lower, (x, nu) order               (FP64)
+ *   S0[RK], S2[RK*15]  averaged statistics (Sec. 4.3): weight and centred
+ *                   second moment in the current chart; the averaged first
+ *                   moment is zero by construction            (FP64)
+ *   Wbar[R]         averaged mean sample weight               (FP64)
+ *   n_seen[R]       samples absorbed so far (beta = 1/n_seen) (int64)
+ *   step_j[R]       Robbins-Monro step index                  (int32)
+ *   status[R]       SDMM_REGION_* of the last fit/init        (int32)
+ *   etab[RK*SDMM_ETAB_FLOATS], qtab[RK*SDMM_QTAB_FLOATS]
+ *                   derived FP32 records read by the E-step and the query
+ *                   kernels; written by every successful M-step and by
+ *                   sdmm_prepare.  Layout is private to the library; 16-byte
+ *                   aligned.
+ * The FP64 arrays are the checkpoint: saving them and calling sdmm_prepare
+ * after a reload restores the tables.
+ */
+typedef struct sdmm_state {
+    double *pi, *mu_x, *mu_w, *L;
+    double *S0, *S2, *Wbar;
+    int64_t *n_seen;
+    int32_t *step_j;
+    int32_t *status;
+    float *etab, *qtab;
+} sdmm_state;
+
+/* A batch of weighted samples (path vertices; Sec. 4.2): x = (px, py, pz),
+   w = (ox, oy, oz) unit, weight w >= 0 (incident-radiance estimate). */
+typedef struct sdmm_samples {
+    const float *px, *py, *pz, *ox, *oy, *oz, *w;  /* [N] each, device     */
+    const int64_t *offsets;                         /* [R+1], device       */
+    int64_t R;                                      /* regions             */
+    int64_t N;                                      /* offsets[R] <= N     */
+} sdmm_samples;
+
+/* Uniform grid of regions over an axis-aligned box: region of x is
+   ix + dims[0]*(iy + dims[1]*iz), i = clamp(floor((x - lo)*scale), 0, dims-1),
+   scale = dims / (hi - lo) evaluated in FP32. */
+typedef struct sdmm_grid {
+    float lo[3], hi[3];
+    int32_t dims[3];
+} sdmm_grid;
+
+/* Fills `cfg` with the paper's constants for K components (Sec. 4.2, 4.3). */
+void sdmm_config_default(sdmm_config *cfg, int32_t K);
+
+/* Thread-local message for the last error of this thread ("" if none). */
+const char *sdmm_last_error(void);
+
+/* Library version string. */
+const char *sdmm_version(void);
+
+/*
+ * Bytes of workspace that sdmm_fit_regions / sdmm_objective /
+ * sdmm_objective_backward / sdmm_fit_plan_create need for R regions and N
+ * samples with this configuration (chunk size included).  Host call.
+ */
+sdmm_status sdmm_fit_workspace_size(const sdmm_config *cfg, int64_t R,
+                                    int64_t N, size_t *bytes);
+
+/*
+ * Mixture initialisation (Sec. 4.3 "Initialization", App. B, App. C) for
+ * regions with at least min_samples samples: n_pos = K/8 spatial seeds (1 if
+ * 8 does not divide K) by weighted k-means++ on position with weights
+ * clamp(w, 0.1, 3) and Euclidean distance; n_dir = K/n_pos directions (cube
+ * corners when 8, else a Fibonacci spiral); Sigma^x = (2 d / n_pos)^2 I3 /
+ * chi2_3^{-1}(0.9), Sigma^nu = (2 pi / n_dir) I2, pi = 1/K, statistics reset.
+ * Surface normals are not available, so the spatial part is isotropic.
+ *   extent[R]     device FP64, longest side d of each region's cell
+ *   uniforms[R*n_pos]  device FP64 in [0, 1): the k-means++ draws
+ * Regions below min_samples get status SKIPPED and are otherwise untouched.
+ * The seed choice is computed in FP64 in sequential order.  Updates etab/qtab.
+ */
+sdmm_status sdmm_init_regions(const sdmm_config *cfg, const sdmm_samples *s,
+                              const double *extent, const double *uniforms,
+                              sdmm_state *st, sdmm_stream stream);
+
+/*
+ * `iters` EM steps of every region on this batch (Sec. 4.2 "Mini-batch EM
+ * fitting"; one launch of each fit kernel per step):
+ *   E-step  responsibilities from pi_k p_k(d_ki), d_ki = (x_i - mu_k^x,
+ *           log_{mu_k}(w_i)), per-sample log-sum-exp in FP32
+ *           (Sec. 3.2 Eq. em-ss-computation)
+ *   stats   weighted sums of [1, d, d d^T] per component, FP32 per work unit,
+ *           reduced in FP64 in a fixed order (deterministic)
+ *   average S^ = (1 - eta_j) S^ + eta_j S/W (Sec. 4.3 Eq. robbins-monroe),
+ *           eta_0 = 1
+ *   M-step  FP64: mean offset m = S^1/S^0, mu^x += m^x, mu_w = exp_{mu_w}(m^nu)
+ *           (Eq. tangent-space-mu-update); centred second moment moved to the
+ *           new chart by J = J_log(mu_new) J_exp_{mu_old}(m^nu) (Sec. 3.4,
+ *           App. A); MAP pi = (beta q + S^0)/(K beta q + sum S^0), Sigma =
+ *           (beta B + S^2)/(beta a + S^0) (Sec. 4.3); 5x5 Cholesky.
+ * beta = prior_scale[r] (device FP64 [R], prior_scale_mode ARRAY) or
+ * 1/n_seen with n_seen counting this batch once.  loglik_out (nullable,
+ * device FP32 [N]) receives the per-sample log-likelihood of the last E-step
+ * (entries of skipped regions are left untouched).  Regions whose status is
+ * not OK after the first step are not updated by later steps of the call.
+ * workspace: device, 256-byte aligned, >= sdmm_fit_workspace_size bytes.
+ */
+sdmm_status sdmm_fit_regions(const sdmm_config *cfg, const sdmm_samples *s,
+                             int32_t iters, const double *prior_scale,
+                             sdmm_state *st, float *loglik_out,
+                             void *workspace, size_t ws_bytes,
+                             sdmm_stream stream);
+
+/* Rebuild the FP32 tables etab/qtab of all R regions from the FP64
+   parameters (after the caller wrote or reloaded pi, mu_x, mu_w, L).
+   logits (nullable, device FP64 [RK]): first sets pi = softmax(logits) per
+   region.  delta (nullable, device FP64 [RK*5]): the E-step records then
+   evaluate each component at the mean offset delta inside its own chart,
+   density N(d - delta; 0, Sigma), as sdmm_objective does for its gradient
+   (the query records and the FP64 parameters are not offset).  A later
+   M-step rewrites the records without offset. */
+sdmm_status sdmm_prepare(const sdmm_config *cfg, int64_t R, sdmm_state *st,
+                         const double *logits, const double *delta,
+                         sdmm_stream stream);
+
+/*
+ * Conditioning on position (Sec. 3.2: closed-form Gaussian conditioning of
+ * the joint; Sec. 3.3: the K components of the query's region).  With
+ * L = [[A, 0], [C^T, D]] (position block A), per query i and component k:
+ *   cond_pi[i*K+k]      pi'_k ~ pi_k N_3(x; mu^x, A A^T), normalised
+ *   cond_m[(i*K+k)*2]   conditional mean of nu in the mu_k chart, C^T A^-1 (x - mu^x)
+ *   cond_L[(i*K+k)*3]   conditional Cholesky factor D = (d00, d10, d11)
+ * qx: device FP32 [Q*3]; region: device int32 [Q] or NULL, then `grid`
+ * (host) maps positions to regions.  Region ids must be < R; the tables of
+ * state `st` must be prepared for R regions.
+ */
+sdmm_status sdmm_condition(const sdmm_config *cfg, const sdmm_state *st,
+                           int64_t R, int64_t Q, const float *qx,
+                           const int32_t *region, const sdmm_grid *grid,
+                           float *cond_pi, float *cond_m, float *cond_L,
+                           sdmm_stream stream);
+
+/*
+ * One guided direction per query (Sec. 3.1 "Sampling"): condition, pick k by
+ * inverse CDF on u0, nu = m_k + D_k z with z from Box-Muller on (1 - u1, u2),
+ * discard when |nu| >= pi (valid = 0, pdf = 0), dir = exp_{mu_k}(nu), and
+ * the solid-angle pdf of the conditioned mixture at dir (Eq. solidangle-pdf,
+ * p^Omega = p^t / sinc|nu|).  Uniforms: `uniforms` (device FP32 [Q*3]) if
+ * not NULL, else Philox4x32-10 (Salmon et al., SC'11) with key = seed and
+ * counter = (i, 0, 0): u = (word >> 8) * 2^-24 for words 0..2.
+ * Outputs (device): dir_out FP32 [Q*3], pdf_out FP32 [Q], valid_out u8 [Q].
+ */
+sdmm_status sdmm_sample(const sdmm_config *cfg, const sdmm_state *st,
+                        int64_t R, int64_t Q, const float *qx,
+                        const int32_t *region, const sdmm_grid *grid,
+                        uint64_t seed, const float *uniforms, float *dir_out,
+                        float *pdf_out, uint8_t *valid_out,
+                        sdmm_stream stream);
+
+/* Solid-angle pdf of the conditioned mixture at given unit directions
+   dir (device FP32 [Q*3]) (Eq. solidangle-pdf); pdf_out device FP32 [Q]. */
+sdmm_status sdmm_pdf(const sdmm_config *cfg, const sdmm_state *st, int64_t R,
+                     int64_t Q, const float *qx, const int32_t *region,
+                     const sdmm_grid *grid, const float *dir, float *pdf_out,
+                     sdmm_stream stream);
+
+/*
+ * Weighted MAP objective per region (the function that the MAP-EM of
+ * Sec. 4.3 ascends; Dirichlet and inverse-Wishart priors after Gauvain-Lee):
+ *   F_r = (1/W) sum_i w_i l_i + sum_k [beta q log pi_k - (beta a/2) log|Sigma_k|
+ *         - (beta/2) tr(B Sigma_k^-1)],   l_i = log sum_k pi_k p_k(d_ki).
+ * F_out: device FP64 [R].  beta as in sdmm_fit_regions (1/n_seen without
+ * counting a new batch; 0 when n_seen = 0).  workspace as for the fit.
+ */
+sdmm_status sdmm_objective(const sdmm_config *cfg, const sdmm_samples *s,
+                           const double *prior_scale, const sdmm_state *st,
+                           double *F_out, void *workspace, size_t ws_bytes,
+                           sdmm_stream stream);
+
+/*
+ * Adjoint of sdmm_objective: given dF (device FP64 [R]), writes
+ * dF_r * dF_r/d(theta) for every component (device FP32):
+ *   g_delta[RK*5]  w.r.t. an offset delta of the mean inside the component's
+ *                  own chart (density N(d - delta; 0, Sigma)), at the offset
+ *                  the E-step records carry (0 unless set by sdmm_prepare)
+ *   g_L[RK*15]     w.r.t. the packed Cholesky factor L
+ *   g_logit[RK]    w.r.t. logits a with pi = softmax(a) per region
+ * The paper has no gradients; this is the derivative of the objective above.
+ */
+sdmm_status sdmm_objective_backward(const sdmm_config *cfg,
+                                    const sdmm_samples *s,
+                                    const double *prior_scale,
+                                    const sdmm_state *st, const double *dF,
+                                    float *g_delta, float *g_L,
+                                    float *g_logit, void *workspace,
+                                    size_t ws_bytes, sdmm_stream stream);
+
+/*
+ * Fit plan: the per-step launch sequence of sdmm_fit_regions for a fixed
+ * configuration, region count, maximum sample count, state and workspace,
+ * captured once into a CUDA graph and replayed per batch.  The batch (sample
+ * pointers, offsets, N) is passed per run and written to a device descriptor
+ * inside the workspace by a small kernel before the replay, so fresh batches
+ * need no re-capture.  Create captures on `stream` (which must not be
+ * capturing already).  Host handle; destroy frees only host-side objects.
+ */
+typedef struct sdmm_fit_plan sdmm_fit_plan;
+
+sdmm_status sdmm_fit_plan_create(const sdmm_config *cfg, int64_t R,
+                                 int64_t N_max, int32_t iters,
+                                 sdmm_state *st, void *workspace,
+                                 size_t ws_bytes, sdmm_stream stream,
+                                 sdmm_fit_plan **plan_out);
+/* Runs the plan on batch `s` (s->R must equal the plan's R, s->N <= N_max).
+   prior_scale and loglik_out as in sdmm_fit_regions; like the sample
+   pointers they may differ from run to run.  Runs on one plan must not
+   overlap on the GPU (they share the plan's workspace). */
+sdmm_status sdmm_fit_plan_run(sdmm_fit_plan *plan, const sdmm_samples *s,
+                              const double *prior_scale, float *loglik_out,
+                              sdmm_stream stream);
+/* Enable per-run event timing of the E-step kernel of each step inside the
+   graph, for up to `capacity` runs before sdmm_fit_plan_timing is read. */
+sdmm_status sdmm_fit_plan_enable_timing(sdmm_fit_plan *plan, int32_t capacity);
+/* Synchronises the plan's events and writes, host-side, the E-step kernel
+   durations (ms) of the runs since the last read: ms_out[*n_out]. */
+sdmm_status sdmm_fit_plan_timing(sdmm_fit_plan *plan, float *ms_out,
+                                 int32_t max, int32_t *n_out);
+sdmm_status sdmm_fit_plan_destroy(sdmm_fit_plan *plan);
+
+/*
+ * Autotuner: times the E-step kernel on this batch for candidate chunk sizes
+ * and CTAs per SM (without touching the state's parameters; the statistics
+ * go to the workspace) and returns the fastest pair.  Synchronises `stream`.
+ * The workspace must be sized for the largest candidate: use
+ * sdmm_fit_workspace_size with chunk = 256.
+ */
+sdmm_status sdmm_autotune(const sdmm_config *cfg, const sdmm_samples *s,
+                          const sdmm_state *st, void *workspace,
+                          size_t ws_bytes, sdmm_stream stream,
+                          int32_t *chunk_out, int32_t *ctas_per_sm_out,
+                          float *best_ms_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SDMM_H */

@@ -253,8 +253,10 @@ static int mstep_region(const or_config *cfg, int K, int64_t r, int64_t M,
         double hS1[5], hS2[15];
         for (int c = 0; c < 5; ++c) hS1[c] = eta * S1[c];
         for (int p = 0; p < 15; ++p) hS2[p] = (1.0 - eta) * st->S2[rk * 15 + p] + eta * S2[p];
-        if (!isfinite(hS0)) { bad = 3; break; }
-        for (int p = 0; p < 15; ++p) if (!isfinite(hS2[p])) bad = 3;
+        int nonfinite = !isfinite(hS0);
+        for (int p = 0; p < 15; ++p) if (!isfinite(hS2[p])) nonfinite = 1;
+        for (int c = 0; c < 5; ++c) if (!isfinite(hS1[c])) nonfinite = 1;
+        if (nonfinite) { bad = 3; break; }
         /* mean offset in the current chart and new mean, Eq. (tangent-space-mu-update) */
         double m[5];
         for (int c = 0; c < 5; ++c) m[c] = hS0 > 0.0 ? hS1[c] / hS0 : 0.0;

@@ -1,0 +1,590 @@
+// api.cu -- the C ABI of include/sdmm.h: argument checks, workspace layout,
+// kernel launch sequences, CUDA-graph fit plans and the autotuner.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.h"
+
+using namespace sdmm;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+sdmm_status fail(sdmm_status code, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+sdmm_status cuda_fail(cudaError_t e, const char* what) {
+    return fail(SDMM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define SDMM_CUDA(call, what)                          \
+    do {                                               \
+        cudaError_t e_ = (call);                       \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+int pow2_ceil(int K) {
+    int p = 1;
+    while (p < K) p <<= 1;
+    return p;
+}
+
+int sm_count() {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    return n;
+}
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+sdmm_status check_config(const sdmm_config* cfg) {
+    if (!cfg) return fail(SDMM_ERR_INVALID_ARG, "config is NULL");
+    if (cfg->K < 1) return fail(SDMM_ERR_INVALID_ARG, "K = %d must be >= 1", cfg->K);
+    if (cfg->K > SDMM_MAX_K) return fail(SDMM_ERR_UNSUPPORTED, "K = %d > %d", cfg->K, SDMM_MAX_K);
+    if (cfg->min_samples < 1) return fail(SDMM_ERR_INVALID_ARG, "min_samples must be >= 1");
+    if (cfg->eta_mode != SDMM_ETA_ROBBINS_MONRO && cfg->eta_mode != SDMM_ETA_ONE)
+        return fail(SDMM_ERR_INVALID_ARG, "eta_mode %d", cfg->eta_mode);
+    if (cfg->estep_density != SDMM_DENSITY_TANGENT && cfg->estep_density != SDMM_DENSITY_SOLID_ANGLE)
+        return fail(SDMM_ERR_INVALID_ARG, "estep_density %d", cfg->estep_density);
+    if (cfg->prior_scale_mode != SDMM_PRIOR_SCALE_SEEN && cfg->prior_scale_mode != SDMM_PRIOR_SCALE_ARRAY)
+        return fail(SDMM_ERR_INVALID_ARG, "prior_scale_mode %d", cfg->prior_scale_mode);
+    if (cfg->precision != SDMM_PREC_FP32 && cfg->precision != SDMM_PREC_TC_3XBF16 &&
+        cfg->precision != SDMM_PREC_TC_TF32)
+        return fail(SDMM_ERR_INVALID_ARG, "precision %d", cfg->precision);
+    if (cfg->chunk != 0 && (cfg->chunk < 256 || cfg->chunk > 65536 || cfg->chunk % 256 != 0))
+        return fail(SDMM_ERR_INVALID_ARG, "chunk %d: 0 or a multiple of 256 in [256, 65536]", cfg->chunk);
+    if (cfg->ctas_per_sm < 0 || cfg->ctas_per_sm > 4)
+        return fail(SDMM_ERR_INVALID_ARG, "ctas_per_sm %d: 0..4", cfg->ctas_per_sm);
+    const double v[6] = {cfg->eta_alpha, cfg->eta_beta, cfg->prior_q, cfg->prior_a,
+                         cfg->prior_B_pos, cfg->prior_B_dir};
+    for (double x : v)
+        if (!std::isfinite(x) || x < 0.0) return fail(SDMM_ERR_INVALID_ARG, "prior/eta constants must be finite and >= 0");
+    return SDMM_OK;
+}
+
+sdmm_status check_state(const sdmm_state* st, bool fit) {
+    if (!st) return fail(SDMM_ERR_INVALID_ARG, "state is NULL");
+    if (!st->pi || !st->mu_x || !st->mu_w || !st->L || !st->etab || !st->qtab)
+        return fail(SDMM_ERR_INVALID_ARG, "state parameter/table pointers must be non-NULL");
+    if (fit && (!st->S0 || !st->S2 || !st->Wbar || !st->n_seen || !st->step_j || !st->status))
+        return fail(SDMM_ERR_INVALID_ARG, "state statistics pointers must be non-NULL");
+    if ((reinterpret_cast<uintptr_t>(st->etab) | reinterpret_cast<uintptr_t>(st->qtab)) & 15u)
+        return fail(SDMM_ERR_INVALID_ARG, "etab/qtab must be 16-byte aligned");
+    return SDMM_OK;
+}
+
+sdmm_status check_samples(const sdmm_samples* s) {
+    if (!s) return fail(SDMM_ERR_INVALID_ARG, "samples is NULL");
+    if (s->R < 1 || s->R > (int64_t)INT32_MAX / 2) return fail(SDMM_ERR_INVALID_ARG, "R = %lld", (long long)s->R);
+    if (s->N < 0) return fail(SDMM_ERR_INVALID_ARG, "N = %lld", (long long)s->N);
+    if (!s->offsets) return fail(SDMM_ERR_INVALID_ARG, "offsets is NULL");
+    const float* p[7] = {s->px, s->py, s->pz, s->ox, s->oy, s->oz, s->w};
+    for (int i = 0; i < 7; ++i) {
+        if (s->N > 0 && !p[i]) return fail(SDMM_ERR_INVALID_ARG, "sample stream %d is NULL", i);
+        if (reinterpret_cast<uintptr_t>(p[i]) & 3u) return fail(SDMM_ERR_INVALID_ARG, "sample stream %d misaligned", i);
+    }
+    return SDMM_OK;
+}
+
+int default_ctas(const sdmm_config* cfg) { return cfg->ctas_per_sm > 0 ? cfg->ctas_per_sm : 2; }
+
+int choose_chunk(const sdmm_config* cfg, int64_t N) {
+    if (cfg->chunk > 0) return cfg->chunk;
+    const int64_t G = (int64_t)std::max(1, sm_count()) * default_ctas(cfg);
+    int64_t c = 256;
+    while (c < 4096 && c * G * 16 < N) c <<= 1;
+    return (int)c;
+}
+
+struct Layout {
+    size_t header, chunk_base, chunk_region, partial, total;
+    int chunk, ps;
+    int64_t max_chunks;
+};
+
+Layout layout(const sdmm_config* cfg, int64_t R, int64_t N, int chunk) {
+    Layout L{};
+    L.chunk = chunk;
+    L.ps = partial_stride(cfg->K);
+    L.max_chunks = (N + chunk - 1) / chunk + R;
+    size_t o = 0;
+    L.header = o;
+    o = align_up(o + sizeof(WsHeader));
+    L.chunk_base = o;
+    o = align_up(o + sizeof(int64_t) * (size_t)(R + 1));
+    L.chunk_region = o;
+    o = align_up(o + sizeof(int32_t) * (size_t)L.max_chunks);
+    L.partial = o;
+    o = align_up(o + sizeof(float) * (size_t)L.max_chunks * L.ps);
+    L.total = o;
+    return L;
+}
+
+struct WsPtrs {
+    WsHeader* hdr;
+    int64_t* cb;
+    int32_t* cr;
+    float* partial;
+};
+
+WsPtrs ws_ptrs(void* ws, const Layout& L) {
+    char* b = static_cast<char*>(ws);
+    return WsPtrs{reinterpret_cast<WsHeader*>(b + L.header), reinterpret_cast<int64_t*>(b + L.chunk_base),
+                  reinterpret_cast<int32_t*>(b + L.chunk_region), reinterpret_cast<float*>(b + L.partial)};
+}
+
+sdmm_status check_ws(void* ws, size_t bytes, const Layout& L) {
+    if (!ws) return fail(SDMM_ERR_INVALID_ARG, "workspace is NULL");
+    if (reinterpret_cast<uintptr_t>(ws) % kAlign) return fail(SDMM_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    if (bytes < L.total)
+        return fail(SDMM_ERR_WORKSPACE, "workspace %zu bytes < required %zu", bytes, L.total);
+    return SDMM_OK;
+}
+
+BatchDesc make_desc(const sdmm_samples* s, const double* prior, float* loglik) {
+    BatchDesc d{};
+    d.p[0] = s->px; d.p[1] = s->py; d.p[2] = s->pz;
+    d.p[3] = s->ox; d.p[4] = s->oy; d.p[5] = s->oz; d.p[6] = s->w;
+    d.offsets = s->offsets;
+    d.R = s->R;
+    d.N = s->N;
+    d.prior_scale = prior;
+    d.loglik = loglik;
+    return d;
+}
+
+// The per-step launch sequence of a fit (shared by direct calls and plans).
+struct FitLaunch {
+    sdmm_config cfg;
+    sdmm_state st;
+    Layout L;
+    WsPtrs w;
+    int64_t R;
+    int iters;
+    int grid;
+    int want_ll;
+};
+
+sdmm_status enqueue_fit(const FitLaunch& f, cudaStream_t s, std::vector<cudaEvent_t>* evs) {
+    const int KP = pow2_ceil(f.cfg.K);
+    SDMM_CUDA(launch_build_chunks(s, f.w.hdr, f.w.cb, f.w.cr, f.L.chunk, f.cfg.min_samples, f.L.max_chunks),
+              "build_chunks");
+    for (int it = 0; it < f.iters; ++it) {
+        if (evs) SDMM_CUDA(cudaEventRecordWithFlags((*evs)[2 * it], s, cudaEventRecordExternal), "event");
+        SDMM_CUDA(launch_accumulate(s, MODE_FIT, KP, f.grid, f.w.hdr, f.w.cb, f.w.cr, f.st.etab, f.cfg.K,
+                                    f.L.chunk, f.cfg.estep_density, f.w.partial, f.L.ps,
+                                    f.want_ll && it == f.iters - 1),
+                  "accumulate");
+        if (evs) SDMM_CUDA(cudaEventRecordWithFlags((*evs)[2 * it + 1], s, cudaEventRecordExternal), "event");
+        SDMM_CUDA(launch_reduce_mstep(s, f.R, f.w.hdr, f.w.cb, f.w.partial, f.L.ps, f.cfg, f.st, it),
+                  "reduce_mstep");
+    }
+    return SDMM_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+extern "C" {
+
+void sdmm_config_default(sdmm_config* cfg, int32_t K) {
+    if (!cfg) return;
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->K = K;
+    cfg->min_samples = 16;                 // Sec. 4.2
+    cfg->eta_mode = SDMM_ETA_ROBBINS_MONRO;
+    cfg->estep_density = SDMM_DENSITY_TANGENT;
+    cfg->prior_scale_mode = SDMM_PRIOR_SCALE_SEEN;
+    cfg->precision = SDMM_PREC_FP32;
+    cfg->chunk = 0;
+    cfg->ctas_per_sm = 0;
+    cfg->eta_alpha = 0.5;                  // Sec. 4.3
+    cfg->eta_beta = 0.1;
+    cfg->prior_q = 1.0;                    // q = 1/K
+    cfg->prior_a = 5.0;                    // a = 5/K
+    cfg->prior_B_pos = 1e-4;               // B = a diag(0.1, 0.1, 1, 1, 1) 1e-4
+    cfg->prior_B_dir = 1e-5;
+}
+
+const char* sdmm_last_error(void) { return g_err; }
+
+const char* sdmm_version(void) { return "sdmm-gb300 0.1 (sm_103a)"; }
+
+sdmm_status sdmm_fit_workspace_size(const sdmm_config* cfg, int64_t R, int64_t N, size_t* bytes) {
+    sdmm_status e = check_config(cfg);
+    if (e) return e;
+    if (!bytes) return fail(SDMM_ERR_INVALID_ARG, "bytes is NULL");
+    if (R < 1 || N < 0) return fail(SDMM_ERR_INVALID_ARG, "R = %lld, N = %lld", (long long)R, (long long)N);
+    *bytes = layout(cfg, R, N, choose_chunk(cfg, N)).total;
+    return SDMM_OK;
+}
+
+sdmm_status sdmm_init_regions(const sdmm_config* cfg, const sdmm_samples* s, const double* extent,
+                              const double* uniforms, sdmm_state* st, sdmm_stream stream) {
+    sdmm_status e;
+    if ((e = check_config(cfg)) || (e = check_samples(s)) || (e = check_state(st, true))) return e;
+    if (!extent || !uniforms) return fail(SDMM_ERR_INVALID_ARG, "extent/uniforms are NULL");
+    SDMM_CUDA(launch_init(stream, s->R, *cfg, make_desc(s, nullptr, nullptr), extent, uniforms, *st),
+              "init_regions");
+    return SDMM_OK;
+}
+
+sdmm_status sdmm_fit_regions(const sdmm_config* cfg, const sdmm_samples* s, int32_t iters,
+                             const double* prior_scale, sdmm_state* st, float* loglik_out,
+                             void* workspace, size_t ws_bytes, sdmm_stream stream) {
+    sdmm_status e;
+    if ((e = check_config(cfg)) || (e = check_samples(s)) || (e = check_state(st, true))) return e;
+    if (iters < 1) return fail(SDMM_ERR_INVALID_ARG, "iters = %d must be >= 1", iters);
+    if (cfg->prior_scale_mode == SDMM_PRIOR_SCALE_ARRAY && !prior_scale)
+        return fail(SDMM_ERR_INVALID_ARG, "prior_scale_mode ARRAY needs prior_scale");
+    if (cfg->precision != SDMM_PREC_FP32)
+        return fail(SDMM_ERR_UNSUPPORTED, "precision %d is not available in sdmm_fit_regions", cfg->precision);
+    const Layout L = layout(cfg, s->R, s->N, choose_chunk(cfg, s->N));
+    if ((e = check_ws(workspace, ws_bytes, L))) return e;
+    const int nsm = sm_count();
+    if (nsm <= 0) return fail(SDMM_ERR_CUDA, "no CUDA device");
+    FitLaunch f{*cfg, *st, L, ws_ptrs(workspace, L), s->R, iters, nsm * default_ctas(cfg),
+                loglik_out != nullptr};
+    SDMM_CUDA(launch_set_desc(stream, f.w.hdr, make_desc(s, prior_scale, loglik_out)), "set_desc");
+    return enqueue_fit(f, stream, nullptr);
+}
+
+sdmm_status sdmm_prepare(const sdmm_config* cfg, int64_t R, sdmm_state* st, const double* logits,
+                         const double* delta, sdmm_stream stream) {
+    sdmm_status e;
+    if ((e = check_config(cfg)) || (e = check_state(st, false))) return e;
+    if (R < 1) return fail(SDMM_ERR_INVALID_ARG, "R = %lld", (long long)R);
+    SDMM_CUDA(launch_prepare(stream, cfg->K, R, *st, logits, delta), "prepare");
+    return SDMM_OK;
+}
+
+// ---------------------------------------------------------------- queries
+static sdmm_status query_common(const sdmm_config* cfg, const sdmm_state* st, int64_t R, int64_t Q,
+                                const float* qx, const int32_t* region, const sdmm_grid* grid,
+                                GridF* g) {
+    sdmm_status e;
+    if ((e = check_config(cfg)) || (e = check_state(st, false))) return e;
+    if (R < 1 || Q < 0) return fail(SDMM_ERR_INVALID_ARG, "R = %lld, Q = %lld", (long long)R, (long long)Q);
+    if (Q > 0 && !qx) return fail(SDMM_ERR_INVALID_ARG, "qx is NULL");
+    std::memset(g, 0, sizeof(*g));
+    if (!region) {
+        if (!grid) return fail(SDMM_ERR_INVALID_ARG, "need region ids or a grid");
+        int64_t cells = 1;
+        for (int c = 0; c < 3; ++c) {
+            if (grid->dims[c] < 1) return fail(SDMM_ERR_INVALID_ARG, "grid dims must be >= 1");
+            if (!(grid->hi[c] > grid->lo[c])) return fail(SDMM_ERR_INVALID_ARG, "grid hi must exceed lo");
+            g->lo[c] = grid->lo[c];
+            g->scale[c] = (float)grid->dims[c] / (grid->hi[c] - grid->lo[c]);
+            g->dims[c] = grid->dims[c];
+            cells *= grid->dims[c];
+        }
+        if (cells > R) return fail(SDMM_ERR_INVALID_ARG, "grid has %lld cells > R", (long long)cells);
+        g->on = 1;
+    }
+    return SDMM_OK;
+}
+
+static int query_grid(int64_t Q) {
+    const int nsm = std::max(1, sm_count());
+    const int64_t groups = (Q + 31) / 32;             // one warp per 32 queries at a time
+    const int64_t ctas = (groups + 7) / 8;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(ctas, (int64_t)nsm * 8));
+}
+
+sdmm_status sdmm_condition(const sdmm_config* cfg, const sdmm_state* st, int64_t R, int64_t Q,
+                           const float* qx, const int32_t* region, const sdmm_grid* grid,
+                           float* cond_pi, float* cond_m, float* cond_L, sdmm_stream stream) {
+    GridF g;
+    sdmm_status e = query_common(cfg, st, R, Q, qx, region, grid, &g);
+    if (e) return e;
+    if (Q > 0 && (!cond_pi || !cond_m || !cond_L)) return fail(SDMM_ERR_INVALID_ARG, "outputs are NULL");
+    if (Q == 0) return SDMM_OK;
+    SDMM_CUDA(launch_query(stream, OP_CONDITION, pow2_ceil(cfg->K), query_grid(Q), st->qtab, cfg->K, R, Q,
+                           qx, region, g, 0, nullptr, nullptr, cond_pi, cond_m, cond_L, nullptr,
+                           nullptr, nullptr),
+              "condition");
+    return SDMM_OK;
+}
+
+sdmm_status sdmm_sample(const sdmm_config* cfg, const sdmm_state* st, int64_t R, int64_t Q,
+                        const float* qx, const int32_t* region, const sdmm_grid* grid, uint64_t seed,
+                        const float* uniforms, float* dir_out, float* pdf_out, uint8_t* valid_out,
+                        sdmm_stream stream) {
+    GridF g;
+    sdmm_status e = query_common(cfg, st, R, Q, qx, region, grid, &g);
+    if (e) return e;
+    if (Q > 0 && (!dir_out || !pdf_out || !valid_out)) return fail(SDMM_ERR_INVALID_ARG, "outputs are NULL");
+    if (Q == 0) return SDMM_OK;
+    SDMM_CUDA(launch_query(stream, OP_SAMPLE, pow2_ceil(cfg->K), query_grid(Q), st->qtab, cfg->K, R, Q, qx,
+                           region, g, seed, uniforms, nullptr, nullptr, nullptr, nullptr, dir_out,
+                           pdf_out, valid_out),
+              "sample");
+    return SDMM_OK;
+}
+
+sdmm_status sdmm_pdf(const sdmm_config* cfg, const sdmm_state* st, int64_t R, int64_t Q,
+                     const float* qx, const int32_t* region, const sdmm_grid* grid, const float* dir,
+                     float* pdf_out, sdmm_stream stream) {
+    GridF g;
+    sdmm_status e = query_common(cfg, st, R, Q, qx, region, grid, &g);
+    if (e) return e;
+    if (Q > 0 && (!dir || !pdf_out)) return fail(SDMM_ERR_INVALID_ARG, "dir/pdf_out are NULL");
+    if (Q == 0) return SDMM_OK;
+    SDMM_CUDA(launch_query(stream, OP_PDF, pow2_ceil(cfg->K), query_grid(Q), st->qtab, cfg->K, R, Q, qx,
+                           region, g, 0, nullptr, dir, nullptr, nullptr, nullptr, nullptr, pdf_out,
+                           nullptr),
+              "pdf");
+    return SDMM_OK;
+}
+
+// ---------------------------------------------------------------- objective
+static sdmm_status objective_common(const sdmm_config* cfg, const sdmm_samples* s,
+                                    const double* prior_scale, const sdmm_state* st, double* F_out,
+                                    const double* dF, float* gd, float* gL, float* ga, void* workspace,
+                                    size_t ws_bytes, cudaStream_t stream) {
+    sdmm_status e;
+    if ((e = check_config(cfg)) || (e = check_samples(s)) || (e = check_state(st, false))) return e;
+    if (!st->n_seen) return fail(SDMM_ERR_INVALID_ARG, "state.n_seen is NULL");
+    if (cfg->prior_scale_mode == SDMM_PRIOR_SCALE_ARRAY && !prior_scale)
+        return fail(SDMM_ERR_INVALID_ARG, "prior_scale_mode ARRAY needs prior_scale");
+    const Layout L = layout(cfg, s->R, s->N, choose_chunk(cfg, s->N));
+    if ((e = check_ws(workspace, ws_bytes, L))) return e;
+    const int nsm = sm_count();
+    if (nsm <= 0) return fail(SDMM_ERR_CUDA, "no CUDA device");
+    const WsPtrs w = ws_ptrs(workspace, L);
+    const int KP = pow2_ceil(cfg->K);
+    SDMM_CUDA(launch_set_desc(stream, w.hdr, make_desc(s, prior_scale, nullptr)), "set_desc");
+    SDMM_CUDA(launch_build_chunks(stream, w.hdr, w.cb, w.cr, L.chunk, 1, L.max_chunks), "build_chunks");
+    SDMM_CUDA(launch_accumulate(stream, dF ? MODE_GRAD : MODE_FIT, KP, nsm * default_ctas(cfg), w.hdr,
+                                w.cb, w.cr, st->etab, cfg->K, L.chunk, cfg->estep_density, w.partial,
+                                L.ps, 0),
+              "accumulate");
+    SDMM_CUDA(launch_reduce_objective(stream, s->R, w.hdr, w.cb, w.partial, L.ps, *cfg, *st, F_out, dF,
+                                      gd, gL, ga),
+              "reduce_objective");
+    return SDMM_OK;
+}
+
+sdmm_status sdmm_objective(const sdmm_config* cfg, const sdmm_samples* s, const double* prior_scale,
+                           const sdmm_state* st, double* F_out, void* workspace, size_t ws_bytes,
+                           sdmm_stream stream) {
+    if (!F_out) return fail(SDMM_ERR_INVALID_ARG, "F_out is NULL");
+    return objective_common(cfg, s, prior_scale, st, F_out, nullptr, nullptr, nullptr, nullptr,
+                            workspace, ws_bytes, stream);
+}
+
+sdmm_status sdmm_objective_backward(const sdmm_config* cfg, const sdmm_samples* s,
+                                    const double* prior_scale, const sdmm_state* st, const double* dF,
+                                    float* g_delta, float* g_L, float* g_logit, void* workspace,
+                                    size_t ws_bytes, sdmm_stream stream) {
+    if (!dF || !g_delta || !g_L || !g_logit) return fail(SDMM_ERR_INVALID_ARG, "dF/gradient outputs are NULL");
+    return objective_common(cfg, s, prior_scale, st, nullptr, dF, g_delta, g_L, g_logit, workspace,
+                            ws_bytes, stream);
+}
+
+// ---------------------------------------------------------------- plans
+struct sdmm_fit_plan {
+    FitLaunch f;
+    int64_t N_max;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<cudaEvent_t> cap_events;       // events recorded by the graph's event nodes
+    std::vector<cudaGraphNode_t> ev_nodes;     // node of cap_events[i]
+    std::vector<cudaEvent_t> pool;             // timing: 2*iters events per run
+    int32_t capacity = 0;
+    int32_t runs = 0;
+};
+
+sdmm_status sdmm_fit_plan_create(const sdmm_config* cfg, int64_t R, int64_t N_max, int32_t iters,
+                                 sdmm_state* st, void* workspace, size_t ws_bytes, sdmm_stream stream,
+                                 sdmm_fit_plan** plan_out) {
+    sdmm_status e;
+    if ((e = check_config(cfg)) || (e = check_state(st, true))) return e;
+    if (!plan_out) return fail(SDMM_ERR_INVALID_ARG, "plan_out is NULL");
+    *plan_out = nullptr;
+    if (R < 1 || N_max < 0 || iters < 1) return fail(SDMM_ERR_INVALID_ARG, "R, N_max, iters out of range");
+    if (cfg->precision != SDMM_PREC_FP32)
+        return fail(SDMM_ERR_UNSUPPORTED, "precision %d is not available in fit plans", cfg->precision);
+    const Layout L = layout(cfg, R, N_max, choose_chunk(cfg, N_max));
+    if ((e = check_ws(workspace, ws_bytes, L))) return e;
+    const int nsm = sm_count();
+    if (nsm <= 0) return fail(SDMM_ERR_CUDA, "no CUDA device");
+    sdmm_fit_plan* p = new sdmm_fit_plan();
+    p->f = FitLaunch{*cfg, *st, L, ws_ptrs(workspace, L), R, iters, nsm * default_ctas(cfg), 1};
+    p->N_max = N_max;
+    p->cap_events.resize(2 * iters);
+    for (auto& ev : p->cap_events) {
+        if (cudaEventCreate(&ev) != cudaSuccess) {
+            sdmm_fit_plan_destroy(p);
+            return fail(SDMM_ERR_CUDA, "cudaEventCreate failed");
+        }
+    }
+    cudaStream_t cs;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+        sdmm_fit_plan_destroy(p);
+        return fail(SDMM_ERR_CUDA, "cudaStreamCreate failed");
+    }
+    (void)stream;
+    cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    sdmm_status se = SDMM_OK;
+    if (ce == cudaSuccess) {
+        se = enqueue_fit(p->f, cs, &p->cap_events);
+        ce = cudaStreamEndCapture(cs, &p->graph);
+    }
+    cudaStreamDestroy(cs);
+    if (se != SDMM_OK || ce != cudaSuccess) {
+        sdmm_fit_plan_destroy(p);
+        return se != SDMM_OK ? se : cuda_fail(ce, "graph capture");
+    }
+    // locate the event-record nodes so that each run can retarget them
+    size_t n = 0;
+    cudaGraphGetNodes(p->graph, nullptr, &n);
+    std::vector<cudaGraphNode_t> nodes(n);
+    cudaGraphGetNodes(p->graph, nodes.data(), &n);
+    p->ev_nodes.assign(p->cap_events.size(), nullptr);
+    for (auto nd : nodes) {
+        cudaGraphNodeType t;
+        cudaGraphNodeGetType(nd, &t);
+        if (t != cudaGraphNodeTypeEventRecord) continue;
+        cudaEvent_t ev;
+        cudaGraphEventRecordNodeGetEvent(nd, &ev);
+        for (size_t i = 0; i < p->cap_events.size(); ++i)
+            if (p->cap_events[i] == ev) p->ev_nodes[i] = nd;
+    }
+    ce = cudaGraphInstantiate(&p->exec, p->graph, 0);
+    if (ce != cudaSuccess) {
+        sdmm_fit_plan_destroy(p);
+        return cuda_fail(ce, "graph instantiate");
+    }
+    *plan_out = p;
+    return SDMM_OK;
+}
+
+sdmm_status sdmm_fit_plan_run(sdmm_fit_plan* p, const sdmm_samples* s, const double* prior_scale,
+                              float* loglik_out, sdmm_stream stream) {
+    sdmm_status e;
+    if (!p) return fail(SDMM_ERR_INVALID_ARG, "plan is NULL");
+    if ((e = check_samples(s))) return e;
+    if (s->R != p->f.R) return fail(SDMM_ERR_INVALID_ARG, "batch R %lld != plan R %lld", (long long)s->R, (long long)p->f.R);
+    if (s->N > p->N_max) return fail(SDMM_ERR_INVALID_ARG, "batch N %lld > plan N_max %lld", (long long)s->N, (long long)p->N_max);
+    if (p->f.cfg.prior_scale_mode == SDMM_PRIOR_SCALE_ARRAY && !prior_scale)
+        return fail(SDMM_ERR_INVALID_ARG, "prior_scale_mode ARRAY needs prior_scale");
+    if (p->capacity > 0 && p->runs < p->capacity) {
+        for (size_t i = 0; i < p->ev_nodes.size(); ++i) {
+            if (!p->ev_nodes[i]) continue;
+            SDMM_CUDA(cudaGraphExecEventRecordNodeSetEvent(p->exec, p->ev_nodes[i],
+                                                           p->pool[(size_t)p->runs * p->ev_nodes.size() + i]),
+                      "retarget event");
+        }
+    }
+    SDMM_CUDA(launch_set_desc(stream, p->f.w.hdr, make_desc(s, prior_scale, loglik_out)), "set_desc");
+    SDMM_CUDA(cudaGraphLaunch(p->exec, stream), "graph launch");
+    if (p->capacity > 0 && p->runs < p->capacity) ++p->runs;
+    return SDMM_OK;
+}
+
+sdmm_status sdmm_fit_plan_enable_timing(sdmm_fit_plan* p, int32_t capacity) {
+    if (!p || capacity < 1) return fail(SDMM_ERR_INVALID_ARG, "plan NULL or capacity < 1");
+    for (auto ev : p->pool) cudaEventDestroy(ev);
+    p->pool.assign((size_t)capacity * p->ev_nodes.size(), nullptr);
+    for (auto& ev : p->pool) SDMM_CUDA(cudaEventCreate(&ev), "cudaEventCreate");
+    p->capacity = capacity;
+    p->runs = 0;
+    return SDMM_OK;
+}
+
+sdmm_status sdmm_fit_plan_timing(sdmm_fit_plan* p, float* ms_out, int32_t max, int32_t* n_out) {
+    if (!p || !n_out || (max > 0 && !ms_out)) return fail(SDMM_ERR_INVALID_ARG, "bad arguments");
+    const size_t per = p->ev_nodes.size();
+    int32_t n = 0;
+    for (int32_t r = 0; r < p->runs; ++r)
+        for (size_t i = 0; i + 1 < per; i += 2) {
+            cudaEvent_t a = p->pool[(size_t)r * per + i], b = p->pool[(size_t)r * per + i + 1];
+            SDMM_CUDA(cudaEventSynchronize(b), "event sync");
+            float ms = 0.f;
+            SDMM_CUDA(cudaEventElapsedTime(&ms, a, b), "event elapsed");
+            if (n < max) ms_out[n] = ms;
+            ++n;
+        }
+    *n_out = std::min(n, max);
+    p->runs = 0;
+    return SDMM_OK;
+}
+
+sdmm_status sdmm_fit_plan_destroy(sdmm_fit_plan* p) {
+    if (!p) return SDMM_OK;
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    for (auto ev : p->cap_events)
+        if (ev) cudaEventDestroy(ev);
+    for (auto ev : p->pool)
+        if (ev) cudaEventDestroy(ev);
+    delete p;
+    return SDMM_OK;
+}
+
+// ---------------------------------------------------------------- autotuner
+sdmm_status sdmm_autotune(const sdmm_config* cfg, const sdmm_samples* s, const sdmm_state* st,
+                          void* workspace, size_t ws_bytes, sdmm_stream stream, int32_t* chunk_out,
+                          int32_t* ctas_out, float* best_ms_out) {
+    sdmm_status e;
+    if ((e = check_config(cfg)) || (e = check_samples(s)) || (e = check_state(st, false))) return e;
+    if (!chunk_out || !ctas_out) return fail(SDMM_ERR_INVALID_ARG, "outputs are NULL");
+    const int nsm = sm_count();
+    if (nsm <= 0) return fail(SDMM_ERR_CUDA, "no CUDA device");
+    const int KP = pow2_ceil(cfg->K);
+    cudaEvent_t a, b;
+    SDMM_CUDA(cudaEventCreate(&a), "event");
+    SDMM_CUDA(cudaEventCreate(&b), "event");
+    float best = INFINITY;
+    int best_c = 0, best_g = 0;
+    const int chunks[] = {256, 512, 1024, 2048, 4096, 8192};
+    for (int c : chunks) {
+        const Layout L = layout(cfg, s->R, s->N, c);
+        if (L.total > ws_bytes || !workspace) continue;
+        const WsPtrs w = ws_ptrs(workspace, L);
+        for (int g = 1; g <= 4; ++g) {
+            float tmin = INFINITY;
+            for (int rep = 0; rep < 4; ++rep) {
+                if (launch_set_desc(stream, w.hdr, make_desc(s, nullptr, nullptr)) != cudaSuccess ||
+                    launch_build_chunks(stream, w.hdr, w.cb, w.cr, c, cfg->min_samples, L.max_chunks) != cudaSuccess)
+                    return fail(SDMM_ERR_CUDA, "autotune launch");
+                cudaEventRecord(a, stream);
+                if (launch_accumulate(stream, MODE_FIT, KP, nsm * g, w.hdr, w.cb, w.cr, st->etab, cfg->K, c,
+                                      cfg->estep_density, w.partial, L.ps, 0) != cudaSuccess)
+                    return fail(SDMM_ERR_CUDA, "autotune launch");
+                cudaEventRecord(b, stream);
+                SDMM_CUDA(cudaEventSynchronize(b), "autotune sync");
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, a, b);
+                if (rep > 0) tmin = std::min(tmin, ms);
+            }
+            if (tmin < best) {
+                best = tmin;
+                best_c = c;
+                best_g = g;
+            }
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (best_c == 0) return fail(SDMM_ERR_WORKSPACE, "workspace too small for any candidate");
+    *chunk_out = best_c;
+    *ctas_out = best_g;
+    if (best_ms_out) *best_ms_out = best;
+    return SDMM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,194 @@
+// common.cuh -- device-side building blocks shared by the SDMM kernels:
+// packed-triangle indexing, the chart rotation R_mu, the FP64 exp map and
+// Jacobian used by the M-step, and the layout of the derived FP32 records.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sdmm.h"
+
+namespace sdmm {
+
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+constexpr double kLog2Pi = 1.8378770664093454835606594728112;
+constexpr float kPiF = 3.14159265358979323846f;
+// inverse CDF of the chi-square distribution with 3 dof at 0.9 (App. B)
+constexpr double kChi2_3_q90 = 6.2513886311703222;
+
+// entry (i, j <= i) of a packed lower-triangular 5x5 matrix
+__host__ __device__ constexpr int pk(int i, int j) { return i * (i + 1) / 2 + j; }
+
+// Statistics per component in the work-unit partials: [s0, s1(5), s2(15)]
+constexpr int kStat = 21;
+// partial record of one work unit: K*21 component values, then W and sum w*l
+__host__ __device__ inline int partial_stride(int K) { return ((K * kStat + 2) + 3) & ~3; }
+
+// ---- derived FP32 records -------------------------------------------------
+// E-step record (SDMM_ETAB_FLOATS = 36 floats):
+//   [0..2] mu_x (+ position offset), rounded to FP32  [3..5] t  [6..8] b
+//   [9..11] mu_w  [12..26] L^-1 packed
+//   [27] c5 = log pi - sum log L_jj - (5/2) log 2 pi
+//   [28..29] in-chart direction offset (0 except for objective evaluation)
+//   [32..34] FP32 remainder of mu_x: x - mu = (x - hi) - lo keeps the
+//            spatial difference accurate for narrow spatial components
+// Query record (SDMM_QTAB_FLOATS = 36 floats):
+//   [0..2] mu_x (FP32)  [3..5] t  [6..8] b  [9..11] mu_w  [12..17] A^-1 packed
+//   [18..23] C^T (2x3 row-major)  [24..26] D (d00, d10, d11)
+//   [27..29] D^-1  [30] cx = log pi - log det A - (3/2) log 2 pi
+//   [31] cn = -log det D - log 2 pi  [32..34] FP32 remainder of mu_x
+// with L = [[A, 0], [C^T, D]] in (x, nu) order.
+constexpr int kE = SDMM_ETAB_FLOATS;
+constexpr int kQ = SDMM_QTAB_FLOATS;
+
+// R_mu with rows (t, b, mu): branchless orthonormal basis of Duff et al.,
+// "Building an Orthonormal Basis, Revisited", JCGT 6(1), 2017.
+__device__ inline void basis_f64(const double mu[3], double t[3], double b[3]) {
+    const double sgn = copysign(1.0, mu[2]);
+    const double a = -1.0 / (sgn + mu[2]);
+    const double c = mu[0] * mu[1] * a;
+    t[0] = 1.0 + sgn * mu[0] * mu[0] * a;
+    t[1] = sgn * c;
+    t[2] = -sgn * mu[0];
+    b[0] = c;
+    b[1] = sgn + mu[1] * mu[1] * a;
+    b[2] = -mu[1];
+}
+
+// sin(r)/r with its Taylor series near zero
+__device__ inline double sinc_f64(double r) {
+    if (fabs(r) < 1e-4) {
+        const double r2 = r * r;
+        return 1.0 - r2 / 6.0 + r2 * r2 / 120.0;
+    }
+    return sin(r) / r;
+}
+
+// exp_mu(nu) = R_mu^T (nu sinc|nu|, cos|nu|)   (Sec. 3.1, Eq. exp)
+__device__ inline void exp_map_f64(const double mu[3], const double nu[2], double out[3]) {
+    double t[3], b[3];
+    basis_f64(mu, t, b);
+    const double r = sqrt(nu[0] * nu[0] + nu[1] * nu[1]);
+    const double s = sinc_f64(r);
+    const double a0 = nu[0] * s, a1 = nu[1] * s, a2 = cos(r);
+    for (int c = 0; c < 3; ++c) out[c] = t[c] * a0 + b[c] * a1 + mu[c] * a2;
+}
+
+// Chart-change Jacobian J = J_log_{mu_new}(mu_new) * J_exp_{mu_old}(nu)
+// (App. A; at the chart centre J_log is the projection onto (t, b) of mu_new).
+__device__ inline void chart_jacobian_f64(const double mu_old[3], const double nu[2],
+                                          const double mu_new[3], double J[4]) {
+    double t0[3], b0[3], t1[3], b1[3];
+    basis_f64(mu_old, t0, b0);
+    basis_f64(mu_new, t1, b1);
+    const double r2 = nu[0] * nu[0] + nu[1] * nu[1];
+    const double r = sqrt(r2);
+    const double s = sinc_f64(r);
+    const double c = (r < 1e-2) ? (-1.0 / 3.0 + r2 / 30.0 - r2 * r2 / 840.0) : (cos(r) - s) / r2;
+    // d exp / d nu in the old chart's coordinates (3x2), then to world
+    const double Jp[3][2] = {{s + nu[0] * nu[0] * c, nu[0] * nu[1] * c},
+                             {nu[0] * nu[1] * c, s + nu[1] * nu[1] * c},
+                             {-nu[0] * s, -nu[1] * s}};
+    double Jw[3][2];
+    for (int row = 0; row < 3; ++row)
+        for (int col = 0; col < 2; ++col)
+            Jw[row][col] = t0[row] * Jp[0][col] + b0[row] * Jp[1][col] + mu_old[row] * Jp[2][col];
+    for (int col = 0; col < 2; ++col) {
+        J[0 * 2 + col] = t1[0] * Jw[0][col] + t1[1] * Jw[1][col] + t1[2] * Jw[2][col];
+        J[1 * 2 + col] = b1[0] * Jw[0][col] + b1[1] * Jw[1][col] + b1[2] * Jw[2][col];
+    }
+}
+
+// Cholesky of a packed symmetric 5x5; false if not positive definite.
+__device__ inline bool cholesky5_f64(const double S[15], double L[15]) {
+    for (int j = 0; j < 5; ++j) {
+        double d = S[pk(j, j)];
+        for (int p = 0; p < j; ++p) d -= L[pk(j, p)] * L[pk(j, p)];
+        if (!(d > 0.0) || !isfinite(d)) return false;
+        const double ljj = sqrt(d);
+        L[pk(j, j)] = ljj;
+        for (int i = j + 1; i < 5; ++i) {
+            double e = S[pk(i, j)];
+            for (int p = 0; p < j; ++p) e -= L[pk(i, p)] * L[pk(j, p)];
+            L[pk(i, j)] = e / ljj;
+        }
+    }
+    return true;
+}
+
+// Inverse of a packed lower-triangular 5x5 (also lower triangular).
+__device__ inline void lower_inverse5_f64(const double L[15], double Li[15]) {
+    for (int j = 0; j < 5; ++j) {
+        Li[pk(j, j)] = 1.0 / L[pk(j, j)];
+        for (int i = j + 1; i < 5; ++i) {
+            double s = 0.0;
+            for (int p = j; p < i; ++p) s += L[pk(i, p)] * Li[pk(p, j)];
+            Li[pk(i, j)] = -s / L[pk(i, i)];
+        }
+    }
+}
+
+// Writes the E-step and query records of one component.
+__device__ inline void write_records(double pi, const double mux[3], const double muw[3],
+                                     const double L[15], float* __restrict__ er,
+                                     float* __restrict__ qr, const double* delta = nullptr) {
+    double t[3], b[3], Li[15];
+    basis_f64(muw, t, b);
+    lower_inverse5_f64(L, Li);
+    const double lpi = pi > 0.0 ? log(pi) : -INFINITY;
+    const double ldA = log(L[pk(0, 0)]) + log(L[pk(1, 1)]) + log(L[pk(2, 2)]);
+    const double ldD = log(L[pk(3, 3)]) + log(L[pk(4, 4)]);
+    for (int c = 0; c < 3; ++c) {
+        er[0 + c] = qr[0 + c] = (float)mux[c];
+        er[3 + c] = qr[3 + c] = (float)t[c];
+        er[6 + c] = qr[6 + c] = (float)b[c];
+        er[9 + c] = qr[9 + c] = (float)muw[c];
+    }
+    for (int p = 0; p < 15; ++p) er[12 + p] = (float)Li[p];
+    er[27] = (float)(lpi - ldA - ldD - 2.5 * kLog2Pi);
+    er[28] = er[29] = er[30] = er[31] = er[35] = qr[35] = 0.f;
+    double me[3] = {mux[0], mux[1], mux[2]};
+    if (delta != nullptr) {
+        for (int c = 0; c < 3; ++c) me[c] += delta[c];
+        er[28] = (float)delta[3];
+        er[29] = (float)delta[4];
+    }
+    for (int c = 0; c < 3; ++c) {
+        er[c] = (float)me[c];
+        er[32 + c] = (float)(me[c] - (double)er[c]);
+        qr[32 + c] = (float)(mux[c] - (double)qr[c]);
+    }
+    for (int p = 0; p < 6; ++p) qr[12 + p] = (float)Li[p];
+    for (int c = 0; c < 3; ++c) {
+        qr[18 + c] = (float)L[pk(3, c)];
+        qr[21 + c] = (float)L[pk(4, c)];
+    }
+    qr[24] = (float)L[pk(3, 3)];
+    qr[25] = (float)L[pk(4, 3)];
+    qr[26] = (float)L[pk(4, 4)];
+    qr[27] = (float)Li[pk(3, 3)];
+    qr[28] = (float)Li[pk(4, 3)];
+    qr[29] = (float)Li[pk(4, 4)];
+    qr[30] = (float)(lpi - ldA - 1.5 * kLog2Pi);
+    qr[31] = (float)(-ldD - kLog2Pi);
+}
+
+// Batch descriptor written into the workspace before each fit step sequence.
+struct BatchDesc {
+    const float* p[7];          // px py pz ox oy oz w
+    const int64_t* offsets;
+    int64_t R;
+    int64_t N;
+    const double* prior_scale;  // nullable
+    float* loglik;              // nullable
+};
+
+// Workspace header (device)
+struct WsHeader {
+    BatchDesc desc;
+    int32_t n_chunks;
+    int32_t queue;
+    int32_t pad_[14];
+};
+
+}  // namespace sdmm

@@ -1,0 +1,700 @@
+// fit.cu -- SDMM fitting kernels for sm_103a.
+//
+//  k_set_desc       writes the batch descriptor into the workspace
+//  k_build_chunks   splits every region into work units of `chunk` samples
+//  k_accumulate     persistent E-step + statistics (or adjoint statistics):
+//                   one lane per mixture component, FP32, per-unit partials
+//  k_reduce_mstep   FP64 fixed-order reduction of a region's partials, then
+//                   Robbins-Monro averaging and the MAP M-step
+//  k_reduce_objective  MAP objective and its adjoint from the partials
+//  k_init_regions   initialisation (k-means++ seeds, App. B covariances)
+//  k_prepare        derived FP32 records from the FP64 parameters
+#include "common.cuh"
+#include "kernels.h"
+
+namespace sdmm {
+
+__global__ void k_set_desc(WsHeader* ws, BatchDesc d) { ws->desc = d; }
+
+// ---------------------------------------------------------------------------
+// Work units.  Region r with M_r >= min_samples samples gets ceil(M_r/chunk)
+// units; chunk_base is the exclusive prefix sum over regions (int64 scan),
+// chunk_region the owner of each unit.  Units beyond the workspace capacity
+// `max_chunks` (possible only when offsets overlap) are not created; the
+// M-step flags their regions.  One CTA of 1024 threads.
+__global__ void __launch_bounds__(1024) k_build_chunks(WsHeader* ws, int64_t* chunk_base,
+                                                       int32_t* chunk_region, int chunk,
+                                                       int min_samples, int64_t max_chunks) {
+    const int64_t R = ws->desc.R, N = ws->desc.N;
+    const int64_t* off = ws->desc.offsets;
+    __shared__ int64_t s_warp[32];
+    __shared__ int64_t s_carry;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < R; base += 1024) {
+        const int64_t r = base + tid;
+        int64_t n = 0;
+        if (r < R) {
+            const int64_t o0 = off[r], o1 = off[r + 1];
+            const bool ok = o0 >= 0 && o1 >= o0 && o1 <= N;
+            const int64_t M = o1 - o0;
+            if (ok && M >= min_samples && M > 0) n = (M + chunk - 1) / chunk;
+        }
+        int64_t v = n;
+        for (int d = 1; d < 32; d <<= 1) {
+            const int64_t u = __shfl_up_sync(0xffffffffu, v, d);
+            if (lane >= d) v += u;
+        }
+        if (lane == 31) s_warp[warp] = v;
+        __syncthreads();
+        if (warp == 0) {
+            int64_t w = s_warp[lane];
+            for (int d = 1; d < 32; d <<= 1) {
+                const int64_t u = __shfl_up_sync(0xffffffffu, w, d);
+                if (lane >= d) w += u;
+            }
+            s_warp[lane] = w;
+        }
+        __syncthreads();
+        const int64_t incl = v + (warp > 0 ? s_warp[warp - 1] : 0);
+        if (r < R) chunk_base[r] = s_carry + incl - n;
+        __syncthreads();
+        if (tid == 1023) s_carry += incl;
+        __syncthreads();
+    }
+    const int64_t total = s_carry;
+    if (tid == 0) {
+        chunk_base[R] = total;
+        ws->n_chunks = (int32_t)min(total, max_chunks);
+        ws->queue = 0;
+    }
+    for (int64_t r = tid; r < R; r += 1024) {
+        const int64_t c0 = chunk_base[r], c1 = min(chunk_base[r + 1], max_chunks);
+        for (int64_t c = c0; c < c1; ++c) chunk_region[c] = (int32_t)r;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// E-step + statistics.  A CTA of 8 warps takes work units from a global queue.
+// Within a warp, lane = (h, k): k = lane % KP is the mixture component and
+// h = lane / KP selects one of SPI = 32/KP samples processed side by side, so
+// each lane keeps its component's parameters and its 21 accumulators in
+// registers for the whole unit.  Samples are read coalesced (one per lane per
+// stream) into a per-warp shared buffer and then broadcast to the KP lanes of
+// each sample.  The per-sample log-sum-exp over components is a butterfly
+// over the KP lanes.
+//
+// MODE_FIT  accumulates w r [1, d, d d^T]          (Sec. 3.2 Eq. em-ss-computation)
+// MODE_GRAD accumulates w r [1, z, z y^T], y = L^-1 d, z = L^-T y (adjoint)
+// Both also accumulate W = sum w and sum w l_i.
+constexpr int kWarps = 8;
+
+template <int KP, int MODE>
+__global__ void __launch_bounds__(kWarps * 32, 2)
+    k_accumulate(WsHeader* __restrict__ ws, const int64_t* __restrict__ chunk_base,
+                 const int32_t* __restrict__ chunk_region, const float* __restrict__ etab, int K,
+                 int chunk, int density, float* __restrict__ partial, int ps, int write_ll) {
+    constexpr int SPI = 32 / KP;
+    constexpr int RED = KP * kStat + 4;
+    __shared__ __align__(16) float sbuf[kWarps][32][8];
+    __shared__ float red[kWarps][RED];
+    __shared__ int s_c;
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int k = lane & (KP - 1), h = lane / KP;
+    const float* __restrict__ px = ws->desc.p[0];
+    const float* __restrict__ py = ws->desc.p[1];
+    const float* __restrict__ pz = ws->desc.p[2];
+    const float* __restrict__ ox = ws->desc.p[3];
+    const float* __restrict__ oy = ws->desc.p[4];
+    const float* __restrict__ oz = ws->desc.p[5];
+    const float* __restrict__ pw = ws->desc.p[6];
+    const int64_t* __restrict__ off = ws->desc.offsets;
+    float* __restrict__ loglik = write_ll ? ws->desc.loglik : nullptr;
+    const int n_chunks = ws->n_chunks;
+
+    float prm[kE];
+    int prev_r = -1;
+    for (;;) {
+        if (threadIdx.x == 0) s_c = atomicAdd(&ws->queue, 1);
+        __syncthreads();
+        const int c = s_c;
+        if (c >= n_chunks) break;
+        const int r = chunk_region[c];
+        const int64_t o1 = off[r + 1];
+        const int64_t start = off[r] + ((int64_t)c - chunk_base[r]) * chunk;
+        const int64_t end = min(start + (int64_t)chunk, o1);
+        if (r != prev_r) {
+            prev_r = r;
+            if (k < K) {
+                const float4* src = reinterpret_cast<const float4*>(etab + ((int64_t)r * K + k) * kE);
+#pragma unroll
+                for (int q = 0; q < kE / 4; ++q) {
+                    const float4 v = __ldg(src + q);
+                    prm[4 * q + 0] = v.x;
+                    prm[4 * q + 1] = v.y;
+                    prm[4 * q + 2] = v.z;
+                    prm[4 * q + 3] = v.w;
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < kE; ++q) prm[q] = 0.f;
+                prm[11] = 1.f;
+                prm[27] = -INFINITY;
+            }
+        }
+        float acc[kStat];
+#pragma unroll
+        for (int s = 0; s < kStat; ++s) acc[s] = 0.f;
+        float wsum = 0.f, wll = 0.f;
+
+        for (int64_t g = start + warp * 32; g < end; g += kWarps * 32) {
+            const int64_t i = g + lane;
+            float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = make_float4(0.f, 0.f, 1.f, 0.f);
+            if (i < end) {
+                a = make_float4(__ldg(px + i), __ldg(py + i), __ldg(pz + i), __ldg(pw + i));
+                b = make_float4(__ldg(ox + i), __ldg(oy + i), __ldg(oz + i), 0.f);
+            }
+            *reinterpret_cast<float4*>(&sbuf[warp][lane][0]) = a;
+            *reinterpret_cast<float4*>(&sbuf[warp][lane][4]) = b;
+            __syncwarp();
+            const int n = (int)min((int64_t)32, end - g);
+            for (int t = 0; t < n; t += SPI) {
+                const int j = t + h;
+                const float4 sa = *reinterpret_cast<const float4*>(&sbuf[warp][j][0]);
+                const float4 sb = *reinterpret_cast<const float4*>(&sbuf[warp][j][4]);
+                // log map at this lane's component (Sec. 3.1 Eq. log)
+                const float u = prm[3] * sb.x + prm[4] * sb.y + prm[5] * sb.z;
+                const float v = prm[6] * sb.x + prm[7] * sb.y + prm[8] * sb.z;
+                const float cz = prm[9] * sb.x + prm[10] * sb.y + prm[11] * sb.z;
+                const float s2 = u * u + v * v;
+                const float rs = rsqrtf(s2);
+                const float th = atan2f(s2 * rs, cz);
+                const bool off_centre = s2 > 0.f;
+                const float gg = off_centre ? th * rs : 1.f;
+                float d[5];
+                d[0] = (sa.x - prm[0]) - prm[32];
+                d[1] = (sa.y - prm[1]) - prm[33];
+                d[2] = (sa.z - prm[2]) - prm[34];
+                d[3] = gg * u - prm[28];
+                d[4] = gg * v - prm[29];
+                const float* Li = prm + 12;
+                float y[5];
+                y[0] = Li[0] * d[0];
+                y[1] = Li[1] * d[0] + Li[2] * d[1];
+                y[2] = Li[3] * d[0] + Li[4] * d[1] + Li[5] * d[2];
+                y[3] = Li[6] * d[0] + Li[7] * d[1] + Li[8] * d[2] + Li[9] * d[3];
+                y[4] = Li[10] * d[0] + Li[11] * d[1] + Li[12] * d[2] + Li[13] * d[3] + Li[14] * d[4];
+                const float q = y[0] * y[0] + y[1] * y[1] + y[2] * y[2] + y[3] * y[3] + y[4] * y[4];
+                float l = prm[27] - 0.5f * q;
+                if (density) l += __logf(gg);
+                if (!off_centre && cz < 0.f) l = -INFINITY;   // cut locus: undefined chart
+                // log-sum-exp over the KP component lanes of this sample
+                float mx = l;
+#pragma unroll
+                for (int o = KP / 2; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+                const float e = (mx == -INFINITY) ? 0.f : __expf(l - mx);
+                float se = e;
+#pragma unroll
+                for (int o = KP / 2; o > 0; o >>= 1) se += __shfl_xor_sync(0xffffffffu, se, o);
+                const float rr = (se > 0.f) ? __fdividef(e, se) : 0.f;
+                const float wt = sa.w;
+                const float wr = wt * rr;
+                if (k == 0) {
+                    const float li = (se > 0.f) ? mx + __logf(se) : -INFINITY;
+                    wsum += wt;
+                    if (wt > 0.f) wll += wt * li;
+                    if (loglik != nullptr && j < n) loglik[g + j] = li;
+                }
+                float x[5];
+                if (MODE == MODE_FIT) {
+#pragma unroll
+                    for (int a2 = 0; a2 < 5; ++a2) x[a2] = d[a2];
+                } else {
+                    x[4] = Li[14] * y[4];
+                    x[3] = Li[9] * y[3] + Li[13] * y[4];
+                    x[2] = Li[5] * y[2] + Li[8] * y[3] + Li[12] * y[4];
+                    x[1] = Li[2] * y[1] + Li[4] * y[2] + Li[7] * y[3] + Li[11] * y[4];
+                    x[0] = Li[0] * y[0] + Li[1] * y[1] + Li[3] * y[2] + Li[6] * y[3] + Li[10] * y[4];
+#pragma unroll
+                    for (int a2 = 0; a2 < 5; ++a2) d[a2] = y[a2];
+                }
+                acc[0] += wr;
+#pragma unroll
+                for (int a2 = 0; a2 < 5; ++a2) {
+                    const float wa = wr * x[a2];
+                    acc[1 + a2] += wa;
+#pragma unroll
+                    for (int b2 = 0; b2 <= a2; ++b2) acc[6 + pk(a2, b2)] += wa * d[b2];
+                }
+            }
+            __syncwarp();
+        }
+        // combine the SPI sample slots of each component
+#pragma unroll
+        for (int o = KP; o < 32; o <<= 1) {
+#pragma unroll
+            for (int s = 0; s < kStat; ++s) acc[s] += __shfl_xor_sync(0xffffffffu, acc[s], o);
+            wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
+            wll += __shfl_xor_sync(0xffffffffu, wll, o);
+        }
+        if (h == 0 && k < K) {
+#pragma unroll
+            for (int s = 0; s < kStat; ++s) red[warp][k * kStat + s] = acc[s];
+        }
+        if (lane == 0) {
+            red[warp][K * kStat] = wsum;
+            red[warp][K * kStat + 1] = wll;
+        }
+        __syncthreads();
+        const int nv = K * kStat + 2;
+        for (int v = threadIdx.x; v < nv; v += kWarps * 32) {
+            float s = 0.f;
+#pragma unroll
+            for (int w = 0; w < kWarps; ++w) s += red[w][v];
+            partial[(int64_t)c * ps + v] = s;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Sum of a region's unit partials in FP64, in unit order (deterministic).
+__device__ inline void reduce_partials(const float* __restrict__ partial, int ps, int64_t c0,
+                                       int64_t c1, int nv, double* __restrict__ out) {
+    for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+        double s = 0.0;
+        for (int64_t c = c0; c < c1; ++c) s += (double)partial[c * ps + v];
+        out[v] = s;
+    }
+}
+
+__device__ inline double prior_beta(const sdmm_config& cfg, const double* prior_scale,
+                                    int64_t r, int64_t seen) {
+    if (cfg.prior_scale_mode == SDMM_PRIOR_SCALE_ARRAY && prior_scale != nullptr)
+        return prior_scale[r];
+    return seen > 0 ? 1.0 / (double)seen : 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// FP64 reduction + averaging + MAP M-step, one CTA per region (Sec. 3.2,
+// Sec. 3.4, Sec. 4.3).  Thread k < K updates component k.
+__global__ void __launch_bounds__(128) k_reduce_mstep(WsHeader* __restrict__ ws,
+                                                      const int64_t* __restrict__ chunk_base,
+                                                      const float* __restrict__ partial, int ps,
+                                                      sdmm_config cfg, sdmm_state st, int iter) {
+    const int64_t r = blockIdx.x;
+    const int K = cfg.K;
+    const int tid = threadIdx.x;
+    __shared__ double s_st[SDMM_MAX_K * kStat + 2];
+    __shared__ double s_S0[SDMM_MAX_K];
+    __shared__ int s_code[SDMM_MAX_K];
+    __shared__ int s_skip;
+
+    // the accumulate kernel of this step has finished: re-arm its work queue
+    if (r == 0 && tid == 0) ws->queue = 0;
+    const int64_t o0 = ws->desc.offsets[r], o1 = ws->desc.offsets[r + 1];
+    const int64_t M = o1 - o0;
+    const int64_t n_chunks = ws->n_chunks;
+    const int64_t c0 = chunk_base[r], c1 = chunk_base[r + 1];
+    if (tid == 0) {
+        int code = -1;  // -1: proceed
+        if (iter == 0) {
+            if (!(o0 >= 0 && o1 >= o0 && o1 <= ws->desc.N) || c1 > n_chunks)
+                code = SDMM_REGION_BAD_OFFSETS;
+            else if (M < cfg.min_samples || M <= 0) code = SDMM_REGION_SKIPPED;
+            if (code >= 0) st.status[r] = code;
+        } else if (st.status[r] != SDMM_REGION_OK) {
+            code = st.status[r];
+        }
+        s_skip = code;
+    }
+    __syncthreads();
+    if (s_skip >= 0) return;
+    reduce_partials(partial, ps, c0, c1, K * kStat + 2, s_st);
+    __syncthreads();
+    const double W = s_st[K * kStat];
+    if (tid == 0) {
+        int code = -1;
+        if (!isfinite(W)) code = SDMM_REGION_NONFINITE;
+        else if (!(W > 0.0)) code = SDMM_REGION_ZERO_WEIGHT;
+        if (code >= 0) st.status[r] = code;
+        s_skip = code;
+    }
+    __syncthreads();
+    if (s_skip >= 0) return;
+
+    const int64_t seen = (iter == 0) ? st.n_seen[r] + M : st.n_seen[r];
+    const double beta = prior_beta(cfg, ws->desc.prior_scale, r, seen);
+    const double eta = (cfg.eta_mode == SDMM_ETA_ONE)
+                           ? 1.0
+                           : pow(cfg.eta_beta * (double)st.step_j[r] + 1.0, -cfg.eta_alpha);
+    const double q = cfg.prior_q / K, a = cfg.prior_a / K;
+
+    double nmx[3], nmw[3], nL[15], nS2[15], hS0 = 0.0;
+    int code = 0;
+    const int64_t rk = r * K + tid;
+    if (tid < K) {
+        const double* sk = s_st + tid * kStat;
+        const double invW = 1.0 / W;
+        // Robbins-Monro average of the normalised batch statistics; the
+        // stored first moment is zero (centred at the current mean)
+        hS0 = (1.0 - eta) * st.S0[rk] + eta * (sk[0] * invW);
+        double m[5], hS2[15];
+        bool fin = isfinite(hS0);
+        for (int c = 0; c < 5; ++c) {
+            const double h1 = eta * (sk[1 + c] * invW);
+            fin = fin && isfinite(h1);
+            m[c] = hS0 > 0.0 ? h1 / hS0 : 0.0;
+        }
+        for (int p = 0; p < 15; ++p) {
+            hS2[p] = (1.0 - eta) * st.S2[rk * 15 + p] + eta * (sk[6 + p] * invW);
+            fin = fin && isfinite(hS2[p]);
+        }
+        if (!fin) {
+            code = SDMM_REGION_NONFINITE;
+        } else {
+            double omx[3], omw[3];
+            for (int c = 0; c < 3; ++c) {
+                omx[c] = st.mu_x[rk * 3 + c];
+                omw[c] = st.mu_w[rk * 3 + c];
+                nmx[c] = omx[c] + m[c];
+            }
+            exp_map_f64(omw, m + 3, nmw);                 // Eq. tangent-space-mu-update
+            // centred second moment in the old chart ...
+            double C[15];
+            for (int i = 0; i < 5; ++i)
+                for (int j = 0; j <= i; ++j) C[pk(i, j)] = hS2[pk(i, j)] - hS0 * m[i] * m[j];
+            // ... moved to the new chart: T C T^T, T = blockdiag(I3, J) (Sec. 3.4)
+            double J[4];
+            chart_jacobian_f64(omw, m + 3, nmw, J);
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j <= i; ++j) nS2[pk(i, j)] = C[pk(i, j)];
+            for (int ia = 0; ia < 2; ++ia)
+                for (int j = 0; j < 3; ++j)
+                    nS2[pk(3 + ia, j)] = J[ia * 2 + 0] * C[pk(3, j)] + J[ia * 2 + 1] * C[pk(4, j)];
+            const double c33 = C[pk(3, 3)], c43 = C[pk(4, 3)], c44 = C[pk(4, 4)];
+            for (int ia = 0; ia < 2; ++ia)
+                for (int ib = 0; ib <= ia; ++ib) {
+                    const double a0 = J[ia * 2 + 0], a1 = J[ia * 2 + 1];
+                    const double b0 = J[ib * 2 + 0], b1 = J[ib * 2 + 1];
+                    nS2[pk(3 + ia, 3 + ib)] =
+                        a0 * (c33 * b0 + c43 * b1) + a1 * (c43 * b0 + c44 * b1);
+                }
+            // MAP covariance (Sec. 4.3)
+            const double Bd[5] = {a * cfg.prior_B_pos, a * cfg.prior_B_pos, a * cfg.prior_B_pos,
+                                  a * cfg.prior_B_dir, a * cfg.prior_B_dir};
+            const double den = beta * a + hS0;
+            double Sig[15];
+            for (int i = 0; i < 5; ++i)
+                for (int j = 0; j <= i; ++j)
+                    Sig[pk(i, j)] = ((i == j ? beta * Bd[i] : 0.0) + nS2[pk(i, j)]) / den;
+            if (!cholesky5_f64(Sig, nL)) code = SDMM_REGION_NUMERIC;
+        }
+        s_code[tid] = code;
+        s_S0[tid] = hS0;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int first = 0;
+        for (int kk = 0; kk < K && first == 0; ++kk) first = s_code[kk];
+        s_skip = first;
+        if (first != 0) st.status[r] = first;
+    }
+    __syncthreads();
+    if (s_skip != 0) return;
+    if (tid < K) {
+        double sumS0 = 0.0;
+        for (int kk = 0; kk < K; ++kk) sumS0 += s_S0[kk];
+        const double npi = (beta * q + hS0) / (K * beta * q + sumS0);  // MAP weights
+        st.pi[rk] = npi;
+        for (int c = 0; c < 3; ++c) {
+            st.mu_x[rk * 3 + c] = nmx[c];
+            st.mu_w[rk * 3 + c] = nmw[c];
+        }
+        for (int p = 0; p < 15; ++p) {
+            st.L[rk * 15 + p] = nL[p];
+            st.S2[rk * 15 + p] = nS2[p];
+        }
+        st.S0[rk] = hS0;
+        write_records(npi, nmx, nmw, nL, st.etab + rk * kE, st.qtab + rk * kQ);
+    }
+    if (tid == 0) {
+        st.Wbar[r] = (1.0 - eta) * st.Wbar[r] + eta * (W / (double)M);
+        st.step_j[r] += 1;
+        st.n_seen[r] = seen;
+        st.status[r] = SDMM_REGION_OK;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// MAP objective (and, with dF != nullptr, its adjoint) from the partials.
+__global__ void __launch_bounds__(128) k_reduce_objective(
+    const WsHeader* __restrict__ ws, const int64_t* __restrict__ chunk_base,
+    const float* __restrict__ partial, int ps, sdmm_config cfg, sdmm_state st, double* F_out,
+    const double* __restrict__ dF, float* g_delta, float* g_L, float* g_logit) {
+    const int64_t r = blockIdx.x;
+    const int K = cfg.K;
+    const int tid = threadIdx.x;
+    __shared__ double s_st[SDMM_MAX_K * kStat + 2];
+    __shared__ double s_Fk[SDMM_MAX_K];
+    const int64_t nc = ws->n_chunks;
+    reduce_partials(partial, ps, min(chunk_base[r], nc), min(chunk_base[r + 1], nc), K * kStat + 2, s_st);
+    __syncthreads();
+    const double W = s_st[K * kStat];
+    const double beta = prior_beta(cfg, ws->desc.prior_scale, r, st.n_seen[r]);
+    const double q = cfg.prior_q / K, a = cfg.prior_a / K;
+    if (tid < K) {
+        const int64_t rk = r * K + tid;
+        const double* L = st.L + rk * 15;
+        double Li[15];
+        lower_inverse5_f64(L, Li);
+        const double Bd[5] = {a * cfg.prior_B_pos, a * cfg.prior_B_pos, a * cfg.prior_B_pos,
+                              a * cfg.prior_B_dir, a * cfg.prior_B_dir};
+        // Sigma^-1 = L^-T L^-1
+        double Sinv[5][5];
+        for (int i = 0; i < 5; ++i)
+            for (int j = 0; j < 5; ++j) {
+                double s = 0.0;
+                for (int m = (i > j ? i : j); m < 5; ++m) s += Li[pk(m, i)] * Li[pk(m, j)];
+                Sinv[i][j] = s;
+            }
+        double logdet = 0.0, trBS = 0.0;
+        for (int j = 0; j < 5; ++j) {
+            logdet += 2.0 * log(L[pk(j, j)]);
+            trBS += Bd[j] * Sinv[j][j];
+        }
+        const double pi = st.pi[rk];
+        s_Fk[tid] = beta * q * log(pi) - 0.5 * beta * a * logdet - 0.5 * beta * trBS;
+        if (dF != nullptr) {
+            const double sc = dF[r];
+            const double* sk = s_st + tid * kStat;
+            const double invW = W > 0.0 ? 1.0 / W : 0.0;
+            for (int c = 0; c < 5; ++c) g_delta[rk * 5 + c] = (float)(sc * sk[1 + c] * invW);
+            for (int i = 0; i < 5; ++i)
+                for (int j = 0; j <= i; ++j) {
+                    double s = 0.0;   // (Sigma^-1 B L^-T)_{ij}
+                    for (int c = 0; c <= j; ++c) s += Sinv[i][c] * Bd[c] * Li[pk(j, c)];
+                    double gv = sk[6 + pk(i, j)] * invW + beta * s;
+                    if (i == j) gv -= (sk[0] * invW + beta * a) / L[pk(i, i)];
+                    g_L[rk * 15 + pk(i, j)] = (float)(sc * gv);
+                }
+            g_logit[rk] = (float)(sc * (sk[0] * invW - pi + beta * q * (1.0 - K * pi)));
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double F = W > 0.0 ? s_st[K * kStat + 1] / W : 0.0;
+        for (int kk = 0; kk < K; ++kk) F += s_Fk[kk];
+        if (F_out != nullptr) F_out[r] = F;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Initialisation (Sec. 4.3 "Initialization", App. B, App. C), one thread per
+// region.  The weighted picks are sequential FP64 sums with explicit
+// round-to-nearest operations (no contraction), so that the chosen samples
+// are reproducible bit for bit.
+__device__ int64_t pick_index(const float* __restrict__ pw, const float* __restrict__ px,
+                              const float* __restrict__ py, const float* __restrict__ pz,
+                              int64_t o, int64_t M, const int64_t* seeds, int n_seeds, double u) {
+    auto weight = [&](int64_t i) {
+        double c = (double)pw[o + i];
+        c = c < 0.1 ? 0.1 : (c > 3.0 ? 3.0 : c);   // App. C: clamp to [W0, W1]
+        if (n_seeds == 0) return c;
+        double dmin = INFINITY;
+        for (int s = 0; s < n_seeds; ++s) {
+            const double dx = __dsub_rn((double)px[o + i], (double)px[o + seeds[s]]);
+            const double dy = __dsub_rn((double)py[o + i], (double)py[o + seeds[s]]);
+            const double dz = __dsub_rn((double)pz[o + i], (double)pz[o + seeds[s]]);
+            const double dd = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)),
+                                                   __dmul_rn(dz, dz)));
+            dmin = dd < dmin ? dd : dmin;
+        }
+        return __dmul_rn(c, dmin);
+    };
+    double tot = 0.0;
+    for (int64_t i = 0; i < M; ++i) tot = __dadd_rn(tot, weight(i));
+    if (!(tot > 0.0)) return -1;
+    const double t = __dmul_rn(u, tot);
+    double cum = 0.0;
+    int64_t last = -1;
+    for (int64_t i = 0; i < M; ++i) {
+        const double p = weight(i);
+        cum = __dadd_rn(cum, p);
+        if (p > 0.0) last = i;
+        if (t < cum) return i;
+    }
+    return last;
+}
+
+__global__ void k_init_regions(sdmm_config cfg, BatchDesc d, const double* __restrict__ extent,
+                               const double* __restrict__ uniforms, sdmm_state st) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= d.R) return;
+    const int K = cfg.K;
+    const int n_pos = (K % 8 == 0) ? K / 8 : 1;
+    const int n_dir = K / n_pos;
+    const int64_t o = d.offsets[r], M = d.offsets[r + 1] - d.offsets[r];
+    st.n_seen[r] = 0;
+    st.step_j[r] = 0;
+    st.Wbar[r] = 0.0;
+    for (int k = 0; k < K; ++k) {
+        st.S0[r * K + k] = 0.0;
+        for (int p = 0; p < 15; ++p) st.S2[(r * K + k) * 15 + p] = 0.0;
+    }
+    if (!(o >= 0 && M >= 0 && d.offsets[r + 1] <= d.N)) {
+        st.status[r] = SDMM_REGION_BAD_OFFSETS;
+        return;
+    }
+    if (M < cfg.min_samples || M <= 0) {
+        st.status[r] = SDMM_REGION_SKIPPED;
+        return;
+    }
+    int64_t seeds[SDMM_MAX_K / 8 > 0 ? SDMM_MAX_K / 8 : 1];
+    const float* px = d.p[0];
+    const float* py = d.p[1];
+    const float* pz = d.p[2];
+    const float* pw = d.p[6];
+    for (int j = 0; j < n_pos; ++j) {
+        const int64_t s = pick_index(pw, px, py, pz, o, M, seeds, j, uniforms[r * n_pos + j]);
+        seeds[j] = (s < 0) ? (j > 0 ? seeds[0] : 0) : s;
+    }
+    const double rst = 2.0 * extent[r] / n_pos;            // App. B: r_st = 2 d / n_pos
+    const double sx = rst / sqrt(kChi2_3_q90);
+    const double sw = sqrt(kTwoPi / n_dir);                  // App. B: sigma^2 = 2 pi / n_dir
+    for (int j = 0; j < n_pos; ++j) {
+        for (int t = 0; t < n_dir; ++t) {
+            const int64_t rk = r * K + j * n_dir + t;
+            double dv[3];
+            if (n_dir == 8) {
+                const double hh = 1.0 / sqrt(3.0);
+                dv[0] = (t & 1) ? -hh : hh;
+                dv[1] = (t & 2) ? -hh : hh;
+                dv[2] = (t & 4) ? -hh : hh;
+            } else {
+                const double ga = 3.141592653589793238462643383279502884 * (3.0 - sqrt(5.0));
+                const double z = 1.0 - (2.0 * t + 1.0) / n_dir;
+                const double rad = sqrt(1.0 - z * z);
+                dv[0] = rad * cos(ga * t);
+                dv[1] = rad * sin(ga * t);
+                dv[2] = z;
+            }
+            double mx[3] = {(double)px[o + seeds[j]], (double)py[o + seeds[j]],
+                            (double)pz[o + seeds[j]]};
+            double L[15];
+            for (int p = 0; p < 15; ++p) L[p] = 0.0;
+            for (int c = 0; c < 3; ++c) L[pk(c, c)] = sx;
+            for (int c = 3; c < 5; ++c) L[pk(c, c)] = sw;
+            st.pi[rk] = 1.0 / K;
+            for (int c = 0; c < 3; ++c) {
+                st.mu_x[rk * 3 + c] = mx[c];
+                st.mu_w[rk * 3 + c] = dv[c];
+            }
+            for (int p = 0; p < 15; ++p) st.L[rk * 15 + p] = L[p];
+            write_records(1.0 / K, mx, dv, L, st.etab + rk * kE, st.qtab + rk * kQ);
+        }
+    }
+    st.status[r] = SDMM_REGION_OK;
+}
+
+// ---------------------------------------------------------------------------
+__global__ void k_prepare(int K, int64_t R, sdmm_state st, const double* __restrict__ logits,
+                          const double* __restrict__ delta) {
+    const int64_t rk = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (rk >= R * K) return;
+    if (logits != nullptr) {
+        // pi = softmax(logits) over the region's K components
+        const int64_t r0 = (rk / K) * K;
+        double mx = -INFINITY;
+        for (int kk = 0; kk < K; ++kk) mx = fmax(mx, logits[r0 + kk]);
+        double s = 0.0;
+        for (int kk = 0; kk < K; ++kk) s += exp(logits[r0 + kk] - mx);
+        st.pi[rk] = exp(logits[rk] - mx) / s;
+    }
+    double mx[3], mw[3], L[15];
+    for (int c = 0; c < 3; ++c) {
+        mx[c] = st.mu_x[rk * 3 + c];
+        mw[c] = st.mu_w[rk * 3 + c];
+    }
+    for (int p = 0; p < 15; ++p) L[p] = st.L[rk * 15 + p];
+    write_records(st.pi[rk], mx, mw, L, st.etab + rk * kE, st.qtab + rk * kQ,
+                  delta != nullptr ? delta + rk * 5 : nullptr);
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launch helpers (declared in kernels.h)
+template <int MODE>
+static cudaError_t launch_acc_mode(int KP, dim3 grid, cudaStream_t s, WsHeader* ws,
+                                   const int64_t* cb, const int32_t* cr, const float* etab, int K,
+                                   int chunk, int density, float* partial, int ps, int write_ll) {
+#define SDMM_ACC_CASE(P)                                                                       \
+    case P:                                                                                    \
+        k_accumulate<P, MODE><<<grid, kWarps * 32, 0, s>>>(ws, cb, cr, etab, K, chunk, density, \
+                                                          partial, ps, write_ll);              \
+        break;
+    switch (KP) {
+        SDMM_ACC_CASE(1)
+        SDMM_ACC_CASE(2)
+        SDMM_ACC_CASE(4)
+        SDMM_ACC_CASE(8)
+        SDMM_ACC_CASE(16)
+        SDMM_ACC_CASE(32)
+        default: return cudaErrorInvalidValue;
+    }
+#undef SDMM_ACC_CASE
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_desc(cudaStream_t s, WsHeader* ws, const BatchDesc& d) {
+    k_set_desc<<<1, 1, 0, s>>>(ws, d);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_build_chunks(cudaStream_t s, WsHeader* ws, int64_t* cb, int32_t* cr, int chunk,
+                                int min_samples, int64_t max_chunks) {
+    k_build_chunks<<<1, 1024, 0, s>>>(ws, cb, cr, chunk, min_samples, max_chunks);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_accumulate(cudaStream_t s, int mode, int KP, int grid, WsHeader* ws,
+                              const int64_t* cb, const int32_t* cr, const float* etab, int K,
+                              int chunk, int density, float* partial, int ps, int write_ll) {
+    if (mode == MODE_FIT)
+        return launch_acc_mode<MODE_FIT>(KP, dim3(grid), s, ws, cb, cr, etab, K, chunk, density,
+                                         partial, ps, write_ll);
+    return launch_acc_mode<MODE_GRAD>(KP, dim3(grid), s, ws, cb, cr, etab, K, chunk, density,
+                                      partial, ps, write_ll);
+}
+
+cudaError_t launch_reduce_mstep(cudaStream_t s, int64_t R, WsHeader* ws, const int64_t* cb,
+                                const float* partial, int ps, const sdmm_config& cfg,
+                                const sdmm_state& st, int iter) {
+    k_reduce_mstep<<<(unsigned)R, 128, 0, s>>>(ws, cb, partial, ps, cfg, st, iter);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_objective(cudaStream_t s, int64_t R, const WsHeader* ws,
+                                    const int64_t* cb, const float* partial, int ps,
+                                    const sdmm_config& cfg, const sdmm_state& st, double* F,
+                                    const double* dF, float* gd, float* gL, float* ga) {
+    k_reduce_objective<<<(unsigned)R, 128, 0, s>>>(ws, cb, partial, ps, cfg, st, F, dF, gd, gL, ga);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init(cudaStream_t s, int64_t R, const sdmm_config& cfg, const BatchDesc& d,
+                        const double* extent, const double* uniforms, const sdmm_state& st) {
+    const unsigned blocks = (unsigned)((R + 127) / 128);
+    k_init_regions<<<blocks, 128, 0, s>>>(cfg, d, extent, uniforms, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prepare(cudaStream_t s, int K, int64_t R, const sdmm_state& st,
+                           const double* logits, const double* delta) {
+    const int64_t n = R * K;
+    const unsigned blocks = (unsigned)((n + 127) / 128);
+    k_prepare<<<blocks, 128, 0, s>>>(K, R, st, logits, delta);
+    return cudaGetLastError();
+}
+
+}  // namespace sdmm

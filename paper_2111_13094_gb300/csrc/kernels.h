@@ -1,0 +1,44 @@
+// kernels.h -- host-side launch helpers of the SDMM kernels (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace sdmm {
+
+enum { MODE_FIT = 0, MODE_GRAD = 1 };
+enum { OP_CONDITION = 0, OP_SAMPLE = 1, OP_PDF = 2 };
+
+struct GridF {
+    float lo[3];
+    float scale[3];
+    int32_t dims[3];
+    int32_t on;
+};
+
+cudaError_t launch_set_desc(cudaStream_t s, WsHeader* ws, const BatchDesc& d);
+cudaError_t launch_build_chunks(cudaStream_t s, WsHeader* ws, int64_t* cb, int32_t* cr, int chunk,
+                                int min_samples, int64_t max_chunks);
+cudaError_t launch_accumulate(cudaStream_t s, int mode, int KP, int grid, WsHeader* ws,
+                              const int64_t* cb, const int32_t* cr, const float* etab, int K,
+                              int chunk, int density, float* partial, int ps, int write_ll);
+cudaError_t launch_reduce_mstep(cudaStream_t s, int64_t R, WsHeader* ws, const int64_t* cb,
+                                const float* partial, int ps, const sdmm_config& cfg,
+                                const sdmm_state& st, int iter);
+cudaError_t launch_reduce_objective(cudaStream_t s, int64_t R, const WsHeader* ws,
+                                    const int64_t* cb, const float* partial, int ps,
+                                    const sdmm_config& cfg, const sdmm_state& st, double* F,
+                                    const double* dF, float* gd, float* gL, float* ga);
+cudaError_t launch_init(cudaStream_t s, int64_t R, const sdmm_config& cfg, const BatchDesc& d,
+                        const double* extent, const double* uniforms, const sdmm_state& st);
+cudaError_t launch_prepare(cudaStream_t s, int K, int64_t R, const sdmm_state& st,
+                           const double* logits, const double* delta);
+
+cudaError_t launch_query(cudaStream_t s, int op, int KP, int grid, const float* qtab, int K,
+                         int64_t R, int64_t Q, const float* qx, const int32_t* region,
+                         const GridF& g, uint64_t seed, const float* uni, const float* dir_in,
+                         float* cond_pi, float* cond_m, float* cond_L, float* dir_out,
+                         float* pdf_out, uint8_t* valid_out);
+
+}  // namespace sdmm

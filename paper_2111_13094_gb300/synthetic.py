@@ -75,20 +75,31 @@ def ground_truth(rng, R, K, cell_lo=None, cell_size=None, parallax=False) -> Gro
     ang = rng.uniform(0.0, math.pi, size=R * K)
     c, s = np.cos(ang), np.sin(ang)
     rot = np.stack([np.stack([c, -s], -1), np.stack([s, c], -1)], -2)      # (RK, 2, 2)
-    cnu = rot @ (sig[:, :, None] ** 2 * np.eye(2)) @ np.swapaxes(rot, 1, 2)
-    cov = np.zeros((R * K, 5, 5))
-    cov[:, :3, :3] = (sx.reshape(-1) ** 2)[:, None, None] * np.eye(3)
-    cov[:, 3:, 3:] = cnu
+    lnu = rot * sig[:, None, :]                                         # (RK, 2, 2)
+    F = np.zeros((R * K, 5, 5))
+    F[:, :3, :3] = sx.reshape(-1)[:, None, None] * np.eye(3)
+    F[:, 3:, 3:] = lnu
     if parallax:
-        # cross-covariance with correlation coefficients up to 0.6 in magnitude
-        rho = rng.uniform(-0.6, 0.6, size=(R * K, 3, 2)) / math.sqrt(3.0)
-        sdx = sx.reshape(-1)[:, None, None]
-        sdn = np.sqrt(np.diagonal(cnu, axis1=1, axis2=2))[:, None, :]
-        cov[:, :3, 3:] = rho * sdx * sdn
-        cov[:, 3:, :3] = np.swapaxes(cov[:, :3, 3:], 1, 2)
+        # direction noise partly driven by position noise: nu = Lnu (rho G z_x
+        # + sqrt(1 - rho^2) z_nu), correlation up to 0.6 (positive definite
+        # by construction)
+        rho = rng.uniform(0.0, 0.6, size=R * K)
+        G = rng.normal(size=(R * K, 2, 3)) / math.sqrt(3.0)
+        F[:, 3:, :3] = lnu @ (rho[:, None, None] * G)
+        F[:, 3:, 3:] = lnu * np.sqrt(1.0 - rho ** 2)[:, None, None]
+    cov = F @ np.swapaxes(F, 1, 2)
     return GroundTruth(pi=pi, mu_x=mu_x, mu_w=mu_w.reshape(R, K, 3),
                        e1=e1.reshape(R, K, 3), e2=e2.reshape(R, K, 3),
                        cov=cov.reshape(R, K, 5, 5))
+
+
+def _component_index(u, reg, gt: GroundTruth):
+    R, K = gt.R, gt.K
+    cum = np.cumsum(gt.pi, axis=1)
+    cum[:, -1] = 1.0
+    glob = (cum + np.arange(R)[:, None]).reshape(-1)
+    k = np.searchsorted(glob, reg + u, side="right") - reg * K
+    return reg * K + np.minimum(k, K - 1)
 
 
 def draw(rng, gt: GroundTruth, counts) -> np.ndarray:
@@ -97,35 +108,85 @@ def draw(rng, gt: GroundTruth, counts) -> np.ndarray:
     R, K = gt.R, gt.K
     N = int(counts.sum())
     reg = np.repeat(np.arange(R), counts)
-    # component by inverse CDF on each region's weights
-    cum = np.cumsum(gt.pi, axis=1)
-    cum[:, -1] = 1.0
-    glob = (cum + np.arange(R)[:, None]).reshape(-1)
-    k = np.searchsorted(glob, reg + rng.random(N), side="right") - reg * K
-    k = np.minimum(k, K - 1)
-    rk = reg * K + k
+    rk = _component_index(rng.random(N), reg, gt)
     chol = np.linalg.cholesky(gt.cov.reshape(R * K, 5, 5))
+    mux = gt.mu_x.reshape(-1, 3)
     out = np.empty((7, N), dtype=np.float32)
     x = np.empty((N, 3))
     nu = np.empty((N, 2))
     todo = np.arange(N)
     while todo.size:
         z = rng.normal(size=(todo.size, 5))
-        v = np.einsum("nij,nj->ni", chol[rk[todo]], z)
-        x[todo] = gt.mu_x.reshape(-1, 3)[rk[todo]] + v[:, :3]
+        idx = rk[todo]
+        v = np.zeros((todo.size, 5))
+        for i in range(5):                      # v = chol z, row by row
+            for j in range(i + 1):
+                v[:, i] += chol[idx, i, j] * z[:, j]
+        x[todo] = mux[idx] + v[:, :3]
         nu[todo] = v[:, 3:]
-        todo = todo[np.linalg.norm(nu[todo], axis=1) >= math.pi]
-    r = np.linalg.norm(nu, axis=1)
+        todo = todo[np.hypot(nu[todo, 0], nu[todo, 1]) >= math.pi]
+    r = np.hypot(nu[:, 0], nu[:, 1])
     safe = np.where(r > 0, r, 1.0)
     e1 = gt.e1.reshape(-1, 3)[rk]
     e2 = gt.e2.reshape(-1, 3)[rk]
-    t = (nu[:, :1] * e1 + nu[:, 1:] * e2) / safe[:, None]
     mu = gt.mu_w.reshape(-1, 3)[rk]
-    d = np.cos(r)[:, None] * mu + np.sin(r)[:, None] * t
+    cr, sr = np.cos(r), np.sin(r) / safe
+    d = cr[:, None] * mu + (sr * nu[:, 0])[:, None] * e1 + (sr * nu[:, 1])[:, None] * e2
     d /= np.linalg.norm(d, axis=1, keepdims=True)
     out[0:3] = x.T
     out[3:6] = d.T
     out[6] = rng.lognormal(0.0, 1.5, size=N)
+    return out
+
+
+def draw_torch(seed, gt: GroundTruth, counts, device="cuda", block=1 << 22):
+    """The same recipe as draw() with torch on `device` (a different random
+    stream, same distribution), for workloads too large to draw on the host.
+    Returns a (7, N) float32 tensor.  Works in blocks of `block` samples."""
+    import torch
+    counts = np.asarray(counts, dtype=np.int64)
+    R, K = gt.R, gt.K
+    N = int(counts.sum())
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    f64 = dict(dtype=torch.float64, device=device)
+    reg_all = torch.repeat_interleave(torch.arange(R, device=device),
+                                      torch.as_tensor(counts, device=device))
+    cum = torch.as_tensor(np.cumsum(gt.pi, axis=1), **f64)
+    cum[:, -1] = 1.0
+    glob = (cum + torch.arange(R, **f64)[:, None]).reshape(-1)
+    chol = torch.as_tensor(np.linalg.cholesky(gt.cov.reshape(R * K, 5, 5)), **f64)
+    mux = torch.as_tensor(gt.mu_x.reshape(-1, 3), **f64)
+    E1 = torch.as_tensor(gt.e1.reshape(-1, 3), **f64)
+    E2 = torch.as_tensor(gt.e2.reshape(-1, 3), **f64)
+    MU = torch.as_tensor(gt.mu_w.reshape(-1, 3), **f64)
+    out = torch.empty(7, N, dtype=torch.float32, device=device)
+    for b0 in range(0, N, block):
+        b1 = min(N, b0 + block)
+        n = b1 - b0
+        reg = reg_all[b0:b1]
+        u = torch.rand(n, generator=g, **f64)
+        k = torch.searchsorted(glob, reg.to(torch.float64) + u, right=True) - reg * K
+        rk = reg * K + torch.clamp(k, max=K - 1)
+        x = torch.empty(n, 3, **f64)
+        nu = torch.empty(n, 2, **f64)
+        todo = torch.arange(n, device=device)
+        while todo.numel():
+            z = torch.randn(todo.numel(), 5, generator=g, **f64)
+            v = torch.einsum("nij,nj->ni", chol[rk[todo]], z)
+            x[todo] = mux[rk[todo]] + v[:, :3]
+            nu[todo] = v[:, 3:]
+            todo = todo[torch.hypot(nu[todo, 0], nu[todo, 1]) >= math.pi]
+        r = torch.hypot(nu[:, 0], nu[:, 1])
+        safe = torch.where(r > 0, r, torch.ones_like(r))
+        sr = torch.sin(r) / safe
+        d = (torch.cos(r)[:, None] * MU[rk] + (sr * nu[:, 0])[:, None] * E1[rk]
+             + (sr * nu[:, 1])[:, None] * E2[rk])
+        d = d / torch.linalg.norm(d, dim=1, keepdim=True)
+        w = torch.exp(1.5 * torch.randn(n, generator=g, **f64))
+        out[0:3, b0:b1] = x.T.to(torch.float32)
+        out[3:6, b0:b1] = d.T.to(torch.float32)
+        out[6, b0:b1] = w.to(torch.float32)
     return out
 
 

@@ -1,0 +1,255 @@
+"""GPU fit path (C ABI -> CUDA kernels) against the FP64 oracle on the same
+seeded inputs: one step at small sizes with ragged tails over K = 1..32,
+the 20-iteration single-region workload, stepwise rounds, statuses, the
+initialisation, graph plans, determinism and resume, and sampled regions of
+the 4,096-region workload."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as orc
+from gpu_util import (LOGLIK_RTOL, PARAM_RTOL, assert_params_close, dev_batch, gpu_state, host,
+                      loglik_err, oracle_init)
+from paper_2111_13094_gb300 import api
+from paper_2111_13094_gb300 import synthetic as syn
+
+pytestmark = pytest.mark.gpu
+
+
+def _small_batch(seed, K, counts):
+    truth = syn.batched_truth(seed, len(counts), K=K, parallax=True)
+    return syn.batched_round(seed, len(counts), np.asarray(counts), 0, truth)
+
+
+@pytest.mark.parametrize("K", [1, 2, 3, 5, 8, 16, 32])
+def test_one_step_matches_oracle(K):
+    counts = [10, 16, 17, 255, 257, 1000, 3001]          # skipped, tiny, ragged, several tiles
+    b = _small_batch(100 + K, K, counts)
+    ost = oracle_init(100 + K, b, K)
+    ocfg = orc.config(K)
+    gcfg = api.config(K, chunk=256)
+    st = gpu_state(ost, gcfg)
+    oll = orc.fit_regions(ocfg, b.offsets, b.samples, 1, ost, want_loglik=True)
+    batch = dev_batch(b)
+    ws = api.workspace(gcfg, b.R, b.N)
+    ll = torch.zeros(b.N, dtype=torch.float32, device="cuda")
+    api.fit_regions(gcfg, batch, 1, st, ws, loglik=ll)
+    g = host(st)
+    assert list(g.status) == list(ost.status)
+    assert ost.status[0] == 1 and np.all(ost.status[1:] == 0)
+    mask = np.zeros(b.N, bool)
+    mask[b.offsets[1]:] = True
+    assert loglik_err(ll.cpu().numpy(), oll, mask) < LOGLIK_RTOL
+    assert_params_close(g, ost)
+    ok = ost.status == 0
+    assert np.array_equal(g.n_seen, ost.n_seen) and np.array_equal(g.step_j, ost.step_j)
+    assert np.allclose(g.Wbar[ok], ost.Wbar[ok], rtol=1e-5)
+    assert np.abs(g.S0 - ost.S0)[ok].max() < 1e-5
+    assert np.abs(g.S2 - ost.S2)[ok].max() < 1e-5 * np.abs(ost.S2[ok]).max() + 1e-9
+
+
+def test_single_region_20_iterations_plain_em():
+    """N = 65,536 samples of a 16-component truth, 20 EM iterations with eta = 1."""
+    K = 16
+    b = syn.single_region(seed=0, N=65536, K=K)
+    ost = oracle_init(0, b, K)
+    st = gpu_state(ost, api.config(K))
+    oll = orc.fit_regions(orc.config(K, eta_mode=1), b.offsets, b.samples, 20, ost, want_loglik=True)
+    gcfg = api.config(K, eta_mode=api.ETA_ONE)
+    ws = api.workspace(gcfg, 1, b.N)
+    ll = torch.zeros(b.N, dtype=torch.float32, device="cuda")
+    api.fit_regions(gcfg, dev_batch(b), 20, st, ws, loglik=ll)
+    g = host(st)
+    assert g.status[0] == 0 and g.step_j[0] == 20 and g.n_seen[0] == b.N
+    assert loglik_err(ll.cpu().numpy(), oll) < LOGLIK_RTOL
+    assert_params_close(g, ost)
+
+
+def test_solid_angle_density_mode():
+    K = 8
+    b = _small_batch(7, K, [500, 2000])
+    ost = oracle_init(7, b, K)
+    st = gpu_state(ost, api.config(K))
+    oll = orc.fit_regions(orc.config(K, estep_density=1), b.offsets, b.samples, 2, ost, want_loglik=True)
+    gcfg = api.config(K, estep_density=api.DENSITY_SOLID_ANGLE)
+    ll = torch.zeros(b.N, dtype=torch.float32, device="cuda")
+    api.fit_regions(gcfg, dev_batch(b), 2, st, api.workspace(gcfg, b.R, b.N), loglik=ll)
+    assert loglik_err(ll.cpu().numpy(), oll) < LOGLIK_RTOL
+    assert_params_close(host(st), ost)
+
+
+def test_stepwise_rounds_match_oracle():
+    """4 Robbins-Monro rounds with fresh batches (averaged statistics carried
+    over and moved between charts)."""
+    K, R = 16, 12
+    truth = syn.batched_truth(21, R, K=K)
+    counts = syn.region_counts(21, R, 256, 8000)
+    batches = [syn.batched_round(21, R, counts, r, truth) for r in range(4)]
+    ost = oracle_init(21, batches[0], K)
+    gcfg = api.config(K)
+    st = gpu_state(ost, gcfg)
+    ws = api.workspace(gcfg, R, int(counts.sum()))
+    for b in batches:
+        orc.fit_regions(orc.config(K), b.offsets, b.samples, 1, ost)
+        api.fit_regions(gcfg, dev_batch(b), 1, st, ws)
+        g = host(st)
+        assert_params_close(g, ost)
+        assert np.array_equal(g.step_j, ost.step_j) and np.array_equal(g.n_seen, ost.n_seen)
+        assert np.abs(g.S0 - ost.S0).max() < 1e-5
+
+
+def test_prior_scale_array_and_region_statuses():
+    K = 4
+    counts = [100, 100, 100, 8]
+    b = _small_batch(31, K, counts)
+    s = b.samples.copy()
+    o = b.offsets
+    s[6, o[1]:o[2]] = 0.0                      # zero weight
+    s[6, o[2] + 3] = np.nan                    # non-finite
+    ost = oracle_init(31, b, K)               # initialised on the clean batch
+    ost.status[:] = 0
+    beta = np.array([1e-3, 1e-3, 1e-3, 1e-3])
+    gcfg = api.config(K, prior_scale_mode=api.PRIOR_SCALE_ARRAY)
+    st = gpu_state(ost, gcfg)
+    bb = syn.Batch(s, o, b.extent, b.truth)
+    orc.fit_regions(orc.config(K, prior_scale_mode=1), o, s, 1, ost, prior_scale=beta)
+    api.fit_regions(gcfg, dev_batch(bb), 1, st, api.workspace(gcfg, 4, s.shape[1]),
+                    prior_scale=torch.from_numpy(beta).cuda())
+    g = host(st)
+    assert list(ost.status) == [0, 4, 3, 1]
+    assert list(g.status) == list(ost.status)
+    assert_params_close(g, ost)
+
+
+def test_bad_offsets_flagged():
+    K = 4
+    b = _small_batch(32, K, [100, 100, 100])
+    ost = oracle_init(32, b, K)
+    gcfg = api.config(K)
+    st = gpu_state(ost, gcfg)
+    off = b.offsets.copy()
+    off[2] = off[1] - 5                        # region 1 decreasing, region 2 overlapping
+    batch = api.SampleBatch(torch.from_numpy(b.samples).cuda(), torch.from_numpy(off).cuda())
+    api.fit_regions(gcfg, batch, 1, st, api.workspace(gcfg, 3, b.N))
+    assert list(host(st).status) == [0, 5, 0]
+
+
+def test_init_regions_matches_oracle():
+    for K in (16, 32, 8, 3):
+        counts = [10, 40, 700, 5000]
+        b = _small_batch(40 + K, K, counts)
+        ost = oracle_init(40 + K, b, K)
+        n_pos = K // 8 if K % 8 == 0 else 1
+        u = syn.init_uniforms(40 + K, b.R, n_pos)
+        gcfg = api.config(K)
+        st = api.MixtureState(b.R, K)
+        api.init_regions(gcfg, dev_batch(b), torch.from_numpy(b.extent.astype(np.float64)).cuda(),
+                         torch.from_numpy(u).cuda(), st)
+        g = host(st)
+        assert list(g.status) == list(ost.status) == [1, 0, 0, 0]
+        ok = ost.status == 0
+        # the chosen seeds are exact copies of the same samples
+        assert np.array_equal(g.mu_x[ok], ost.mu_x[ok])
+        assert np.allclose(g.mu_w[ok], ost.mu_w[ok], atol=1e-15)
+        assert np.array_equal(g.L[ok], ost.L[ok]) and np.array_equal(g.pi[ok], ost.pi[ok])
+
+
+def test_plan_graph_equals_direct_calls_and_is_deterministic():
+    K, R = 16, 24
+    truth = syn.batched_truth(5, R, K=K)
+    counts = syn.region_counts(5, R, 256, 20000)
+    batches = [syn.batched_round(5, R, counts, r, truth) for r in range(3)]
+    ost = oracle_init(5, batches[0], K)
+    gcfg = api.config(K)
+    a = gpu_state(ost, gcfg)
+    c = gpu_state(ost, gcfg)
+    d = gpu_state(ost, gcfg)
+    N = int(counts.sum())
+    ws1, ws2, ws3 = (api.workspace(gcfg, R, N) for _ in range(3))
+    plan = api.FitPlan(gcfg, R, N, 2, c, ws2)
+    plan.enable_timing(8)
+    for b in batches:
+        db = dev_batch(b)
+        api.fit_regions(gcfg, db, 2, a, ws1)
+        plan.run(db)
+        api.fit_regions(gcfg, db, 2, d, ws3)
+    times = plan.timing()
+    plan.close()
+    assert len(times) == 6 and all(t > 0 for t in times)
+    for f in api.MixtureState.FIELDS:
+        assert torch.equal(getattr(a, f), getattr(c, f)), f
+        assert torch.equal(getattr(a, f), getattr(d, f)), f
+
+
+def test_checkpoint_resume_is_bit_identical():
+    K, R = 16, 8
+    truth = syn.batched_truth(6, R, K=K)
+    counts = syn.region_counts(6, R, 256, 5000)
+    batches = [dev_batch(syn.batched_round(6, R, counts, r, truth)) for r in range(4)]
+    ost = oracle_init(6, syn.batched_round(6, R, counts, 0, truth), K)
+    gcfg = api.config(K)
+    ws = api.workspace(gcfg, R, int(counts.sum()))
+    a = gpu_state(ost, gcfg)
+    for b in batches:
+        api.fit_regions(gcfg, b, 1, a, ws)
+    b0 = gpu_state(ost, gcfg)
+    for b in batches[:2]:
+        api.fit_regions(gcfg, b, 1, b0, ws)
+    saved = {k: v.cpu() for k, v in b0.state_dict().items()}
+    c = api.MixtureState(R, K)
+    c.load_state_dict({k: v.cuda() for k, v in saved.items()}, cfg=gcfg)
+    for b in batches[2:]:
+        api.fit_regions(gcfg, b, 1, c, ws)
+    for f in api.MixtureState.FIELDS:
+        assert torch.equal(getattr(a, f), getattr(c, f)), f
+
+
+def test_batched_4096_regions_sampled_against_oracle():
+    """4,096 regions with log-uniform counts in [256, 65,536] (about 48M
+    samples), one stepwise round in one launch sequence; eight regions
+    (smallest, largest and six random) re-fitted by the oracle."""
+    K, R = 16, 4096
+    truth = syn.batched_truth(1, R, K=K)
+    counts = syn.region_counts(1, R)
+    dev_s = syn.draw_torch(1, truth, counts, device="cuda")
+    _, h, _ = syn.region_grid(R)
+    b = syn.Batch(dev_s.cpu().numpy(), syn.offsets_from_counts(counts), h, truth)
+    gcfg = api.config(K)
+    st = api.MixtureState(R, K)
+    batch = api.SampleBatch(dev_s, torch.from_numpy(b.offsets).cuda())
+    u = syn.init_uniforms(1, R, 2)
+    api.init_regions(gcfg, batch, torch.from_numpy(b.extent.astype(np.float64)).cuda(),
+                     torch.from_numpy(u).cuda(), st)
+    init = host(st)
+    ll = torch.zeros(b.N, dtype=torch.float32, device="cuda")
+    api.fit_regions(gcfg, batch, 1, st, api.workspace(gcfg, R, b.N), loglik=ll)
+    g = host(st)
+    assert np.all(g.status == 0)
+    rng = np.random.default_rng(0)
+    pick = np.unique(np.concatenate([[np.argmin(counts), np.argmax(counts)], rng.choice(R, 6, replace=False)]))
+    sub_counts = counts[pick]
+    sub_off = syn.offsets_from_counts(sub_counts)
+    sub = np.concatenate([b.samples[:, b.offsets[r]:b.offsets[r + 1]] for r in pick], axis=1)
+    ost = orc.State(len(pick), K)
+    for f in orc.State.FIELDS:
+        getattr(ost, f)[...] = getattr(init, f)[pick]
+    oll = orc.fit_regions(orc.config(K), sub_off, sub, 1, ost, want_loglik=True)
+    gsub = orc.State(len(pick), K)
+    for f in orc.State.FIELDS:
+        getattr(gsub, f)[...] = getattr(g, f)[pick]
+    assert_params_close(gsub, ost)
+    gll = np.concatenate([ll[b.offsets[r]:b.offsets[r + 1]].cpu().numpy() for r in pick])
+    assert loglik_err(gll, oll) < LOGLIK_RTOL
+
+
+def test_autotune_returns_a_valid_candidate():
+    K, R = 16, 64
+    truth = syn.batched_truth(9, R, K=K)
+    counts = syn.region_counts(9, R)
+    b = syn.batched_round(9, R, counts, 0, truth)
+    ost = oracle_init(9, b, K)
+    gcfg = api.config(K, chunk=256)
+    st = gpu_state(ost, gcfg)
+    ws = api.workspace(gcfg, R, b.N)
+    chunk, ctas, ms = api.autotune(gcfg, dev_batch(b), st, ws)
+    assert chunk in (256, 512, 1024, 2048, 4096, 8192) and 1 <= ctas <= 4 and ms > 0

@@ -1,0 +1,201 @@
+"""GPU query path (condition, sample, pdf) against the FP64 oracle, on small
+cases and on sampled outputs of the 16M-query / 65,536-region workload."""
+import math
+
+import numpy as np
+import pytest
+import torch
+from scipy import stats
+
+import oracle as orc
+from gpu_util import PDF_RTOL, gpu_state
+from paper_2111_13094_gb300 import api
+from paper_2111_13094_gb300 import synthetic as syn
+
+pytestmark = pytest.mark.gpu
+
+
+def _mixtures(seed, dims, K):
+    pi, mu_x, mu_w, L = syn.random_mixtures(seed, dims, K)
+    R = int(np.prod(dims))
+    ost = orc.State(R, K)
+    ost.set_params(pi, mu_x, mu_w, L)
+    return ost
+
+
+def _queries(seed, Q, dims):
+    qx = syn.query_points(seed, Q)
+    return qx, syn.grid_region(qx, dims)
+
+
+@pytest.mark.parametrize("K", [1, 3, 16, 32])
+def test_condition_matches_oracle(K):
+    dims = (4, 4, 2)
+    ost = _mixtures(1, dims, K)
+    cfg = api.config(K)
+    st = gpu_state(ost, cfg)
+    qx, reg = _queries(2, 3000, dims)
+    cpi, cm, cL = api.condition(cfg, st, torch.from_numpy(qx).cuda(), region=torch.from_numpy(reg).cuda())
+    opi, om, oL = orc.condition(K, ost.pi, ost.mu_x, ost.mu_w, ost.L, qx, reg)
+    assert np.abs(cpi.cpu().numpy() - opi).max() < 2e-5
+    assert np.abs(cm.cpu().numpy() - om).max() < 1e-5 * max(1.0, np.abs(om).max())
+    assert np.allclose(cL.cpu().numpy(), oL, rtol=1e-6)
+
+
+def _angle(a, b):
+    a = a / np.linalg.norm(a, axis=1, keepdims=True)
+    b = b / np.linalg.norm(b, axis=1, keepdims=True)
+    return 2 * np.arcsin(np.clip(np.linalg.norm(a - b, axis=1) / 2, 0, 1))
+
+
+@pytest.mark.parametrize("K", [2, 16, 32])
+def test_sample_and_pdf_match_oracle(K):
+    dims = (4, 4, 4)
+    ost = _mixtures(3, dims, K)
+    cfg = api.config(K)
+    st = gpu_state(ost, cfg)
+    Q = 20000
+    qx, reg = _queries(4, Q, dims)
+    u = np.random.default_rng(5).random((Q, 3), dtype=np.float32)
+    d, p, v = api.sample(cfg, st, torch.from_numpy(qx).cuda(), region=torch.from_numpy(reg).cuda(),
+                         uniforms=torch.from_numpy(u).cuda())
+    d, p, v = d.cpu().numpy(), p.cpu().numpy(), v.cpu().numpy()
+    o = orc.sample(K, ost.pi, ost.mu_x, ost.mu_w, ost.L, qx, reg, u)
+    same = o["margin"] > 1e-5                          # component choice is unique
+    assert same.mean() > 0.999
+    assert np.array_equal(v[same], o["valid"][same])
+    ok = same & (o["valid"] == 1)
+    assert _angle(d[ok].astype(np.float64), o["dir"][ok]).max() < 1e-4
+    # the reported pdf equals the FP64 pdf of the returned (FP32) direction
+    po = orc.pdf(K, ost.pi, ost.mu_x, ost.mu_w, ost.L, qx, reg, d.astype(np.float64))
+    vv = v == 1
+    rel = np.abs(p[vv] - po[vv]) / po[vv]
+    assert np.quantile(rel, 0.999) < PDF_RTOL, np.quantile(rel, [0.5, 0.99, 0.999, 1.0])
+    assert rel.max() < 10 * PDF_RTOL
+    assert np.all(p[~vv] == 0)
+
+
+def test_pdf_entry_matches_oracle():
+    K = 16
+    dims = (2, 2, 2)
+    ost = _mixtures(6, dims, K)
+    cfg = api.config(K)
+    st = gpu_state(ost, cfg)
+    Q = 20000
+    qx, reg = _queries(7, Q, dims)
+    rng = np.random.default_rng(8)
+    dirs = rng.normal(size=(Q, 3))
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    dirs = dirs.astype(np.float32)
+    p = api.pdf(cfg, st, torch.from_numpy(qx).cuda(), torch.from_numpy(dirs).cuda(),
+                region=torch.from_numpy(reg).cuda()).cpu().numpy()
+    po = orc.pdf(K, ost.pi, ost.mu_x, ost.mu_w, ost.L, qx, reg, dirs.astype(np.float64))
+    big = po > 1e-6 * po.max()
+    rel = np.abs(p[big] - po[big]) / po[big]
+    assert np.quantile(rel, 0.999) < PDF_RTOL, np.quantile(rel, [0.5, 0.99, 0.999, 1.0])
+    assert np.abs(p - po).max() < 1e-4 * po.max()
+
+
+def test_philox_and_grid_paths_are_exact():
+    """Device Philox uniforms equal the oracle's bit for bit, and the grid
+    lookup gives the generator's cell ids."""
+    K = 16
+    dims = (8, 4, 4)
+    ost = _mixtures(9, dims, K)
+    cfg = api.config(K)
+    st = gpu_state(ost, cfg)
+    Q = 50000
+    qx, reg = _queries(10, Q, dims)
+    tq = torch.from_numpy(qx).cuda()
+    u = orc.uniforms(1234, Q)
+    a = api.sample(cfg, st, tq, region=torch.from_numpy(reg).cuda(), uniforms=torch.from_numpy(u).cuda())
+    b = api.sample(cfg, st, tq, grid=api.Grid((0, 0, 0), (1, 1, 1), dims), seed=1234)
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
+
+
+def test_sample_histogram_chi_square_on_gpu():
+    K = 3
+    rng = np.random.default_rng(11)
+    pi = rng.dirichlet(np.ones(K))[None]
+    mu_x = rng.uniform(0.3, 0.7, (1, K, 3))
+    mu_w = rng.normal(size=(1, K, 3))
+    mu_w /= np.linalg.norm(mu_w, axis=2, keepdims=True)
+    L = np.zeros((1, K, 15))
+    for k in range(K):
+        diag = np.concatenate([rng.uniform(0.05, 0.2, 3), rng.uniform(0.4, 1.1, 2)])
+        for i in range(5):
+            for j in range(i + 1):
+                L[0, k, i * (i + 1) // 2 + j] = diag[i] if i == j else 0.4 * rng.normal() * diag[i]
+    ost = orc.State(1, K)
+    ost.set_params(pi, mu_x, mu_w, L)
+    cfg = api.config(K)
+    st = gpu_state(ost, cfg)
+    N = 1_000_000
+    x = np.tile(np.array([[0.5, 0.5, 0.5]], np.float32), (N, 1))
+    d, p, v = api.sample(cfg, st, torch.from_numpy(x).cuda(), region=torch.zeros(N, dtype=torch.int32).cuda(),
+                         seed=77)
+    d, v = d.cpu().numpy(), v.cpu().numpy().astype(bool)
+    n_z, n_phi, sub = 12, 24, 6
+    xs, ws = np.polynomial.legendre.leggauss(sub)
+    mass = np.zeros(n_z * n_phi)
+    dirs, wts = [], []
+    for iz in range(n_z):
+        z0, z1 = -1 + 2 * iz / n_z, -1 + 2 * (iz + 1) / n_z
+        for ip in range(n_phi):
+            p0, p1 = 2 * math.pi * ip / n_phi, 2 * math.pi * (ip + 1) / n_phi
+            Z, P = np.meshgrid((xs + 1) / 2 * (z1 - z0) + z0, (xs + 1) / 2 * (p1 - p0) + p0, indexing="ij")
+            s = np.sqrt(1 - Z * Z)
+            dirs.append(np.stack([s * np.cos(P), s * np.sin(P), Z], -1).reshape(-1, 3))
+            wts.append((np.outer(ws, ws) * (z1 - z0) / 2 * (p1 - p0) / 2).reshape(-1))
+    dirs, wts = np.concatenate(dirs), np.concatenate(wts)
+    pq = orc.pdf(K, ost.pi, ost.mu_x, ost.mu_w, ost.L, np.repeat(x[:1], len(dirs), 0),
+                 np.zeros(len(dirs), np.int32), dirs)
+    mass = (pq * wts).reshape(n_z * n_phi, -1).sum(1)
+    dd = d[v].astype(np.float64)
+    iz = np.minimum(((dd[:, 2] + 1) / 2 * n_z).astype(int), n_z - 1)
+    ph = np.mod(np.arctan2(dd[:, 1], dd[:, 0]), 2 * math.pi)
+    ip = np.minimum((ph / (2 * math.pi) * n_phi).astype(int), n_phi - 1)
+    counts = np.bincount(iz * n_phi + ip, minlength=n_z * n_phi)
+    obs = np.append(counts, (~v).sum()).astype(float)
+    exp = np.append(mass, 1 - mass.sum()) * N
+    keep = exp >= 5
+    obs = np.append(obs[keep], obs[~keep].sum())
+    exp = np.append(exp[keep], exp[~keep].sum())
+    if exp[-1] <= 0:
+        obs, exp = obs[:-1], exp[:-1]
+    chi2 = float(np.sum((obs - exp) ** 2 / exp))
+    assert stats.chi2.sf(chi2, obs.size - 1) > 1e-3, chi2
+
+
+def test_query_workload_16M_sampled_against_oracle():
+    """16M query positions uniform in the unit cube, 65,536 grid regions with
+    K = 16 mixtures, one Philox draw per query; 20,000 sampled queries are
+    recomputed by the oracle."""
+    K = 16
+    dims = (64, 32, 32)
+    ost = _mixtures(12, dims, K)
+    cfg = api.config(K)
+    st = gpu_state(ost, cfg)
+    Q = 16 * 2 ** 20
+    qx = syn.query_points(13, Q)
+    tq = torch.from_numpy(qx).cuda()
+    d, p, v = api.sample(cfg, st, tq, grid=api.Grid((0, 0, 0), (1, 1, 1), dims), seed=99)
+    torch.cuda.synchronize()
+    idx = np.sort(np.random.default_rng(14).choice(Q, 20000, replace=False))
+    u = orc.uniforms(99, Q)[idx]
+    reg = syn.grid_region(qx[idx], dims)
+    o = orc.sample(K, ost.pi, ost.mu_x, ost.mu_w, ost.L, qx[idx], reg, u)
+    dg = d[torch.from_numpy(idx).cuda()].cpu().numpy().astype(np.float64)
+    vg = v[torch.from_numpy(idx).cuda()].cpu().numpy()
+    pg = p[torch.from_numpy(idx).cuda()].cpu().numpy()
+    same = o["margin"] > 1e-5
+    assert np.array_equal(vg[same], o["valid"][same])
+    ok = same & (o["valid"] == 1)
+    assert _angle(dg[ok], o["dir"][ok]).max() < 1e-4
+    po = orc.pdf(K, ost.pi, ost.mu_x, ost.mu_w, ost.L, qx[idx], reg, dg)
+    vv = vg == 1
+    rel = np.abs(pg[vv] - po[vv]) / po[vv]
+    assert np.quantile(rel, 0.999) < PDF_RTOL
+    # discard rate (|nu| >= pi) is small, as the paper reports for its lobes
+    assert 1.0 - v.float().mean().item() < 0.01
