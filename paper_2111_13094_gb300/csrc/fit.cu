@@ -69,8 +69,10 @@ __global__ void __launch_bounds__(1024) k_build_chunks(WsHeader* ws, int64_t* ch
         ws->n_chunks = (int32_t)min(total, max_chunks);
         ws->queue = 0;
     }
+    __syncthreads();   // chunk_base is complete before any thread reads a neighbour's entry
     for (int64_t r = tid; r < R; r += 1024) {
-        const int64_t c0 = chunk_base[r], c1 = min(chunk_base[r + 1], max_chunks);
+        const int64_t c0 = chunk_base[r];
+        const int64_t c1 = min(r + 1 < R ? chunk_base[r + 1] : total, max_chunks);
         for (int64_t c = c0; c < c1; ++c) chunk_region[c] = (int32_t)r;
     }
 }
@@ -113,6 +115,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2)
     const int64_t* __restrict__ off = ws->desc.offsets;
     float* __restrict__ loglik = write_ll ? ws->desc.loglik : nullptr;
     const int n_chunks = ws->n_chunks;
+    const int64_t R = ws->desc.R;
 
     float prm[kE];
     int prev_r = -1;
@@ -122,6 +125,10 @@ __global__ void __launch_bounds__(kWarps * 32, 2)
         const int c = s_c;
         if (c >= n_chunks) break;
         const int r = chunk_region[c];
+        if (r < 0 || r >= R) {               // never happens for units built by k_build_chunks
+            __syncthreads();                 // (uniform branch) s_c is read before it is rewritten
+            continue;
+        }
         const int64_t o1 = off[r + 1];
         const int64_t start = off[r] + ((int64_t)c - chunk_base[r]) * chunk;
         const int64_t end = min(start + (int64_t)chunk, o1);
