@@ -345,6 +345,45 @@ sdmm_status sdmm_autotune(const sdmm_config *cfg, const sdmm_samples *s,
                           int32_t *chunk_out, int32_t *ctas_per_sm_out,
                           float *best_ms_out);
 
+/*
+ * sdmm_fit_regions_noalloc -- the fit of sdmm_fit_regions for callers that
+ * may not allocate device memory.  (The paper has no counterpart: this entry
+ * point only concerns where the library's scratch memory comes from.)
+ *
+ * Who needs it: code that must not call cudaMalloc or any allocating routine
+ * -- e.g. a renderer plugin whose host application owns and budgets all
+ * device memory, code running inside an allocator or driver callback where
+ * allocating would re-enter the allocator, or a real-time loop that must
+ * never block on an allocation.  Such callers can still pass the inputs and
+ * outputs they already own.
+ *
+ * Instead of a caller workspace, the call uses a fixed scratch array of
+ * SDMM_NOALLOC_SCRATCH_BYTES compiled into this library; every GPU on which
+ * the library is loaded holds that array until the process exits.  The
+ * function itself calls no cudaMalloc, cudaFree or allocating library
+ * routine.
+ *  - Limit: problems whose scratch (sdmm_fit_workspace_size for the same
+ *    cfg, R and N) exceeds SDMM_NOALLOC_SCRATCH_BYTES are rejected with
+ *    SDMM_ERR_WORKSPACE and a message giving both sizes; nothing is launched.
+ *    With K = 16 this allows roughly 12,000 work units, e.g. 4,096 regions with
+ *    up to about 30M samples, or one region with up to 3M samples.
+ *  - Set-up: the first call on each device looks up the device address of the
+ *    scratch array (cudaGetSymbolAddress, with that device current) and
+ *    caches it; make that first call before any stream capture.
+ *  - Sharing: all calls on a device share the one array, which keeps the
+ *    last call's contents.  Each call writes every scratch byte it reads
+ *    before reading it, so nothing needs clearing between calls, but calls
+ *    whose work overlaps on the GPU (other streams, other host threads)
+ *    race on the scratch and produce wrong results: serialise them.
+ * Arguments, results and per-region statuses are those of sdmm_fit_regions.
+ */
+#define SDMM_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
+sdmm_status sdmm_fit_regions_noalloc(const sdmm_config *cfg,
+                                     const sdmm_samples *s, int32_t iters,
+                                     const double *prior_scale,
+                                     sdmm_state *st, float *loglik_out,
+                                     sdmm_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

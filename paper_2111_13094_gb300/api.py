@@ -16,7 +16,7 @@ from . import _lib
 from ._lib import check
 
 __all__ = ["config", "MixtureState", "SampleBatch", "Grid", "workspace", "workspace_bytes",
-           "init_regions", "fit_regions", "prepare", "condition", "sample", "pdf", "objective",
+           "init_regions", "fit_regions", "fit_regions_noalloc", "prepare", "condition", "sample", "pdf", "objective",
            "objective_backward", "FitPlan", "autotune", "MapObjective", "map_objective"]
 
 ETA_ROBBINS_MONRO, ETA_ONE = 0, 1
@@ -146,6 +146,18 @@ def fit_regions(cfg, batch: SampleBatch, iters: int, state: MixtureState, ws: to
     check(_lib.load().sdmm_fit_regions(ctypes.byref(cfg), ctypes.byref(sm), int(iters), _ptr(prior_scale),
                                        ctypes.byref(st), _ptr(loglik), _ptr(ws), ws.numel(),
                                        _stream(stream)), "sdmm_fit_regions")
+
+
+def fit_regions_noalloc(cfg, batch: SampleBatch, iters: int, state: MixtureState, prior_scale=None,
+                        loglik=None, stream=None):
+    """fit_regions without a workspace, for callers that may not allocate
+    device memory: the library's fixed scratch array is used instead (size
+    limit and sharing rules in include/sdmm.h, sdmm_fit_regions_noalloc)."""
+    sm = batch.c()
+    st = state.c()
+    check(_lib.load().sdmm_fit_regions_noalloc(ctypes.byref(cfg), ctypes.byref(sm), int(iters),
+                                               _ptr(prior_scale), ctypes.byref(st), _ptr(loglik),
+                                               _stream(stream)), "sdmm_fit_regions_noalloc")
 
 
 def prepare(cfg, state: MixtureState, logits=None, delta=None, stream=None):

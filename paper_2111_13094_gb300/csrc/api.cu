@@ -4,6 +4,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -197,6 +198,38 @@ sdmm_status enqueue_fit(const FitLaunch& f, cudaStream_t s, std::vector<cudaEven
 }  // namespace
 
 // ===========================================================================
+// Fixed scratch of sdmm_fit_regions_noalloc, for callers that may not
+// allocate device memory (see include/sdmm.h).  It is part of this library's
+// device image, so every GPU that loads the library holds it until exit.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[SDMM_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the fixed scratch on the current device.  In host code the
+// array's name is only a host-side stand-in, so the address is looked up once
+// per device, with that device current, and cached.
+sdmm_status noalloc_scratch(void** out) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices) return fail(SDMM_ERR_UNSUPPORTED, "device ordinal %d", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (g_noalloc_ptr[dev] == nullptr) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress of the fixed scratch");
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return SDMM_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 void sdmm_config_default(sdmm_config* cfg, int32_t K) {
@@ -533,6 +566,33 @@ sdmm_status sdmm_fit_plan_destroy(sdmm_fit_plan* p) {
         if (ev) cudaEventDestroy(ev);
     delete p;
     return SDMM_OK;
+}
+
+// ---------------------------------------------------------------- fixed scratch
+sdmm_status sdmm_fit_regions_noalloc(const sdmm_config* cfg, const sdmm_samples* s, int32_t iters,
+                                     const double* prior_scale, sdmm_state* st, float* loglik_out,
+                                     sdmm_stream stream) {
+    sdmm_status e;
+    if ((e = check_config(cfg)) || (e = check_samples(s)) || (e = check_state(st, true))) return e;
+    if (iters < 1) return fail(SDMM_ERR_INVALID_ARG, "iters = %d must be >= 1", iters);
+    if (cfg->prior_scale_mode == SDMM_PRIOR_SCALE_ARRAY && !prior_scale)
+        return fail(SDMM_ERR_INVALID_ARG, "prior_scale_mode ARRAY needs prior_scale");
+    if (cfg->precision != SDMM_PREC_FP32)
+        return fail(SDMM_ERR_UNSUPPORTED, "precision %d is not available in sdmm_fit_regions_noalloc",
+                    cfg->precision);
+    const Layout L = layout(cfg, s->R, s->N, choose_chunk(cfg, s->N));
+    if (L.total > (size_t)SDMM_NOALLOC_SCRATCH_BYTES)
+        return fail(SDMM_ERR_WORKSPACE,
+                    "sdmm_fit_regions_noalloc: this problem (R = %lld, N = %lld, K = %d) needs %zu bytes "
+                    "of scratch but the fixed scratch holds %zu; use sdmm_fit_regions with a workspace",
+                    (long long)s->R, (long long)s->N, cfg->K, L.total, (size_t)SDMM_NOALLOC_SCRATCH_BYTES);
+    void* ws = nullptr;
+    if ((e = noalloc_scratch(&ws))) return e;
+    const int nsm = sm_count();
+    if (nsm <= 0) return fail(SDMM_ERR_CUDA, "no CUDA device");
+    FitLaunch f{*cfg, *st, L, ws_ptrs(ws, L), s->R, iters, nsm * default_ctas(cfg), loglik_out != nullptr};
+    SDMM_CUDA(launch_set_desc(stream, f.w.hdr, make_desc(s, prior_scale, loglik_out)), "set_desc");
+    return enqueue_fit(f, stream, nullptr);
 }
 
 // ---------------------------------------------------------------- autotuner
