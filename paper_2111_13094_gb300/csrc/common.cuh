@@ -99,6 +99,27 @@ __device__ inline void chart_jacobian_f64(const double mu_old[3], const double n
     }
 }
 
+// atan2(s, c) for s >= 0, in [0, pi].  Octant reduction to t = min/max in
+// [0, 1] and atan(t) = t P(t^2), P of degree 7 with coefficients fitted by
+// csrc/fit_atan_poly.py (max relative error 2.2e-7 in FP32).
+__device__ __forceinline__ float atan2_pos(float s, float c) {
+    const float ac = fabsf(c);
+    const float mn = fminf(s, ac), mx = fmaxf(s, ac);
+    const float t = mx > 0.f ? __fdividef(mn, mx) : 0.f;
+    const float u = t * t;
+    float p = -0.00482251868f;
+    p = fmaf(p, u, 0.0247340072f);
+    p = fmaf(p, u, -0.0602030531f);
+    p = fmaf(p, u, 0.0996846780f);
+    p = fmaf(p, u, -0.140413254f);
+    p = fmaf(p, u, 0.199742138f);
+    p = fmaf(p, u, -0.333323926f);
+    p = fmaf(p, u, 1.0f) * t;
+    if (s > ac) p = 1.57079637f - p;
+    if (c < 0.f) p = 3.14159274f - p;
+    return p;
+}
+
 // Cholesky of a packed symmetric 5x5; false if not positive definite.
 __device__ inline bool cholesky5_f64(const double S[15], double L[15]) {
     for (int j = 0; j < 5; ++j) {

@@ -118,6 +118,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2)
     const int64_t R = ws->desc.R;
 
     float prm[kE];
+    float lmax = 0.f;
     int prev_r = -1;
     for (;;) {
         if (threadIdx.x == 0) s_c = atomicAdd(&ws->queue, 1);
@@ -150,6 +151,11 @@ __global__ void __launch_bounds__(kWarps * 32, 2)
                 prm[11] = 1.f;
                 prm[27] = -INFINITY;
             }
+            // upper bound of every component's log-density in this region:
+            // l_k = c5_k - q/2 <= c5_k (tangent density), so exp(l - lmax) <= 1
+            lmax = prm[27];
+#pragma unroll
+            for (int o = KP / 2; o > 0; o >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
         }
         float acc[kStat];
 #pragma unroll
@@ -167,6 +173,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2)
             *reinterpret_cast<float4*>(&sbuf[warp][lane][4]) = b;
             __syncwarp();
             const int n = (int)min((int64_t)32, end - g);
+#pragma unroll 2
             for (int t = 0; t < n; t += SPI) {
                 const int j = t + h;
                 const float4 sa = *reinterpret_cast<const float4*>(&sbuf[warp][j][0]);
@@ -177,7 +184,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2)
                 const float cz = prm[9] * sb.x + prm[10] * sb.y + prm[11] * sb.z;
                 const float s2 = u * u + v * v;
                 const float rs = rsqrtf(s2);
-                const float th = atan2f(s2 * rs, cz);
+                const float th = atan2_pos(s2 * rs, cz);
                 const bool off_centre = s2 > 0.f;
                 const float gg = off_centre ? th * rs : 1.f;
                 float d[5];
@@ -197,23 +204,30 @@ __global__ void __launch_bounds__(kWarps * 32, 2)
                 float l = prm[27] - 0.5f * q;
                 if (density) l += __logf(gg);
                 if (!off_centre && cz < 0.f) l = -INFINITY;   // cut locus: undefined chart
-                // log-sum-exp over the KP component lanes of this sample
-                float mx = l;
-#pragma unroll
-                for (int o = KP / 2; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-                const float e = (mx == -INFINITY) ? 0.f : __expf(l - mx);
+                // log-sum-exp over the KP component lanes of this sample, shifted
+                // by the region bound; the exact per-sample maximum is used only
+                // when that underflows (or when the bound does not hold)
+                float ref = lmax;
+                float e = __expf(l - ref);
                 float se = e;
 #pragma unroll
                 for (int o = KP / 2; o > 0; o >>= 1) se += __shfl_xor_sync(0xffffffffu, se, o);
+                if (__any_sync(0xffffffffu, !(se > 0.f) || se > 1e30f || density)) {
+                    ref = l;
+#pragma unroll
+                    for (int o = KP / 2; o > 0; o >>= 1) ref = fmaxf(ref, __shfl_xor_sync(0xffffffffu, ref, o));
+                    e = (ref == -INFINITY) ? 0.f : __expf(l - ref);
+                    se = e;
+#pragma unroll
+                    for (int o = KP / 2; o > 0; o >>= 1) se += __shfl_xor_sync(0xffffffffu, se, o);
+                }
                 const float rr = (se > 0.f) ? __fdividef(e, se) : 0.f;
                 const float wt = sa.w;
                 const float wr = wt * rr;
-                if (k == 0) {
-                    const float li = (se > 0.f) ? mx + __logf(se) : -INFINITY;
-                    wsum += wt;
-                    if (wt > 0.f) wll += wt * li;
-                    if (loglik != nullptr && j < n) loglik[g + j] = li;
-                }
+                const float li = (se > 0.f) ? ref + __logf(se) : -INFINITY;
+                wsum += wt;
+                wll += (wt > 0.f) ? wt * li : 0.f;
+                if (loglik != nullptr && k == 0 && j < n) loglik[g + j] = li;
                 float x[5];
                 if (MODE == MODE_FIT) {
 #pragma unroll

@@ -137,6 +137,7 @@ __global__ void __launch_bounds__(256)
             const float lw = P[30] - 0.5f * (z0 * z0 + z1 * z1 + z2 * z2);
             const float m0 = P[18] * z0 + P[19] * z1 + P[20] * z2;   // C^T z
             const float m1 = P[21] * z0 + P[22] * z1 + P[23] * z2;
+            // normalise pi'_k over the KP component lanes (log-sum-exp)
             float mx = lw;
 #pragma unroll
             for (int o = KP / 2; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(FULL, mx, o));
@@ -209,7 +210,7 @@ __global__ void __launch_bounds__(256)
             const float cz = P[9] * w0 + P[10] * w1 + P[11] * w2;
             const float s2v = u * u + v * v;
             const float rs = rsqrtf(s2v);
-            const float th = atan2f(s2v * rs, cz);
+            const float th = atan2_pos(s2v * rs, cz);
             const bool off_centre = s2v > 0.f;
             const float gg = off_centre ? th * rs : 1.f;      // theta / sin(theta) = 1/sinc
             const float d0 = gg * u - m0, d1 = gg * v - m1;
