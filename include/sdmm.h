@@ -346,6 +346,24 @@ sdmm_status sdmm_autotune(const sdmm_config *cfg, const sdmm_samples *s,
                           float *best_ms_out);
 
 /*
+ * Self-test of the tensor-core contraction path: D = A B^T for one tile with
+ * A (128 x Kd) and B (N x Kd) given in FP32 (device, row-major), rounded to
+ * the operand format `kind` (0: BF16, tcgen05.mma kind::f16; 1: TF32,
+ * kind::tf32), staged in shared memory in the same K-major layout and
+ * multiplied with the same descriptors, MMA issue, commit and TMEM read-out
+ * as the contraction-form E-step; D (device FP32, 128 x N) accumulates in
+ * FP32.  N: multiple of 16 in [16, 256]; Kd: multiple of 16 (BF16) or 8
+ * (TF32), at most 64.  `variant` 0 selects the library's descriptor offsets
+ * (leading-dimension offset along K); 1 swaps the two offsets (diagnostics).
+ * status (device int32): set to 1 if the MMA did not complete within 2 s.
+ * (The paper has no counterpart: this checks the hardware path.)
+ */
+sdmm_status sdmm_tc_selftest(int32_t kind, int32_t N, int32_t Kd,
+                             const float *A, const float *B, float *D,
+                             int32_t variant, int32_t *status,
+                             sdmm_stream stream);
+
+/*
  * sdmm_fit_regions_noalloc -- the fit of sdmm_fit_regions for callers that
  * may not allocate device memory.  (The paper has no counterpart: this entry
  * point only concerns where the library's scratch memory comes from.)

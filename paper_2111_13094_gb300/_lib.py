@@ -23,7 +23,7 @@ SYMBOLS = ["sdmm_config_default", "sdmm_last_error", "sdmm_version", "sdmm_fit_w
            "sdmm_sample", "sdmm_pdf", "sdmm_objective", "sdmm_objective_backward",
            "sdmm_fit_plan_create", "sdmm_fit_plan_run", "sdmm_fit_plan_enable_timing",
            "sdmm_fit_plan_timing", "sdmm_fit_plan_destroy", "sdmm_autotune",
-           "sdmm_fit_regions_noalloc"]
+           "sdmm_fit_regions_noalloc", "sdmm_tc_selftest"]
 
 SDMM_NOALLOC_SCRATCH_BYTES = 16 * 1024 * 1024
 
@@ -89,6 +89,7 @@ def _declare(L):
         "sdmm_autotune": [_PC, _PSm, _PS, _P, ctypes.c_size_t, _P, ctypes.POINTER(_I32),
                           ctypes.POINTER(_I32), ctypes.POINTER(ctypes.c_float)],
         "sdmm_fit_regions_noalloc": [_PC, _PSm, _I32, _P, _PS, _P, _P],
+        "sdmm_tc_selftest": [_I32, _I32, _I32, _P, _P, _P, _I32, _P, _P],
     }
     for name, args in sig.items():
         f = getattr(L, name)

@@ -568,6 +568,19 @@ sdmm_status sdmm_fit_plan_destroy(sdmm_fit_plan* p) {
     return SDMM_OK;
 }
 
+// ---------------------------------------------------------------- tensor-core self-test
+sdmm_status sdmm_tc_selftest(int32_t kind, int32_t N, int32_t Kd, const float* A, const float* B, float* D,
+                             int32_t variant, int32_t* status, sdmm_stream stream) {
+    if (kind != 0 && kind != 1) return fail(SDMM_ERR_INVALID_ARG, "kind %d: 0 (BF16) or 1 (TF32)", kind);
+    if (N < 16 || N > 256 || N % 16) return fail(SDMM_ERR_INVALID_ARG, "N = %d: multiple of 16 in [16, 256]", N);
+    const int kq = kind == 0 ? 16 : 8;
+    if (Kd < kq || Kd > 64 || Kd % kq) return fail(SDMM_ERR_INVALID_ARG, "Kd = %d: multiple of %d, at most 64", Kd, kq);
+    if (variant != 0 && variant != 1) return fail(SDMM_ERR_INVALID_ARG, "variant %d", variant);
+    if (!A || !B || !D || !status) return fail(SDMM_ERR_INVALID_ARG, "NULL pointer");
+    SDMM_CUDA(launch_tc_selftest(stream, kind, N, Kd, A, B, D, variant, status), "tc_selftest");
+    return SDMM_OK;
+}
+
 // ---------------------------------------------------------------- fixed scratch
 sdmm_status sdmm_fit_regions_noalloc(const sdmm_config* cfg, const sdmm_samples* s, int32_t iters,
                                      const double* prior_scale, sdmm_state* st, float* loglik_out,

@@ -1,0 +1,50 @@
+"""The tensor-core helpers (shared-memory layout, descriptors, tcgen05.mma,
+commit, TMEM read-out) against an FP64 product of the same rounded
+operands, for BF16 (kind::f16) and TF32 (kind::tf32) tiles."""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2111_13094_gb300 import _lib
+
+pytestmark = pytest.mark.gpu
+
+
+def _round_tf32(x):
+    """Round FP32 to TF32 (10 explicit mantissa bits), nearest, ties away."""
+    b = np.asarray(x, np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + 0x1000) & 0xFFFFE000
+    return b.astype(np.uint32).view(np.float32)
+
+
+def _run(kind, N, Kd, variant, seed=0):
+    rng = np.random.default_rng(seed)
+    A = rng.normal(size=(128, Kd)).astype(np.float32)
+    B = rng.normal(size=(N, Kd)).astype(np.float32)
+    tA, tB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    D = torch.full((128, N), float("nan"), device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    lib = _lib.load()
+    s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    code = lib.sdmm_tc_selftest(kind, N, Kd, ctypes.c_void_p(tA.data_ptr()), ctypes.c_void_p(tB.data_ptr()),
+                                ctypes.c_void_p(D.data_ptr()), variant, ctypes.c_void_p(st.data_ptr()), s)
+    assert code == 0, lib.sdmm_last_error()
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0, "MMA did not complete"
+    if kind == 0:
+        Ar = tA.bfloat16().double().cpu().numpy()
+        Br = tB.bfloat16().double().cpu().numpy()
+    else:
+        Ar, Br = _round_tf32(A).astype(np.float64), _round_tf32(B).astype(np.float64)
+    ref = Ar @ Br.T
+    return D.cpu().numpy().astype(np.float64), ref
+
+
+@pytest.mark.parametrize("kind,Kd", [(0, 16), (0, 32), (0, 64), (1, 8), (1, 32)])
+@pytest.mark.parametrize("N", [16, 96, 256])
+def test_tc_tile_matches_fp64_product(kind, N, Kd):
+    D, ref = _run(kind, N, Kd, variant=0)
+    err = np.abs(D - ref).max()
+    assert err < 1e-4 * max(1.0, np.abs(ref).max()), err
