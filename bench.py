@@ -33,7 +33,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "EM sample-iterations/s and guided queries/s vs plain FP32 at matched log-lik"
 UNIT = "sample-iterations/s"
-R_REGIONS, K_COMP, ROUNDS = 4096, 16, 4
+K_COMP, ROUNDS = 16, 4
 Q_DIMS, Q_COUNT = (64, 32, 32), 16 * 2 ** 20
 # algorithmic FP32 work of the E-step + statistics per (sample, component):
 # log map 23, Mahalanobis 39, log-sum-exp and responsibility 6, statistics 46
@@ -106,7 +106,7 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------
-def cpu_baseline(budget_s=15.0, seed=1):
+def cpu_baseline(budget_s=15.0, seed=1, R_REGIONS=4096):
     """The FP64 oracle, as it stands, on a bounded sample of the fit workload
     (whole regions in seed order until the budget), single-threaded."""
     import oracle as orc
@@ -160,6 +160,41 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------------------
+def measure_e2e(args, batches, off, st, plan, stream, e0, e1, world, N):
+    """Same step through the public API with host buffers: each round's batch
+    is copied from pinned host memory into one device buffer, the plan runs,
+    and the fitted parameters are read back."""
+    import torch
+
+    from paper_2111_13094_gb300 import api
+    host = [b.samples.cpu().pin_memory() for b in batches]
+    dbuf = torch.empty_like(batches[0].samples)
+    dbatch = api.SampleBatch(dbuf, off)
+    params = (st.pi, st.mu_x, st.mu_w, st.L)
+    out_host = [torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in params]
+
+    def e2e_step():
+        for hs in host:
+            dbuf.copy_(hs, non_blocking=True)
+            plan.run(dbatch)
+        for o, t in zip(out_host, params):
+            o.copy_(t, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    n = max(2, args.steps // 10)
+    e0.record(stream)
+    for _ in range(n):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / n
+    h2d = sum(hs.numel() * hs.element_size() for hs in host)
+    d2h = sum(o.numel() * o.element_size() for o in out_host)
+    return {"value": world * ROUNDS * N / (ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "ms_per_step": ms}
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -178,6 +213,7 @@ def run_gpu(args):
     seed = 1 + 1000 * rank                     # every rank fits its own regions (weak scaling)
 
     # ---- inputs resident in HBM
+    R_REGIONS = args.regions
     truth = syn.batched_truth(seed, R_REGIONS, K=K_COMP)
     counts = syn.region_counts(seed, R_REGIONS)
     N = int(counts.sum())
@@ -185,7 +221,9 @@ def run_gpu(args):
     batches = [api.SampleBatch(syn.draw_torch(seed * 100 + r, truth, counts, device=dev), off)
                for r in range(ROUNDS)]
     _, h, _ = syn.region_grid(R_REGIONS)
-    cfg = api.config(K_COMP)
+    prec = {"fp32": api.PREC_FP32, "3xbf16": api.PREC_TC_3XBF16, "tf32": api.PREC_TC_TF32,
+            "3xtf32": api.PREC_TC_3XTF32}[args.precision]
+    cfg = api.config(K_COMP, precision=prec)
     st = api.MixtureState(R_REGIONS, K_COMP, device=dev)
     api.init_regions(cfg, batches[0], torch.from_numpy(h.astype(np.float64)).to(dev),
                      torch.from_numpy(syn.init_uniforms(seed, R_REGIONS, 2)).to(dev), st)
@@ -219,7 +257,9 @@ def run_gpu(args):
         ms = float(t.item())
         dist.barrier()
     kern = plan.timing()
-    status_ok = bool((st.status == 0).all().item())
+    codes, cnt = torch.unique(st.status, return_counts=True)
+    status_counts = {int(c): int(n) for c, n in zip(codes.cpu(), cnt.cpu())}
+    status_ok = status_counts.get(0, 0) == R_REGIONS
     value = world * args.steps * ROUNDS * N / (ms * 1e-3)
 
     # ---- E-step kernel roofline (FP32 ALU bound)
@@ -230,7 +270,8 @@ def run_gpu(args):
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     peak = n_sm * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": None, "kernel": "k_accumulate<16,FIT>",
+            "frac": achieved / peak, "traffic": None,
+            "kernel": "k_accumulate<16,FIT>" if prec == api.PREC_FP32 else f"k_tc_estep<16,{args.precision}>",
             "kernel_ms": kms, "launches_timed": len(kern),
             "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x 2 flop x {peaks.get('sm_max_mhz', 2070.0):.0f} MHz "
                           f"({src} max clock)",
@@ -238,31 +279,9 @@ def run_gpu(args):
             "hbm_frac": N * BYTES_PER_SAMPLE / (kms * 1e-3) / 1e9 / peaks.get("hbm_gbs", 6800.0)}
 
     # ---- end to end through the public API with host buffers
-    host = [b.samples.cpu().pin_memory() for b in batches]
-    dbuf = torch.empty_like(batches[0].samples)
-    dbatch = api.SampleBatch(dbuf, off)
-    out_host = [torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in (st.pi, st.mu_x, st.mu_w, st.L)]
-
-    def e2e_step():
-        for hs in host:
-            dbuf.copy_(hs, non_blocking=True)
-            plan.run(dbatch)
-        for o, t in zip(out_host, (st.pi, st.mu_x, st.mu_w, st.L)):
-            o.copy_(t, non_blocking=True)
-
-    e2e_step()
-    torch.cuda.synchronize()
-    n_e2e = max(2, args.steps // 10)
-    e0.record(stream)
-    for _ in range(n_e2e):
-        e2e_step()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / n_e2e
-    h2d = sum(hs.numel() * hs.element_size() for hs in host)
-    d2h = sum(o.numel() * o.element_size() for o in out_host)
-    plan.close()
-    del host, dbuf
+    e2e = None
+    if not args.no_e2e:
+        e2e = measure_e2e(args, batches, off, st, plan, stream, e0, e1, world, N)
 
     # ---- query workload: 16M guided queries over 65,536 grid regions
     qres = None
@@ -311,15 +330,15 @@ def run_gpu(args):
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic (seeded; shapes of the paper's leaves: K=16, log-uniform leaf sizes)",
-                "config": {"workload": "batched stepwise MAP-EM fit: 4096 regions x K=16, sample counts "
+                "config": {"workload": f"batched stepwise MAP-EM fit: {R_REGIONS} regions x K=16, sample counts "
                                        "log-uniform in [256, 65536], 4 Robbins-Monro rounds per step with a "
                                        "fresh batch each, CUDA-graph replay per round",
                            "regions": R_REGIONS, "K": K_COMP, "rounds_per_step": ROUNDS,
                            "samples_per_round": N, "per_rank": True,
                            "l2": "inputs larger than L2 (about 1.35 GB per round)",
-                           "all_regions_ok": status_ok},
-                "clocks": ck, "e2e": {"value": world * ROUNDS * N / (e2e_ms * 1e-3), "unit": UNIT,
-                                      "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                           "all_regions_ok": status_ok, "status_counts": status_counts,
+                           "precision": args.precision},
+                "clocks": ck, "e2e": e2e,
                 "gpu_launches": args.steps * ROUNDS * 4,
                 "roofline": roof, "cpu_baseline": cpu, "queries": qres}
         print(json.dumps(line), flush=True)
@@ -336,6 +355,10 @@ def main():
     ap.add_argument("--no-queries", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--regions", type=int, default=4096, help="regions of the fit workload")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "3xbf16", "tf32", "3xtf32"],
+                    help="E-step arithmetic: FP32 SIMT or a tensor-core contraction form")
+    ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)        # at least 3 untimed steps, reported as run
     if args.impl == "reference":

@@ -66,13 +66,16 @@ enum {
                                     failing step left the region unchanged      */
     SDMM_REGION_NONFINITE = 3,   /* non-finite weights or statistics            */
     SDMM_REGION_ZERO_WEIGHT = 4, /* all sample weights are zero                 */
-    SDMM_REGION_BAD_OFFSETS = 5  /* offsets decrease or exceed N                */
+    SDMM_REGION_BAD_OFFSETS = 5, /* offsets decrease or exceed N                */
+    SDMM_REGION_DEVICE_TIMEOUT = 6 /* a tensor-core wait of the E-step timed out;
+                                      no region was updated in that step        */
 };
 
 enum { SDMM_ETA_ROBBINS_MONRO = 0, SDMM_ETA_ONE = 1 };
 enum { SDMM_DENSITY_TANGENT = 0, SDMM_DENSITY_SOLID_ANGLE = 1 };
 enum { SDMM_PRIOR_SCALE_SEEN = 0, SDMM_PRIOR_SCALE_ARRAY = 1 };
-enum { SDMM_PREC_FP32 = 0, SDMM_PREC_TC_3XBF16 = 1, SDMM_PREC_TC_TF32 = 2 };
+enum { SDMM_PREC_FP32 = 0, SDMM_PREC_TC_3XBF16 = 1, SDMM_PREC_TC_TF32 = 2,
+       SDMM_PREC_TC_3XTF32 = 3 };
 
 #define SDMM_MAX_K 32
 /* Floats per component in the derived FP32 tables (see sdmm_state). */
@@ -91,7 +94,14 @@ typedef struct sdmm_config {
                                   computation) or the solid-angle density     */
     int32_t prior_scale_mode;  /* SDMM_PRIOR_SCALE_*: beta = 1/n_seen, or the
                                   caller's per-region array                   */
-    int32_t precision;         /* SDMM_PREC_*: E-step arithmetic              */
+    int32_t precision;         /* SDMM_PREC_*: E-step arithmetic.  FP32: SIMT
+                                  kernel.  TC_*: contraction form on the
+                                  tensor cores (K = 16 or 32, tangent
+                                  density): per-sample features times a
+                                  per-region coefficient matrix in split
+                                  3xBF16, TF32 or split 3xTF32, statistics
+                                  as a second product in split 3xBF16, FP32
+                                  accumulation in TMEM                        */
     int32_t chunk;             /* samples per work unit of the fit kernels;
                                   0 = library heuristic; else a multiple of
                                   256 in [256, 65536]                        */
@@ -353,8 +363,10 @@ sdmm_status sdmm_autotune(const sdmm_config *cfg, const sdmm_samples *s,
  * multiplied with the same descriptors, MMA issue, commit and TMEM read-out
  * as the contraction-form E-step; D (device FP32, 128 x N) accumulates in
  * FP32.  N: multiple of 16 in [16, 256]; Kd: multiple of 16 (BF16) or 8
- * (TF32), at most 64.  `variant` 0 selects the library's descriptor offsets
- * (leading-dimension offset along K); 1 swaps the two offsets (diagnostics).
+ * (TF32), at most 64.  `variant` bits: 1 swaps the two descriptor offsets of
+ * K-major operands (diagnostics), 2 / 4 stage A / B MN-major (BF16 only),
+ * 8 swaps the offsets of MN-major operands (diagnostics).  Variants 0 and
+ * 4 are the layouts the contraction-form E-step uses.
  * status (device int32): set to 1 if the MMA did not complete within 2 s.
  * (The paper has no counterpart: this checks the hardware path.)
  */

@@ -61,9 +61,12 @@ sdmm_status check_config(const sdmm_config* cfg) {
         return fail(SDMM_ERR_INVALID_ARG, "estep_density %d", cfg->estep_density);
     if (cfg->prior_scale_mode != SDMM_PRIOR_SCALE_SEEN && cfg->prior_scale_mode != SDMM_PRIOR_SCALE_ARRAY)
         return fail(SDMM_ERR_INVALID_ARG, "prior_scale_mode %d", cfg->prior_scale_mode);
-    if (cfg->precision != SDMM_PREC_FP32 && cfg->precision != SDMM_PREC_TC_3XBF16 &&
-        cfg->precision != SDMM_PREC_TC_TF32)
+    if (cfg->precision < SDMM_PREC_FP32 || cfg->precision > SDMM_PREC_TC_3XTF32)
         return fail(SDMM_ERR_INVALID_ARG, "precision %d", cfg->precision);
+    if (cfg->precision != SDMM_PREC_FP32 && !(cfg->K == 16 || cfg->K == 32))
+        return fail(SDMM_ERR_UNSUPPORTED, "tensor-core precision needs K = 16 or 32 (K = %d)", cfg->K);
+    if (cfg->precision != SDMM_PREC_FP32 && cfg->estep_density != SDMM_DENSITY_TANGENT)
+        return fail(SDMM_ERR_UNSUPPORTED, "tensor-core precision supports the tangent density only");
     if (cfg->chunk != 0 && (cfg->chunk < 256 || cfg->chunk > 65536 || cfg->chunk % 256 != 0))
         return fail(SDMM_ERR_INVALID_ARG, "chunk %d: 0 or a multiple of 256 in [256, 65536]", cfg->chunk);
     if (cfg->ctas_per_sm < 0 || cfg->ctas_per_sm > 4)
@@ -110,15 +113,18 @@ int choose_chunk(const sdmm_config* cfg, int64_t N) {
 }
 
 struct Layout {
-    size_t header, chunk_base, chunk_region, partial, total;
+    size_t header, chunk_base, chunk_region, partial, ctab, xref, total;
     int chunk, ps;
     int64_t max_chunks;
 };
 
+bool tensor_core(const sdmm_config* cfg) { return cfg->precision != SDMM_PREC_FP32; }
+
 Layout layout(const sdmm_config* cfg, int64_t R, int64_t N, int chunk) {
     Layout L{};
     L.chunk = chunk;
-    L.ps = partial_stride(cfg->K);
+    // tensor-core partials hold 3K feature-space rows of 28, the SIMT ones 21K statistics
+    L.ps = tensor_core(cfg) ? ((3 * cfg->K * kFeat + 2) + 3) & ~3 : partial_stride(cfg->K);
     L.max_chunks = (N + chunk - 1) / chunk + R;
     size_t o = 0;
     L.header = o;
@@ -129,6 +135,13 @@ Layout layout(const sdmm_config* cfg, int64_t R, int64_t N, int chunk) {
     o = align_up(o + sizeof(int32_t) * (size_t)L.max_chunks);
     L.partial = o;
     o = align_up(o + sizeof(float) * (size_t)L.max_chunks * L.ps);
+    L.ctab = L.xref = o;
+    if (tensor_core(cfg)) {
+        L.ctab = o;
+        o = align_up(o + sizeof(float) * (size_t)R * cfg->K * 6 * 32);
+        L.xref = o;
+        o = align_up(o + sizeof(float) * (size_t)R * 4);
+    }
     L.total = o;
     return L;
 }
@@ -138,12 +151,15 @@ struct WsPtrs {
     int64_t* cb;
     int32_t* cr;
     float* partial;
+    float* ctab;
+    float* xref;
 };
 
 WsPtrs ws_ptrs(void* ws, const Layout& L) {
     char* b = static_cast<char*>(ws);
     return WsPtrs{reinterpret_cast<WsHeader*>(b + L.header), reinterpret_cast<int64_t*>(b + L.chunk_base),
-                  reinterpret_cast<int32_t*>(b + L.chunk_region), reinterpret_cast<float*>(b + L.partial)};
+                  reinterpret_cast<int32_t*>(b + L.chunk_region), reinterpret_cast<float*>(b + L.partial),
+                  reinterpret_cast<float*>(b + L.ctab), reinterpret_cast<float*>(b + L.xref)};
 }
 
 sdmm_status check_ws(void* ws, size_t bytes, const Layout& L) {
@@ -180,16 +196,27 @@ struct FitLaunch {
 
 sdmm_status enqueue_fit(const FitLaunch& f, cudaStream_t s, std::vector<cudaEvent_t>* evs) {
     const int KP = pow2_ceil(f.cfg.K);
+    const bool tcore = tensor_core(&f.cfg);
     SDMM_CUDA(launch_build_chunks(s, f.w.hdr, f.w.cb, f.w.cr, f.L.chunk, f.cfg.min_samples, f.L.max_chunks),
               "build_chunks");
     for (int it = 0; it < f.iters; ++it) {
+        const int wll = f.want_ll && it == f.iters - 1;
+        if (tcore)
+            SDMM_CUDA(launch_tc_prepare(s, f.cfg.K, f.R, f.st, f.w.ctab, f.w.xref), "tc_prepare");
         if (evs) SDMM_CUDA(cudaEventRecordWithFlags((*evs)[2 * it], s, cudaEventRecordExternal), "event");
-        SDMM_CUDA(launch_accumulate(s, MODE_FIT, KP, f.grid, f.w.hdr, f.w.cb, f.w.cr, f.st.etab, f.cfg.K,
-                                    f.L.chunk, f.cfg.estep_density, f.w.partial, f.L.ps,
-                                    f.want_ll && it == f.iters - 1),
-                  "accumulate");
+        if (tcore) {
+            const int grid = std::max(1, sm_count()) * tc_ctas_per_sm(f.cfg.K, f.cfg.precision);
+            SDMM_CUDA(launch_tc_estep(s, f.cfg.K, f.cfg.precision, grid, f.w.hdr, f.w.cb, f.w.cr, f.w.ctab,
+                                      f.w.xref, f.L.chunk, f.w.partial, f.L.ps, wll),
+                      "tc_estep");
+        } else {
+            SDMM_CUDA(launch_accumulate(s, MODE_FIT, KP, f.grid, f.w.hdr, f.w.cb, f.w.cr, f.st.etab, f.cfg.K,
+                                        f.L.chunk, f.cfg.estep_density, f.w.partial, f.L.ps, wll),
+                      "accumulate");
+        }
         if (evs) SDMM_CUDA(cudaEventRecordWithFlags((*evs)[2 * it + 1], s, cudaEventRecordExternal), "event");
-        SDMM_CUDA(launch_reduce_mstep(s, f.R, f.w.hdr, f.w.cb, f.w.partial, f.L.ps, f.cfg, f.st, it),
+        SDMM_CUDA(launch_reduce_mstep(s, f.R, f.w.hdr, f.w.cb, f.w.partial, f.L.ps, f.cfg, f.st, it,
+                                      tcore ? f.w.xref : nullptr),
                   "reduce_mstep");
     }
     return SDMM_OK;
@@ -282,8 +309,6 @@ sdmm_status sdmm_fit_regions(const sdmm_config* cfg, const sdmm_samples* s, int3
     if (iters < 1) return fail(SDMM_ERR_INVALID_ARG, "iters = %d must be >= 1", iters);
     if (cfg->prior_scale_mode == SDMM_PRIOR_SCALE_ARRAY && !prior_scale)
         return fail(SDMM_ERR_INVALID_ARG, "prior_scale_mode ARRAY needs prior_scale");
-    if (cfg->precision != SDMM_PREC_FP32)
-        return fail(SDMM_ERR_UNSUPPORTED, "precision %d is not available in sdmm_fit_regions", cfg->precision);
     const Layout L = layout(cfg, s->R, s->N, choose_chunk(cfg, s->N));
     if ((e = check_ws(workspace, ws_bytes, L))) return e;
     const int nsm = sm_count();
@@ -448,8 +473,6 @@ sdmm_status sdmm_fit_plan_create(const sdmm_config* cfg, int64_t R, int64_t N_ma
     if (!plan_out) return fail(SDMM_ERR_INVALID_ARG, "plan_out is NULL");
     *plan_out = nullptr;
     if (R < 1 || N_max < 0 || iters < 1) return fail(SDMM_ERR_INVALID_ARG, "R, N_max, iters out of range");
-    if (cfg->precision != SDMM_PREC_FP32)
-        return fail(SDMM_ERR_UNSUPPORTED, "precision %d is not available in fit plans", cfg->precision);
     const Layout L = layout(cfg, R, N_max, choose_chunk(cfg, N_max));
     if ((e = check_ws(workspace, ws_bytes, L))) return e;
     const int nsm = sm_count();
@@ -575,7 +598,8 @@ sdmm_status sdmm_tc_selftest(int32_t kind, int32_t N, int32_t Kd, const float* A
     if (N < 16 || N > 256 || N % 16) return fail(SDMM_ERR_INVALID_ARG, "N = %d: multiple of 16 in [16, 256]", N);
     const int kq = kind == 0 ? 16 : 8;
     if (Kd < kq || Kd > 64 || Kd % kq) return fail(SDMM_ERR_INVALID_ARG, "Kd = %d: multiple of %d, at most 64", Kd, kq);
-    if (variant != 0 && variant != 1) return fail(SDMM_ERR_INVALID_ARG, "variant %d", variant);
+    if (variant < 0 || variant > 15) return fail(SDMM_ERR_INVALID_ARG, "variant %d", variant);
+    if (kind != 0 && (variant & 6)) return fail(SDMM_ERR_INVALID_ARG, "MN-major operands are tested for BF16 only");
     if (!A || !B || !D || !status) return fail(SDMM_ERR_INVALID_ARG, "NULL pointer");
     SDMM_CUDA(launch_tc_selftest(stream, kind, N, Kd, A, B, D, variant, status), "tc_selftest");
     return SDMM_OK;

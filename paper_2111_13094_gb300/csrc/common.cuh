@@ -21,6 +21,9 @@ __host__ __device__ constexpr int pk(int i, int j) { return i * (i + 1) / 2 + j;
 
 // Statistics per component in the work-unit partials: [s0, s1(5), s2(15)]
 constexpr int kStat = 21;
+// Shared per-sample features of the contraction form:
+// [1, x' (3), vech(x'x') (6), w (3), w (x) x' (9), vech(ww) (6)]
+constexpr int kFeat = 28;
 // partial record of one work unit: K*21 component values, then W and sum w*l
 __host__ __device__ inline int partial_stride(int K) { return ((K * kStat + 2) + 3) & ~3; }
 
@@ -209,7 +212,8 @@ struct WsHeader {
     BatchDesc desc;
     int32_t n_chunks;
     int32_t queue;
-    int32_t pad_[14];
+    int32_t err;        // set by the tensor-core E-step when an MMA wait times out
+    int32_t pad_[13];
 };
 
 }  // namespace sdmm

@@ -68,6 +68,7 @@ __global__ void __launch_bounds__(1024) k_build_chunks(WsHeader* ws, int64_t* ch
         chunk_base[R] = total;
         ws->n_chunks = (int32_t)min(total, max_chunks);
         ws->queue = 0;
+        ws->err = 0;
     }
     __syncthreads();   // chunk_base is complete before any thread reads a neighbour's entry
     for (int64_t r = tid; r < R; r += 1024) {
@@ -300,14 +301,54 @@ __device__ inline double prior_beta(const sdmm_config& cfg, const double* prior_
 // ---------------------------------------------------------------------------
 // FP64 reduction + averaging + MAP M-step, one CTA per region (Sec. 3.2,
 // Sec. 3.4, Sec. 4.3).  Thread k < K updates component k.
+// Feature-space statistics of one component (contraction form) to the
+// chart statistics [s0, s1 (5), s2 (15)].  Rows a, b, c hold sums of
+// w r phi, w r g phi and w r g^2 phi over the features
+// phi = [1, x', vech(x'x'), w, w (x) x', vech(ww)] with x' = x - xref.
+__device__ inline void features_to_stats(const double* Fa, const double* Fb, const double* Fc,
+                                         const double mp[3], const double muw[3], double* out) {
+    double t[3], b[3];
+    basis_f64(muw, t, b);
+    const double A[2][3] = {{t[0], t[1], t[2]}, {b[0], b[1], b[2]}};
+    static constexpr int V[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};   // vech index of (p, q)
+    const double s0 = Fa[0];
+    const double Sx[3] = {Fa[1], Fa[2], Fa[3]};
+    double* s1 = out + 1;
+    double* s2 = out + 6;
+    out[0] = s0;
+    for (int a = 0; a < 3; ++a) s1[a] = Sx[a] - mp[a] * s0;
+    for (int a = 0; a < 3; ++a)
+        for (int c = 0; c <= a; ++c)
+            s2[pk(a, c)] = Fa[4 + V[a][c]] - mp[a] * Sx[c] - Sx[a] * mp[c] + s0 * mp[a] * mp[c];
+    const double Gw[3] = {Fb[10], Fb[11], Fb[12]};
+    for (int j = 0; j < 2; ++j) {
+        s1[3 + j] = A[j][0] * Gw[0] + A[j][1] * Gw[1] + A[j][2] * Gw[2];
+        for (int a = 0; a < 3; ++a) {
+            double v = 0.0;
+            for (int p = 0; p < 3; ++p) v += A[j][p] * (Fb[13 + 3 * p + a] - mp[a] * Gw[p]);
+            s2[pk(3 + j, a)] = v;
+        }
+    }
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j <= i; ++j) {
+            double v = 0.0;
+            for (int p = 0; p < 3; ++p)
+                for (int q = 0; q < 3; ++q) v += A[i][p] * Fc[22 + V[p][q]] * A[j][q];
+            s2[pk(3 + i, 3 + j)] = v;
+        }
+}
+
+template <bool FEAT>
 __global__ void __launch_bounds__(128) k_reduce_mstep(WsHeader* __restrict__ ws,
                                                       const int64_t* __restrict__ chunk_base,
                                                       const float* __restrict__ partial, int ps,
-                                                      sdmm_config cfg, sdmm_state st, int iter) {
+                                                      sdmm_config cfg, sdmm_state st, int iter,
+                                                      const float* __restrict__ xref) {
     const int64_t r = blockIdx.x;
     const int K = cfg.K;
     const int tid = threadIdx.x;
     __shared__ double s_st[SDMM_MAX_K * kStat + 2];
+    __shared__ double s_feat[FEAT ? 3 * SDMM_MAX_K * kFeat + 2 : 1];
     __shared__ double s_S0[SDMM_MAX_K];
     __shared__ int s_code[SDMM_MAX_K];
     __shared__ int s_skip;
@@ -332,12 +373,32 @@ __global__ void __launch_bounds__(128) k_reduce_mstep(WsHeader* __restrict__ ws,
     }
     __syncthreads();
     if (s_skip >= 0) return;
-    reduce_partials(partial, ps, c0, c1, K * kStat + 2, s_st);
+    if (FEAT) {
+        reduce_partials(partial, ps, c0, c1, 3 * K * kFeat + 2, s_feat);
+        __syncthreads();
+        if (tid < K) {
+            const int64_t rk = r * K + tid;
+            double mp[3], muw[3];
+            for (int c = 0; c < 3; ++c) {
+                mp[c] = st.mu_x[rk * 3 + c] - (double)xref[r * 4 + c];
+                muw[c] = st.mu_w[rk * 3 + c];
+            }
+            features_to_stats(s_feat + tid * kFeat, s_feat + (K + tid) * kFeat,
+                              s_feat + (2 * K + tid) * kFeat, mp, muw, s_st + tid * kStat);
+        }
+        if (tid == 0) {
+            s_st[K * kStat] = s_feat[3 * K * kFeat];
+            s_st[K * kStat + 1] = s_feat[3 * K * kFeat + 1];
+        }
+    } else {
+        reduce_partials(partial, ps, c0, c1, K * kStat + 2, s_st);
+    }
     __syncthreads();
     const double W = s_st[K * kStat];
     if (tid == 0) {
         int code = -1;
-        if (!isfinite(W)) code = SDMM_REGION_NONFINITE;
+        if (ws->err != 0) code = SDMM_REGION_DEVICE_TIMEOUT;
+        else if (!isfinite(W)) code = SDMM_REGION_NONFINITE;
         else if (!(W > 0.0)) code = SDMM_REGION_ZERO_WEIGHT;
         if (code >= 0) st.status[r] = code;
         s_skip = code;
@@ -690,8 +751,11 @@ cudaError_t launch_accumulate(cudaStream_t s, int mode, int KP, int grid, WsHead
 
 cudaError_t launch_reduce_mstep(cudaStream_t s, int64_t R, WsHeader* ws, const int64_t* cb,
                                 const float* partial, int ps, const sdmm_config& cfg,
-                                const sdmm_state& st, int iter) {
-    k_reduce_mstep<<<(unsigned)R, 128, 0, s>>>(ws, cb, partial, ps, cfg, st, iter);
+                                const sdmm_state& st, int iter, const float* xref) {
+    if (xref != nullptr)
+        k_reduce_mstep<true><<<(unsigned)R, 128, 0, s>>>(ws, cb, partial, ps, cfg, st, iter, xref);
+    else
+        k_reduce_mstep<false><<<(unsigned)R, 128, 0, s>>>(ws, cb, partial, ps, cfg, st, iter, xref);
     return cudaGetLastError();
 }
 

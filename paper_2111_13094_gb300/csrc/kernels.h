@@ -25,7 +25,15 @@ cudaError_t launch_accumulate(cudaStream_t s, int mode, int KP, int grid, WsHead
                               int chunk, int density, float* partial, int ps, int write_ll);
 cudaError_t launch_reduce_mstep(cudaStream_t s, int64_t R, WsHeader* ws, const int64_t* cb,
                                 const float* partial, int ps, const sdmm_config& cfg,
-                                const sdmm_state& st, int iter);
+                                const sdmm_state& st, int iter, const float* xref);
+// contraction form on the tensor cores
+size_t tc_smem_bytes(int K, int prec);
+int tc_ctas_per_sm(int K, int prec);
+cudaError_t launch_tc_prepare(cudaStream_t s, int K, int64_t R, const sdmm_state& st, float* ctab,
+                              float* xref);
+cudaError_t launch_tc_estep(cudaStream_t s, int K, int prec, int grid, WsHeader* ws, const int64_t* cb,
+                            const int32_t* cr, const float* ctab, const float* xref, int chunk,
+                            float* partial, int ps, int write_ll);
 cudaError_t launch_reduce_objective(cudaStream_t s, int64_t R, const WsHeader* ws,
                                     const int64_t* cb, const float* partial, int ps,
                                     const sdmm_config& cfg, const sdmm_state& st, double* F,

@@ -25,6 +25,15 @@ __host__ __device__ __forceinline__ uint32_t kmajor_offset(int row, int k, int C
     return (uint32_t)(((row >> 3) * (C / per) + (k / per)) * 128 + (row & 7) * 16 + (k % per) * esize);
 }
 
+// byte offset of element (mn, k) of an MN-major tile with MN elements along
+// the M (or N) dimension: core matrices hold 8 K-rows of 8 contiguous MN
+// elements (BF16); MN blocks are 128 B apart, K blocks (MN/8)*128 B apart.
+// Its descriptor takes the K-block distance as the leading-dimension offset
+// and the MN-block distance (128 B) as the stride offset.
+__host__ __device__ __forceinline__ uint32_t mnmajor_offset(int mn, int k, int MN) {
+    return (uint32_t)(((k >> 3) * (MN >> 3) + (mn >> 3)) * 128 + (k & 7) * 16 + (mn & 7) * 2);
+}
+
 // Shared-memory matrix descriptor (tcgen05): start address, leading and stride
 // dimension byte offsets (all >> 4), descriptor version 1 at bits 46-47, no
 // swizzle (layout type 0 at bits 61-63).
@@ -40,11 +49,14 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
 // Instruction descriptor: FP32 accumulator, A and B of format `fmt`
 // (kind::f16: 0 = F16, 1 = BF16; kind::tf32: 2 = TF32), both K-major,
 // M x N tile.
-__host__ __device__ __forceinline__ uint32_t instr_desc(int fmt, int M, int N) {
+__host__ __device__ __forceinline__ uint32_t instr_desc(int fmt, int M, int N, int a_mn = 0,
+                                                        int b_mn = 0) {
     uint32_t d = 0;
     d |= 1u << 4;                        // D format: F32
     d |= (uint32_t)fmt << 7;             // A format
     d |= (uint32_t)fmt << 10;            // B format
+    d |= (uint32_t)(a_mn & 1) << 15;     // A: 0 K-major, 1 MN-major
+    d |= (uint32_t)(b_mn & 1) << 16;     // B: 0 K-major, 1 MN-major
     d |= (uint32_t)(N >> 3) << 17;       // N / 8
     d |= (uint32_t)(M >> 4) << 24;       // M / 16
     return d;

@@ -48,3 +48,18 @@ def test_tc_tile_matches_fp64_product(kind, N, Kd):
     D, ref = _run(kind, N, Kd, variant=0)
     err = np.abs(D - ref).max()
     assert err < 1e-4 * max(1.0, np.abs(ref).max()), err
+
+
+@pytest.mark.parametrize("variant", [2, 4, 6])          # A and/or B staged MN-major (BF16)
+@pytest.mark.parametrize("N,Kd", [(32, 64), (96, 32), (128, 64)])
+def test_tc_mn_major_tiles(variant, N, Kd):
+    D, ref = _run(0, N, Kd, variant=variant)
+    assert np.abs(D - ref).max() < 1e-4 * max(1.0, np.abs(ref).max())
+
+
+def test_tc_swapped_offsets_are_detected():
+    """The diagnostic variants that swap the two descriptor offsets must give a
+    wrong product: the tests above would catch a wrong layout reading."""
+    for variant in (1, 10):
+        D, ref = _run(0, 96, 32, variant=variant)
+        assert np.abs(D - ref).max() > 1.0
