@@ -62,13 +62,19 @@ typedef enum {
 enum {
     SDMM_REGION_OK = 0,
     SDMM_REGION_SKIPPED = 1,     /* fewer than min_samples samples (Sec. 4.2)   */
-    SDMM_REGION_NUMERIC = 2,     /* a covariance was not positive definite; the
-                                    failing step left the region unchanged      */
+    SDMM_REGION_NUMERIC = 2,     /* a covariance was not positive definite even
+                                    with the floor below; the failing step left
+                                    the region unchanged                        */
     SDMM_REGION_NONFINITE = 3,   /* non-finite weights or statistics            */
     SDMM_REGION_ZERO_WEIGHT = 4, /* all sample weights are zero                 */
     SDMM_REGION_BAD_OFFSETS = 5, /* offsets decrease or exceed N                */
-    SDMM_REGION_DEVICE_TIMEOUT = 6 /* a tensor-core wait of the E-step timed out;
+    SDMM_REGION_DEVICE_TIMEOUT = 6, /* a tensor-core wait of the E-step timed out;
                                       no region was updated in that step        */
+    SDMM_REGION_REPAIRED = 7     /* updated; a component's MAP covariance was not
+                                    positive definite in working precision and
+                                    got the smallest tau * B / a (tau = 1e-6,
+                                    1e-4, 1e-2, 1) that makes it so; if even
+                                    tau = 1 fails the status is NUMERIC        */
 };
 
 enum { SDMM_ETA_ROBBINS_MONRO = 0, SDMM_ETA_ONE = 1 };
@@ -365,8 +371,9 @@ sdmm_status sdmm_autotune(const sdmm_config *cfg, const sdmm_samples *s,
  * FP32.  N: multiple of 16 in [16, 256]; Kd: multiple of 16 (BF16) or 8
  * (TF32), at most 64.  `variant` bits: 1 swaps the two descriptor offsets of
  * K-major operands (diagnostics), 2 / 4 stage A / B MN-major (BF16 only),
- * 8 swaps the offsets of MN-major operands (diagnostics).  Variants 0 and
- * 4 are the layouts the contraction-form E-step uses.
+ * 8 swaps the offsets of MN-major operands (diagnostics), 16 makes A 64 x Kd
+ * (M = 64; D then holds all 128 TMEM lanes, showing where the 64 rows sit).
+ * Variants 0, 4 and 6 are the layouts the contraction-form E-step uses.
  * status (device int32): set to 1 if the MMA did not complete within 2 s.
  * (The paper has no counterpart: this checks the hardware path.)
  */

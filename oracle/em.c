@@ -240,7 +240,7 @@ static int mstep_region(const or_config *cfg, int K, int64_t r, int64_t M,
     double *nmw = (double *)malloc(sizeof(double) * 3 * K);
     double *nL = (double *)malloc(sizeof(double) * 15 * K);
     double *npi = (double *)malloc(sizeof(double) * K);
-    int bad = 0;
+    int bad = 0, repaired = 0;
     double sumS0 = 0.0;
     for (int k = 0; k < K && !bad; ++k) {
         const int64_t rk = base + k;
@@ -288,7 +288,21 @@ static int mstep_region(const or_config *cfg, int K, int64_t r, int64_t M,
             for (int j = 0; j <= i; ++j)
                 Sig[PK(i, j)] = ((i == j ? beta * Bd[i] : 0.0) + nS2[k * 15 + PK(i, j)]) /
                                 (beta * a + hS0);
-        if (or_cholesky5(Sig, nL + k * 15)) bad = 2;
+        if (or_cholesky5(Sig, nL + k * 15)) {
+            /* Numerical floor (reading; the paper's prior is meant to stop
+               collapse but vanishes as beta -> 0): add the smallest of
+               tau * B / a, tau = 1e-6, 1e-4, 1e-2, 1, that makes the
+               covariance positive definite; the region is flagged. */
+            int fixed = 0;
+            for (double tau = 1e-6; tau <= 1.0 && !fixed; tau *= 100.0) {
+                double S2f[15];
+                for (int p = 0; p < 15; ++p) S2f[p] = Sig[p];
+                for (int c = 0; c < 5; ++c) S2f[PK(c, c)] += tau * Bd[c] / a;
+                fixed = !or_cholesky5(S2f, nL + k * 15);
+            }
+            if (fixed) repaired = 1;
+            else bad = 2;
+        }
     }
     if (!bad) {
         /* MAP weights, Sec. 4.3 */
@@ -311,7 +325,7 @@ static int mstep_region(const or_config *cfg, int K, int64_t r, int64_t M,
         st->step_j[r] += 1;
     }
     free(nS0); free(nS2); free(nmx); free(nmw); free(nL); free(npi);
-    return bad;
+    return bad ? bad : (repaired ? 7 : 0);
 }
 
 /*
@@ -347,7 +361,8 @@ int or_fit_regions(const or_config *cfg, int64_t R, const int64_t *offsets,
         int status = 0;
         double *resp = NULL;
         if (cfg->cov_update == 1) resp = (double *)malloc(sizeof(double) * M * K);
-        for (int it = 0; it < iters && !status; ++it) {
+        int worst = 0;
+        for (int it = 0; it < iters && (status == 0 || status == 7); ++it) {
             double W;
             const int64_t rk = r * K;
             or_estep_region(cfg, K, st->pi + rk, st->mu_x + rk * 3, st->mu_w + rk * 3,
@@ -384,10 +399,11 @@ int or_fit_regions(const or_config *cfg, int64_t R, const int64_t *offsets,
                 two = s2b;
             }
             status = mstep_region(cfg, K, r, M, s0, s1, s2, W, two, beta, st);
-            if (!status) st->n_seen[r] = seen;
+            if (status == 0 || status == 7) st->n_seen[r] = seen;
+            if (status == 7) worst = 7;
         }
         free(resp);
-        st->status[r] = status;
+        st->status[r] = (status == 0 && worst) ? worst : status;
     }
     free(s0); free(s1); free(s2); free(s2b);
     return 0;

@@ -33,8 +33,9 @@
  *   in the 5-D order (x0, x1, x2, nu0, nu1): position first, then direction.
  *
  * Per-region status codes: 0 ok, 1 skipped (fewer than min_samples samples),
- * 2 numeric (a covariance was not positive definite; region left unchanged),
- * 3 non-finite statistics, 4 zero total weight.
+ * 2 numeric (a covariance was not positive definite even with the numerical
+ * floor; region left unchanged), 3 non-finite statistics, 4 zero total weight,
+ * 7 repaired (updated; a covariance needed the numerical floor).
  */
 #ifndef SDMM_ORACLE_H
 #define SDMM_ORACLE_H

@@ -366,7 +366,7 @@ __global__ void __launch_bounds__(128) k_reduce_mstep(WsHeader* __restrict__ ws,
                 code = SDMM_REGION_BAD_OFFSETS;
             else if (M < cfg.min_samples || M <= 0) code = SDMM_REGION_SKIPPED;
             if (code >= 0) st.status[r] = code;
-        } else if (st.status[r] != SDMM_REGION_OK) {
+        } else if (st.status[r] != SDMM_REGION_OK && st.status[r] != SDMM_REGION_REPAIRED) {
             code = st.status[r];
         }
         s_skip = code;
@@ -471,20 +471,38 @@ __global__ void __launch_bounds__(128) k_reduce_mstep(WsHeader* __restrict__ ws,
             for (int i = 0; i < 5; ++i)
                 for (int j = 0; j <= i; ++j)
                     Sig[pk(i, j)] = ((i == j ? beta * Bd[i] : 0.0) + nS2[pk(i, j)]) / den;
-            if (!cholesky5_f64(Sig, nL)) code = SDMM_REGION_NUMERIC;
+            if (!cholesky5_f64(Sig, nL)) {
+                // numerical floor: smallest tau * B / a (tau = 1e-6 ... 1) that
+                // makes the covariance positive definite; the region is flagged
+                code = SDMM_REGION_NUMERIC;
+                for (double tau = 1e-6; tau <= 1.0; tau *= 100.0) {
+                    double Sf[15];
+                    for (int p = 0; p < 15; ++p) Sf[p] = Sig[p];
+                    for (int c = 0; c < 5; ++c) Sf[pk(c, c)] += tau * Bd[c] / a;
+                    if (cholesky5_f64(Sf, nL)) {
+                        code = SDMM_REGION_REPAIRED;
+                        break;
+                    }
+                }
+            }
         }
         s_code[tid] = code;
         s_S0[tid] = hS0;
     }
     __syncthreads();
     if (tid == 0) {
-        int first = 0;
-        for (int kk = 0; kk < K && first == 0; ++kk) first = s_code[kk];
+        int first = 0, repaired = 0;
+        for (int kk = 0; kk < K && first == 0; ++kk) {
+            if (s_code[kk] == SDMM_REGION_REPAIRED) repaired = 1;
+            else first = s_code[kk];
+        }
         s_skip = first;
         if (first != 0) st.status[r] = first;
+        s_code[0] = repaired;
     }
     __syncthreads();
     if (s_skip != 0) return;
+    const bool repaired = s_code[0] != 0;
     if (tid < K) {
         double sumS0 = 0.0;
         for (int kk = 0; kk < K; ++kk) sumS0 += s_S0[kk];
@@ -505,7 +523,9 @@ __global__ void __launch_bounds__(128) k_reduce_mstep(WsHeader* __restrict__ ws,
         st.Wbar[r] = (1.0 - eta) * st.Wbar[r] + eta * (W / (double)M);
         st.step_j[r] += 1;
         st.n_seen[r] = seen;
-        st.status[r] = SDMM_REGION_OK;
+        // a repair in any step of this call is reported (later steps continue)
+        if (repaired) st.status[r] = SDMM_REGION_REPAIRED;
+        else if (iter == 0) st.status[r] = SDMM_REGION_OK;
     }
 }
 

@@ -370,7 +370,8 @@ def test_region_status_codes(orc):
     assert list(st.status) == [1, 0, 4, 3]
     for r in (0, 2, 3):
         assert np.array_equal(st.L[r], before.L[r]) and st.n_seen[r] == 0
-    # non-positive-definite covariance: zero prior scale and collinear samples
+    # collapsed covariance (identical samples, zero prior scale): the MAP
+    # covariance is 0; the numerical floor adds 1e-6 B / a and flags the region
     x2 = np.zeros((50, 3)) + 0.5
     s2 = _samples(x2, np.tile([0, 0, 1.0], (50, 1)), np.ones(50, np.float32))
     st2 = orc.State(1, 1)
@@ -378,6 +379,8 @@ def test_region_status_codes(orc):
     st2.mu_x[:] = 0.5
     st2.mu_w[:] = [0, 0, 1.0]
     st2.L[:] = _pack(np.eye(5) * 0.1)
-    keep = st2.L.copy()
-    orc.fit_regions(orc.config(1, prior_scale_mode=1), [0, 50], s2, 1, st2, prior_scale=np.zeros(1))
-    assert st2.status[0] == 2 and np.array_equal(st2.L, keep) and st2.step_j[0] == 0
+    cfg = orc.config(1, prior_scale_mode=1)
+    orc.fit_regions(cfg, [0, 50], s2, 1, st2, prior_scale=np.zeros(1))
+    assert st2.status[0] == 7 and st2.step_j[0] == 1
+    floor = 1e-6 * np.array([cfg.prior_B_pos] * 3 + [cfg.prior_B_dir] * 2)
+    assert np.allclose(st2.L[0, 0, [0, 2, 5, 9, 14]], np.sqrt(floor), rtol=1e-6)
