@@ -113,7 +113,7 @@ int choose_chunk(const sdmm_config* cfg, int64_t N) {
 }
 
 struct Layout {
-    size_t header, chunk_base, chunk_region, partial, ctab, xref, total;
+    size_t header, chunk_base, chunk_region, partial, ctab, xref, units, total;
     int chunk, ps;
     int64_t max_chunks;
 };
@@ -123,8 +123,9 @@ bool tensor_core(const sdmm_config* cfg) { return cfg->precision != SDMM_PREC_FP
 Layout layout(const sdmm_config* cfg, int64_t R, int64_t N, int chunk) {
     Layout L{};
     L.chunk = chunk;
-    // tensor-core partials hold 3K feature-space rows of 28, the SIMT ones 21K statistics
-    L.ps = tensor_core(cfg) ? ((3 * cfg->K * kFeat + 2) + 3) & ~3 : partial_stride(cfg->K);
+    // tensor-core partials hold 3K feature-space rows of 28 and four per-quadrant
+    // (W, sum w l) pairs, the SIMT ones 21K statistics
+    L.ps = tensor_core(cfg) ? ((3 * cfg->K * kFeat + 8) + 3) & ~3 : partial_stride(cfg->K);
     L.max_chunks = (N + chunk - 1) / chunk + R;
     size_t o = 0;
     L.header = o;
@@ -135,12 +136,14 @@ Layout layout(const sdmm_config* cfg, int64_t R, int64_t N, int chunk) {
     o = align_up(o + sizeof(int32_t) * (size_t)L.max_chunks);
     L.partial = o;
     o = align_up(o + sizeof(float) * (size_t)L.max_chunks * L.ps);
-    L.ctab = L.xref = o;
+    L.ctab = L.xref = L.units = o;
     if (tensor_core(cfg)) {
         L.ctab = o;
         o = align_up(o + sizeof(float) * (size_t)R * cfg->K * 6 * 32);
         L.xref = o;
         o = align_up(o + sizeof(float) * (size_t)R * 4);
+        L.units = o;
+        o = align_up(o + sizeof(int64_t) * 2 * (size_t)L.max_chunks);
     }
     L.total = o;
     return L;
@@ -153,13 +156,15 @@ struct WsPtrs {
     float* partial;
     float* ctab;
     float* xref;
+    int64_t* units;     // tensor-core path only, else null
 };
 
 WsPtrs ws_ptrs(void* ws, const Layout& L) {
     char* b = static_cast<char*>(ws);
     return WsPtrs{reinterpret_cast<WsHeader*>(b + L.header), reinterpret_cast<int64_t*>(b + L.chunk_base),
                   reinterpret_cast<int32_t*>(b + L.chunk_region), reinterpret_cast<float*>(b + L.partial),
-                  reinterpret_cast<float*>(b + L.ctab), reinterpret_cast<float*>(b + L.xref)};
+                  reinterpret_cast<float*>(b + L.ctab), reinterpret_cast<float*>(b + L.xref),
+                  L.units < L.total ? reinterpret_cast<int64_t*>(b + L.units) : nullptr};
 }
 
 sdmm_status check_ws(void* ws, size_t bytes, const Layout& L) {
@@ -197,7 +202,8 @@ struct FitLaunch {
 sdmm_status enqueue_fit(const FitLaunch& f, cudaStream_t s, std::vector<cudaEvent_t>* evs) {
     const int KP = pow2_ceil(f.cfg.K);
     const bool tcore = tensor_core(&f.cfg);
-    SDMM_CUDA(launch_build_chunks(s, f.w.hdr, f.w.cb, f.w.cr, f.L.chunk, f.cfg.min_samples, f.L.max_chunks),
+    SDMM_CUDA(launch_build_chunks(s, f.w.hdr, f.w.cb, f.w.cr, f.w.units, f.L.chunk, f.cfg.min_samples,
+                                  f.L.max_chunks),
               "build_chunks");
     for (int it = 0; it < f.iters; ++it) {
         const int wll = f.want_ll && it == f.iters - 1;
@@ -205,9 +211,9 @@ sdmm_status enqueue_fit(const FitLaunch& f, cudaStream_t s, std::vector<cudaEven
             SDMM_CUDA(launch_tc_prepare(s, f.cfg.K, f.R, f.st, f.w.ctab, f.w.xref), "tc_prepare");
         if (evs) SDMM_CUDA(cudaEventRecordWithFlags((*evs)[2 * it], s, cudaEventRecordExternal), "event");
         if (tcore) {
-            const int grid = std::max(1, sm_count()) * tc_ctas_per_sm(f.cfg.K, f.cfg.precision);
-            SDMM_CUDA(launch_tc_estep(s, f.cfg.K, f.cfg.precision, grid, f.w.hdr, f.w.cb, f.w.cr, f.w.ctab,
-                                      f.w.xref, f.L.chunk, f.w.partial, f.L.ps, wll),
+            const int grid = std::max(1, sm_count()) * tc_ctas_per_sm(f.cfg.K, f.cfg.precision);   // persistent
+            SDMM_CUDA(launch_tc_estep(s, f.cfg.K, f.cfg.precision, grid, f.w.hdr, f.w.cr, f.w.units, f.w.ctab,
+                                      f.w.xref, f.w.partial, f.L.ps, wll),
                       "tc_estep");
         } else {
             SDMM_CUDA(launch_accumulate(s, MODE_FIT, KP, f.grid, f.w.hdr, f.w.cb, f.w.cr, f.st.etab, f.cfg.K,
@@ -424,7 +430,7 @@ static sdmm_status objective_common(const sdmm_config* cfg, const sdmm_samples* 
     const WsPtrs w = ws_ptrs(workspace, L);
     const int KP = pow2_ceil(cfg->K);
     SDMM_CUDA(launch_set_desc(stream, w.hdr, make_desc(s, prior_scale, nullptr)), "set_desc");
-    SDMM_CUDA(launch_build_chunks(stream, w.hdr, w.cb, w.cr, L.chunk, 1, L.max_chunks), "build_chunks");
+    SDMM_CUDA(launch_build_chunks(stream, w.hdr, w.cb, w.cr, nullptr, L.chunk, 1, L.max_chunks), "build_chunks");
     SDMM_CUDA(launch_accumulate(stream, dF ? MODE_GRAD : MODE_FIT, KP, nsm * default_ctas(cfg), w.hdr,
                                 w.cb, w.cr, st->etab, cfg->K, L.chunk, cfg->estep_density, w.partial,
                                 L.ps, 0),
@@ -598,7 +604,7 @@ sdmm_status sdmm_tc_selftest(int32_t kind, int32_t N, int32_t Kd, const float* A
     if (N < 16 || N > 256 || N % 16) return fail(SDMM_ERR_INVALID_ARG, "N = %d: multiple of 16 in [16, 256]", N);
     const int kq = kind == 0 ? 16 : 8;
     if (Kd < kq || Kd > 64 || Kd % kq) return fail(SDMM_ERR_INVALID_ARG, "Kd = %d: multiple of %d, at most 64", Kd, kq);
-    if (variant < 0 || variant > 15) return fail(SDMM_ERR_INVALID_ARG, "variant %d", variant);
+    if (variant < 0 || variant > 31) return fail(SDMM_ERR_INVALID_ARG, "variant %d", variant);
     if (kind != 0 && (variant & 6)) return fail(SDMM_ERR_INVALID_ARG, "MN-major operands are tested for BF16 only");
     if (!A || !B || !D || !status) return fail(SDMM_ERR_INVALID_ARG, "NULL pointer");
     SDMM_CUDA(launch_tc_selftest(stream, kind, N, Kd, A, B, D, variant, status), "tc_selftest");
@@ -656,7 +662,7 @@ sdmm_status sdmm_autotune(const sdmm_config* cfg, const sdmm_samples* s, const s
             float tmin = INFINITY;
             for (int rep = 0; rep < 4; ++rep) {
                 if (launch_set_desc(stream, w.hdr, make_desc(s, nullptr, nullptr)) != cudaSuccess ||
-                    launch_build_chunks(stream, w.hdr, w.cb, w.cr, c, cfg->min_samples, L.max_chunks) != cudaSuccess)
+                    launch_build_chunks(stream, w.hdr, w.cb, w.cr, nullptr, c, cfg->min_samples, L.max_chunks) != cudaSuccess)
                     return fail(SDMM_ERR_CUDA, "autotune launch");
                 cudaEventRecord(a, stream);
                 if (launch_accumulate(stream, MODE_FIT, KP, nsm * g, w.hdr, w.cb, w.cr, st->etab, cfg->K, c,

@@ -21,9 +21,11 @@ __global__ void k_set_desc(WsHeader* ws, BatchDesc d) { ws->desc = d; }
 // units; chunk_base is the exclusive prefix sum over regions (int64 scan),
 // chunk_region the owner of each unit.  Units beyond the workspace capacity
 // `max_chunks` (possible only when offsets overlap) are not created; the
-// M-step flags their regions.  One CTA of 1024 threads.
+// M-step flags their regions.  When `units` is given, it receives each unit's
+// sample range [start, end) (the tensor-core E-step reads it).  One CTA of
+// 1024 threads.
 __global__ void __launch_bounds__(1024) k_build_chunks(WsHeader* ws, int64_t* chunk_base,
-                                                       int32_t* chunk_region, int chunk,
+                                                       int32_t* chunk_region, int64_t* units, int chunk,
                                                        int min_samples, int64_t max_chunks) {
     const int64_t R = ws->desc.R, N = ws->desc.N;
     const int64_t* off = ws->desc.offsets;
@@ -74,7 +76,14 @@ __global__ void __launch_bounds__(1024) k_build_chunks(WsHeader* ws, int64_t* ch
     for (int64_t r = tid; r < R; r += 1024) {
         const int64_t c0 = chunk_base[r];
         const int64_t c1 = min(r + 1 < R ? chunk_base[r + 1] : total, max_chunks);
-        for (int64_t c = c0; c < c1; ++c) chunk_region[c] = (int32_t)r;
+        for (int64_t c = c0; c < c1; ++c) {
+            chunk_region[c] = (int32_t)r;
+            if (units != nullptr) {               // sample range [start, end) of unit c
+                const int64_t start = off[r] + (c - c0) * chunk;
+                units[2 * c] = start;
+                units[2 * c + 1] = min(start + (int64_t)chunk, off[r + 1]);
+            }
+        }
     }
 }
 
@@ -348,7 +357,7 @@ __global__ void __launch_bounds__(128) k_reduce_mstep(WsHeader* __restrict__ ws,
     const int K = cfg.K;
     const int tid = threadIdx.x;
     __shared__ double s_st[SDMM_MAX_K * kStat + 2];
-    __shared__ double s_feat[FEAT ? 3 * SDMM_MAX_K * kFeat + 2 : 1];
+    __shared__ double s_feat[FEAT ? 3 * SDMM_MAX_K * kFeat + 8 : 1];
     __shared__ double s_S0[SDMM_MAX_K];
     __shared__ int s_code[SDMM_MAX_K];
     __shared__ int s_skip;
@@ -374,7 +383,7 @@ __global__ void __launch_bounds__(128) k_reduce_mstep(WsHeader* __restrict__ ws,
     __syncthreads();
     if (s_skip >= 0) return;
     if (FEAT) {
-        reduce_partials(partial, ps, c0, c1, 3 * K * kFeat + 2, s_feat);
+        reduce_partials(partial, ps, c0, c1, 3 * K * kFeat + 8, s_feat);
         __syncthreads();
         if (tid < K) {
             const int64_t rk = r * K + tid;
@@ -386,9 +395,10 @@ __global__ void __launch_bounds__(128) k_reduce_mstep(WsHeader* __restrict__ ws,
             features_to_stats(s_feat + tid * kFeat, s_feat + (K + tid) * kFeat,
                               s_feat + (2 * K + tid) * kFeat, mp, muw, s_st + tid * kStat);
         }
-        if (tid == 0) {
-            s_st[K * kStat] = s_feat[3 * K * kFeat];
-            s_st[K * kStat + 1] = s_feat[3 * K * kFeat + 1];
+        if (tid == 0) {   // W and sum w l arrive as four per-quadrant parts each
+            const double* wq = s_feat + 3 * K * kFeat;
+            s_st[K * kStat] = (wq[0] + wq[1]) + (wq[2] + wq[3]);
+            s_st[K * kStat + 1] = (wq[4] + wq[5]) + (wq[6] + wq[7]);
         }
     } else {
         reduce_partials(partial, ps, c0, c1, K * kStat + 2, s_st);
@@ -753,9 +763,9 @@ cudaError_t launch_set_desc(cudaStream_t s, WsHeader* ws, const BatchDesc& d) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_build_chunks(cudaStream_t s, WsHeader* ws, int64_t* cb, int32_t* cr, int chunk,
-                                int min_samples, int64_t max_chunks) {
-    k_build_chunks<<<1, 1024, 0, s>>>(ws, cb, cr, chunk, min_samples, max_chunks);
+cudaError_t launch_build_chunks(cudaStream_t s, WsHeader* ws, int64_t* cb, int32_t* cr, int64_t* units,
+                                int chunk, int min_samples, int64_t max_chunks) {
+    k_build_chunks<<<1, 1024, 0, s>>>(ws, cb, cr, units, chunk, min_samples, max_chunks);
     return cudaGetLastError();
 }
 

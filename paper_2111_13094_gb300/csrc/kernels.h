@@ -18,8 +18,8 @@ struct GridF {
 };
 
 cudaError_t launch_set_desc(cudaStream_t s, WsHeader* ws, const BatchDesc& d);
-cudaError_t launch_build_chunks(cudaStream_t s, WsHeader* ws, int64_t* cb, int32_t* cr, int chunk,
-                                int min_samples, int64_t max_chunks);
+cudaError_t launch_build_chunks(cudaStream_t s, WsHeader* ws, int64_t* cb, int32_t* cr, int64_t* units,
+                                int chunk, int min_samples, int64_t max_chunks);
 cudaError_t launch_accumulate(cudaStream_t s, int mode, int KP, int grid, WsHeader* ws,
                               const int64_t* cb, const int32_t* cr, const float* etab, int K,
                               int chunk, int density, float* partial, int ps, int write_ll);
@@ -28,12 +28,13 @@ cudaError_t launch_reduce_mstep(cudaStream_t s, int64_t R, WsHeader* ws, const i
                                 const sdmm_state& st, int iter, const float* xref);
 // contraction form on the tensor cores
 size_t tc_smem_bytes(int K, int prec);
-int tc_ctas_per_sm(int K, int prec);
+
 cudaError_t launch_tc_prepare(cudaStream_t s, int K, int64_t R, const sdmm_state& st, float* ctab,
                               float* xref);
-cudaError_t launch_tc_estep(cudaStream_t s, int K, int prec, int grid, WsHeader* ws, const int64_t* cb,
-                            const int32_t* cr, const float* ctab, const float* xref, int chunk,
-                            float* partial, int ps, int write_ll);
+int tc_ctas_per_sm(int K, int prec);
+cudaError_t launch_tc_estep(cudaStream_t s, int K, int prec, int grid, WsHeader* ws, const int32_t* cr,
+                            const int64_t* units, const float* ctab, const float* xref, float* partial,
+                            int ps, int write_ll);
 cudaError_t launch_reduce_objective(cudaStream_t s, int64_t R, const WsHeader* ws,
                                     const int64_t* cb, const float* partial, int ps,
                                     const sdmm_config& cfg, const sdmm_state& st, double* F,

@@ -123,6 +123,16 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
         : "=r"(ok) : "r"(smem_addr(bar)), "r"(parity) : "memory");
     return ok != 0;
 }
+// as mbar_try_wait, but the thread may stay suspended (without issuing) for up
+// to `hint_ns` nanoseconds while the phase is still incomplete
+__device__ __forceinline__ bool mbar_try_wait_hint(uint64_t* bar, uint32_t parity, uint32_t hint_ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok) : "r"(smem_addr(bar)), "r"(parity), "r"(hint_ns) : "memory");
+    return ok != 0;
+}
 __device__ __forceinline__ uint64_t global_ns() {
     uint64_t t;
     asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
@@ -130,14 +140,67 @@ __device__ __forceinline__ uint64_t global_ns() {
 }
 // Waits for phase `parity` of `bar` for at most `limit_ns` nanoseconds.
 // Returns false on timeout (the caller records an error and stops).
+// Each poll suspends the thread for up to 0.1 ms, so waiting costs almost no
+// issue slots.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     while (true) {
-        if (mbar_try_wait(bar, parity)) return true;
+        if (mbar_try_wait_hint(bar, parity, 100000u)) return true;
         if (global_ns() - t0 > limit_ns) return false;
     }
 }
+
+// ---- shared memory through 32-bit shared-window addresses
+__device__ __forceinline__ void sts128(uint32_t a, uint32_t x, uint32_t y, uint32_t z, uint32_t w) {
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" :: "r"(a), "r"(x), "r"(y), "r"(z), "r"(w) : "memory");
+}
+__device__ __forceinline__ void sts64(uint32_t a, uint32_t x, uint32_t y) {
+    asm volatile("st.shared.v2.b32 [%0], {%1, %2};" :: "r"(a), "r"(x), "r"(y) : "memory");
+}
+__device__ __forceinline__ void sts32(uint32_t a, float x) {
+    asm volatile("st.shared.f32 [%0], %1;" :: "r"(a), "f"(x) : "memory");
+}
+__device__ __forceinline__ float lds32(uint32_t a) {
+    float x;
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(x) : "r"(a) : "memory");
+    return x;
+}
+__device__ __forceinline__ float2 lds64(uint32_t a) {
+    float2 x;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(x.x), "=f"(x.y) : "r"(a) : "memory");
+    return x;
+}
+// 4-byte asynchronous copy global -> shared (shared-window address; zero
+// fill when `valid` is false, `src` must still be a readable address)
+__device__ __forceinline__ void cp_async4s(uint32_t dst, const void* src, bool valid) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" :: "r"(dst), "l"(src), "r"(valid ? 4 : 0) : "memory");
+}
+
+// completion of this thread's asynchronous copies: commit / wait groups
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory"); }
+
+// arrive once on `bar` (release, CTA scope)
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_addr(bar)) : "memory");
+}
+
+// named barrier ID over N threads that returns whether any of them passed p != 0
+template <int ID, int N>
+__device__ __forceinline__ bool bar_red_or(bool p) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred q, s;\n\tsetp.ne.u32 q, %1, 0;\n\t"
+        "bar.red.or.pred s, %2, %3, q;\n\tselp.u32 %0, 1, 0, s;\n\t}\n"
+        : "=r"(r) : "r"((uint32_t)p), "n"(ID), "n"(N) : "memory");
+    return r != 0;
+}
+
+// shared-memory descriptor moved by `bytes` (the address field is the low 14
+// bits of the descriptor, in 16-byte units; callers stay inside one tile)
+__device__ __forceinline__ uint64_t desc_add(uint64_t d, uint32_t bytes) { return d + (uint64_t)(bytes >> 4); }
 
 // ---- TMEM -> registers: 32 lanes x 32 bit, 16 consecutive columns per
 // thread (lane quadrant of the calling warp), waiting for the load in the
@@ -154,6 +217,29 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
         : "r"(taddr) : "memory");
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Single-instruction approximations of the special-function unit (PTX
+// .approx.ftz forms; inputs and results flush subnormals to zero)
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float lg2_approx(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
 }
 
 // FP32 -> TF32 (round to nearest, ties away), kept in a 32-bit container

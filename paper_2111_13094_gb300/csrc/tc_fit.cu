@@ -17,7 +17,8 @@ namespace sdmm {
 constexpr uint64_t kTcWaitNs = 2000000000ull;   // 2 s bound on any MMA wait
 
 // variant bits: 0 swap the K-major offsets; 1 A MN-major; 2 B MN-major;
-// 3 swap the MN-major offsets (BF16 only for MN-major)
+// 3 swap the MN-major offsets (BF16 only for MN-major); 4 M = 64 (the read-out
+// then shows where the 64 accumulator rows sit among the 128 TMEM lanes)
 constexpr int kSelftestSmem = 200 * 1024;
 
 __global__ void __launch_bounds__(128) k_tc_selftest(int kind, int N, int Kd, const float* __restrict__ A,
@@ -29,11 +30,12 @@ __global__ void __launch_bounds__(128) k_tc_selftest(int kind, int N, int Kd, co
     const int tid = threadIdx.x, warp = tid >> 5;
     const int esize = kind == 0 ? 2 : 4;
     const int a_mn = (variant >> 1) & 1, b_mn = (variant >> 2) & 1;
+    const int M = (variant & 16) ? 64 : 128;
     unsigned char* sA = smem;
     unsigned char* sB = smem + 128 * Kd * esize;
-    for (int e = tid; e < 128 * Kd; e += 128) {
+    for (int e = tid; e < M * Kd; e += 128) {
         const int row = e / Kd, k = e % Kd;
-        const uint32_t o = a_mn ? tc::mnmajor_offset(row, k, 128) : tc::kmajor_offset(row, k, Kd, esize);
+        const uint32_t o = a_mn ? tc::mnmajor_offset(row, k, M) : tc::kmajor_offset(row, k, Kd, esize);
         if (kind == 0) *reinterpret_cast<__nv_bfloat16*>(sA + o) = __float2bfloat16_rn(A[e]);
         else *reinterpret_cast<float*>(sA + o) = tc::to_tf32(A[e]);
     }
@@ -76,9 +78,9 @@ __global__ void __launch_bounds__(128) k_tc_selftest(int kind, int N, int Kd, co
             }
         };
         uint32_t al, as, aa, bl, bs, ba;
-        offs(a_mn, 128, &al, &as, &aa);
+        offs(a_mn, M, &al, &as, &aa);
         offs(b_mn, N, &bl, &bs, &ba);
-        const uint32_t idesc = tc::instr_desc(kind == 0 ? 1 : 2, 128, N, a_mn, b_mn);
+        const uint32_t idesc = tc::instr_desc(kind == 0 ? 1 : 2, M, N, a_mn, b_mn);
         for (int s = 0; s < Kd / kstep; ++s) {
             const uint64_t ad = tc::smem_desc(tc::smem_addr(sA) + s * aa, al, as);
             const uint64_t bd = tc::smem_desc(tc::smem_addr(sB) + s * ba, bl, bs);
@@ -138,8 +140,11 @@ cudaError_t launch_tc_selftest(cudaStream_t s, int kind, int N, int Kd, const fl
 // a_hi b_lo + a_lo b_hi (three MMAs, FP32 accumulation).
 constexpr int kTile = 128;
 constexpr int kPhiPad = 32;     // features padded to the MMA K granularity
+constexpr double kLog2E = 1.4426950408889634074;
+constexpr float kLn2 = 0.693147180559945309f;
 
-// coefficient rows of component rk: ctab[rk][6][32] (u, v, c, T0, T1, T2)
+// coefficient rows of component rk: ctab[rk][6][32] (u, v, c, T0, T1, T2),
+// the last three scaled by log2(e)
 __global__ void k_tc_prepare(int K, int64_t R, sdmm_state st, float* __restrict__ ctab,
                              float* __restrict__ xref) {
     const int64_t rk = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -187,6 +192,9 @@ __global__ void k_tc_prepare(int K, int64_t R, sdmm_state st, float* __restrict_
     const double pi = st.pi[rk];
     double c5 = (pi > 0.0 ? log(pi) : -INFINITY) - 2.5 * kLog2Pi;
     for (int j = 0; j < 5; ++j) c5 -= log(L[pk(j, j)]);
+    // a component of zero weight keeps a finite, negligible constant: an
+    // infinite one would turn the split-product low part into NaN
+    c5 = fmax(c5, -1e30);
     double row[6][kPhiPad];
     for (int i = 0; i < 6; ++i)
         for (int f = 0; f < kPhiPad; ++f) row[i][f] = 0.0;
@@ -214,33 +222,70 @@ __global__ void k_tc_prepare(int K, int64_t R, sdmm_state st, float* __restrict_
         row[4][10 + p] = mp[0] * M[0][p] + mp[1] * M[1][p] + mp[2] * M[2][p];
         for (int q = 0; q < 3; ++q) row[4][13 + 3 * p + q] = -M[q][p];
     }
+    // T0, T1, T2 are stored times log2(e): the kernel's log-sum-exp runs in base 2
+    for (int i = 3; i < 6; ++i)
+        for (int f = 0; f < kPhiPad; ++f) row[i][f] *= kLog2E;
     float* out = ctab + rk * 6 * kPhiPad;
     for (int i = 0; i < 6; ++i)
         for (int f = 0; f < kPhiPad; ++f) out[i * kPhiPad + f] = (float)row[i][f];
 }
 
-// ---- shared-memory plan of k_tc_estep (byte offsets, 1024-aligned base)
+// ---- k_tc_estep: a software-pipelined persistent kernel of 8 warps per CTA
+// (two CTAs per SM where shared memory allows).  Warp w reads TMEM lane
+// quadrant q = w % 4 (samples 32q..32q+31 of a tile) and owns component
+// group h = w / 4 (K/2 components), so the two warps of a quadrant split the
+// components of the same 32 samples.  Tiles of 128 samples flow through
+//   phase A(t): load samples of tile t+2; features of tile t+1; issue GEMM
+//               2(t-1); wait GEMM 1(t); l_k of tile t (own components) with
+//               a local max and sum for the log-sum-exp
+//   phase B(t): issue GEMM 1(t+1); merge the two groups' (max, sum); w r_k;
+//               wait GEMM 2(t-1); statistics operand of tile t
+// Warps meet only in pairs (the two warps of a quadrant, on a named
+// barrier); operands reach the issuing lanes (warp 5: GEMM 1, warp 4: GEMM 2)
+// through mbarrier arrivals of all eight warps, and products complete through
+// tcgen05.commit mbarriers, so both products run while the CUDA cores work on
+// the neighbouring tiles.  TMEM holds two GEMM 1 accumulators (tiles t, t+1)
+// and the GEMM 2 accumulator of the current work unit; the BF16 features are
+// triple-buffered (GEMM 2 of tile t-1 and GEMM 1 of tile t+1 read them while
+// tile t+2's are written), the TF32 features double-buffered.  Every wait is
+// bounded; a timeout sets the workspace error flag and a CTA-wide abort flag
+// that ends every other wait, and the CTA drains and stops.
+constexpr int kTcGroups = 2;                   // component groups per sample
+constexpr int kTcWarps = 4 * kTcGroups;
+constexpr int kTcThreads = kTcWarps * 32;
+constexpr int kTcStatic = 4096;                // static shared memory of k_tc_estep (about 3 KB used)
+
 template <int K, int PREC>
 struct TcPlan {
-    static constexpr bool kTf32 = PREC != SDMM_PREC_TC_3XBF16;    // GEMM 1 in TF32
-    static constexpr bool kSplit1 = PREC != SDMM_PREC_TC_TF32;     // GEMM 1 split (3 products)
-    static constexpr int kE1 = kTf32 ? 4 : 2;                      // GEMM 1 element size
-    static constexpr int kNQ = 6 * K;                              // GEMM 1 columns
-    static constexpr int kPhi1 = kTile * kPhiPad * kE1;            // one GEMM 1 feature tile
-    static constexpr int kPhiB = kTile * kPhiPad * 2;              // one BF16 feature tile
-    static constexpr int kC1 = kNQ * kPhiPad * kE1;                // one coefficient tile
-    static constexpr int kA2 = kTile * kTile * 2;                  // one statistics operand
-    static constexpr int oPhi1h = 0;
-    static constexpr int oPhi1l = oPhi1h + kPhi1;
-    static constexpr int oPhiBh = oPhi1l + (kSplit1 ? kPhi1 : 0);
-    static constexpr int oPhiBl = oPhiBh + (kTf32 ? kPhiB : 0);    // BF16 copy only for TF32 GEMM 1
-    static constexpr int oC1h = oPhiBl + (kTf32 ? kPhiB : 0);
-    static constexpr int oC1l = oC1h + kC1;
-    static constexpr int oA2h = oC1l + (kSplit1 ? kC1 : 0);
-    static constexpr int oA2l = oA2h + kA2;
-    static constexpr int kBytes = oA2l + kA2;
-    static constexpr uint32_t kCols = (kNQ + 32 <= 128) ? 128 : 256;   // TMEM: D1 then D2
-    static constexpr uint32_t kD2 = kNQ;                                 // D2 column offset
+    static constexpr bool kTf32 = PREC != SDMM_PREC_TC_3XBF16;     // GEMM 1 in TF32
+    static constexpr bool kSplit1 = PREC != SDMM_PREC_TC_TF32;      // GEMM 1 split (3 products)
+    static constexpr int kE1 = kTf32 ? 4 : 2;                       // GEMM 1 element size
+    static constexpr int kNQ = 6 * K;                               // GEMM 1 columns
+    static constexpr int kKG = K / kTcGroups;                       // components per warp group
+    static constexpr int kM2 = (3 * K <= 64) ? 64 : 128;            // GEMM 2 rows (3K used)
+    static constexpr int kHalfB = kTile * kPhiPad * 2;              // BF16 feature tile (hi or lo)
+    static constexpr int kHalfT = kTile * kPhiPad * 4;              // TF32 feature tile (hi or lo)
+    static constexpr int kPhiB = 2 * kHalfB;                        // hi + lo
+    static constexpr int kPhiT = kTf32 ? (kSplit1 ? 2 : 1) * kHalfT : 0;
+    static constexpr int kHalfC = kNQ * kPhiPad * kE1;              // coefficient tile (hi or lo)
+    static constexpr int kC1 = (kSplit1 ? 2 : 1) * kHalfC;
+    static constexpr int kHalfA = kM2 * kTile * 2;                  // statistics operand (hi or lo)
+    static constexpr int kA2 = 2 * kHalfA;
+    static constexpr int kStage = 7 * kTile * 4;                    // one tile's samples (7 streams)
+    static constexpr int kRest = 2 * kPhiT + kC1 + kA2 + 3 * kStage;
+    static constexpr int kNB = 3 * kPhiB + kRest + kTcStatic <= 227 * 1024 ? 3 : 2;
+    static constexpr int oPhiB = 0;
+    static constexpr int oPhiT = kNB * kPhiB;
+    static constexpr int oC1 = oPhiT + 2 * kPhiT;
+    static constexpr int oA2 = oC1 + kC1;
+    static constexpr int oStage = oA2 + kA2;
+    static constexpr int kBytes = oStage + 3 * kStage;
+    static constexpr uint32_t kD2 = 2 * kNQ;                        // D1[0], D1[1], then D2
+    static constexpr uint32_t kCols = kD2 + 32 <= 256 ? 256 : 512;
+    static constexpr int kCtas = (kBytes + kTcStatic + 1024) * 2 <= 228 * 1024 && kCols * 2 <= 512 ? 2 : 1;
+    static_assert(kBytes + kTcStatic <= 227 * 1024, "shared memory plan too large");
+    static_assert(kTf32 || kNB == 3, "GEMM 1 in BF16 reads the triple-buffered features early");
+    static_assert(kD2 + 32 <= 512, "TMEM plan too large");
 };
 
 template <int E>
@@ -256,62 +301,80 @@ __device__ __forceinline__ void store_split(unsigned char* hi, unsigned char* lo
     }
 }
 
-// 8 consecutive BF16 values (hi and lo parts) as two 16-byte stores
-__device__ __forceinline__ void store8_split_bf16(unsigned char* hi, unsigned char* lo, uint32_t off,
-                                                  const float* v) {
-    uint32_t h[4], l[4];
+// hi and lo BF16 parts of n = 4 or 8 consecutive values (one 8- or 16-byte store
+// each), through 32-bit shared-window addresses
+template <int N>
+__device__ __forceinline__ void sts_split_bf16(uint32_t hi, uint32_t lo, const float* v) {
+    uint32_t h[N / 2], l[N / 2];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < N / 2; ++i) {
         const __nv_bfloat162 p = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
         const float2 pf = __bfloat1622float2(p);
         const __nv_bfloat162 q = __floats2bfloat162_rn(v[2 * i] - pf.x, v[2 * i + 1] - pf.y);
         h[i] = *reinterpret_cast<const uint32_t*>(&p);
         l[i] = *reinterpret_cast<const uint32_t*>(&q);
     }
-    *reinterpret_cast<uint4*>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
-    *reinterpret_cast<uint4*>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
+    if (N == 8) {
+        tc::sts128(hi, h[0], h[1], h[2], h[3]);
+        tc::sts128(lo, l[0], l[1], l[2], l[3]);
+    } else {
+        tc::sts64(hi, h[0], h[1]);
+        tc::sts64(lo, l[0], l[1]);
+    }
+}
+// hi (and, if LO, lo) TF32 parts of 4 consecutive values (16-byte stores)
+template <bool LO>
+__device__ __forceinline__ void sts_split_tf32(uint32_t hi, uint32_t lo, const float* v) {
+    float h[4], l[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        h[i] = tc::to_tf32(v[i]);
+        l[i] = tc::to_tf32(v[i] - h[i]);
+    }
+    tc::sts128(hi, __float_as_uint(h[0]), __float_as_uint(h[1]), __float_as_uint(h[2]), __float_as_uint(h[3]));
+    if (LO) tc::sts128(lo, __float_as_uint(l[0]), __float_as_uint(l[1]), __float_as_uint(l[2]), __float_as_uint(l[3]));
 }
 
+
+// A tile of up to 128 consecutive samples of one work unit.
+struct TcTile {
+    int64_t g0;         // first sample
+    int c, r;           // unit, region (r < 0: no valid sample)
+    int n;              // valid samples in the tile (0..128)
+    bool first, live;   // first tile of its unit; tile exists
+};
+
 template <int K, int PREC>
-__global__ void __launch_bounds__(128, 1)
-    k_tc_estep(WsHeader* __restrict__ ws, const int64_t* __restrict__ chunk_base,
-               const int32_t* __restrict__ chunk_region, const float* __restrict__ ctab,
-               const float* __restrict__ xref, int chunk, float* __restrict__ partial, int ps,
-               int write_ll) {
+__global__ void __launch_bounds__(kTcThreads, TcPlan<K, PREC>::kCtas)
+    k_tc_estep(WsHeader* __restrict__ ws, const int32_t* __restrict__ chunk_region,
+               const int64_t* __restrict__ units, const float* __restrict__ ctab,
+               const float* __restrict__ xref, float* __restrict__ partial, int ps, int write_ll) {
     using P = TcPlan<K, PREC>;
+    constexpr int KG = P::kKG;
+    constexpr int RPQ = P::kM2 / 4;                // GEMM 2 rows per TMEM lane quadrant
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ __align__(8) uint64_t bar1, bar2;
+    // bar1 / bar2: GEMM 1 / GEMM 2 completed; rdy1 / rdy2: their operands are
+    // in shared memory (one arrival per warp)
+    __shared__ __align__(8) uint64_t bar1, bar2, rdy1, rdy2;
     __shared__ uint32_t tmem_base;
-    __shared__ int s_c, s_abort;
-    __shared__ float s_red[2][4];
+    __shared__ int s_abort;
+    __shared__ float2 s_ml[kTcGroups][kTile];      // per group, per sample: (m, sum 2^(l_k log2 e - m))
+    __shared__ float s_xr[3][4][4];                // per staging slot and quadrant: region reference point
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int quad = warp & 3, grp = warp >> 2;
+    const int smp = quad * 32 + lane;              // sample (TMEM lane) of this thread
 
-    const float* __restrict__ px = ws->desc.p[0];
-    const float* __restrict__ py = ws->desc.p[1];
-    const float* __restrict__ pz = ws->desc.p[2];
-    const float* __restrict__ ox = ws->desc.p[3];
-    const float* __restrict__ oy = ws->desc.p[4];
-    const float* __restrict__ oz = ws->desc.p[5];
-    const float* __restrict__ pw = ws->desc.p[6];
-    const int64_t* __restrict__ off = ws->desc.offsets;
-    float* __restrict__ loglik = write_ll ? ws->desc.loglik : nullptr;
-    const int n_chunks = ws->n_chunks;
-    const int64_t R = ws->desc.R;
+    unsigned char* const sC1h = smem + P::oC1;
+    unsigned char* const sC1l = P::kSplit1 ? smem + P::oC1 + P::kHalfC : nullptr;
+    unsigned char* const sA2h = smem + P::oA2;
+    unsigned char* const sA2l = smem + P::oA2 + P::kHalfA;
+    auto phiB = [&](int b) { return smem + P::oPhiB + b * P::kPhiB; };
+    auto phiT = [&](int b) { return smem + P::oPhiT + b * P::kPhiT; };
 
-    unsigned char* sPhi1h = smem + P::oPhi1h;
-    unsigned char* sPhi1l = P::kSplit1 ? smem + P::oPhi1l : nullptr;
-    unsigned char* sPhiBh = P::kTf32 ? smem + P::oPhiBh : smem + P::oPhi1h;
-    unsigned char* sPhiBl = P::kTf32 ? smem + P::oPhiBl : smem + P::oPhi1l;
-    unsigned char* sC1h = smem + P::oC1h;
-    unsigned char* sC1l = P::kSplit1 ? smem + P::oC1l : nullptr;
-    unsigned char* sA2h = smem + P::oA2h;
-    unsigned char* sA2l = smem + P::oA2l;
-
-    // rows 3K..127 of the statistics operand stay zero
-    for (int e = tid * 16; e < P::kA2; e += kTile * 16) {
+    // rows 3K..M2-1 of the statistics operand only reach accumulator rows
+    // that are never read; they are cleared once all the same
+    for (int e = tid * 16; e < P::kA2; e += kTcThreads * 16)
         *reinterpret_cast<uint4*>(sA2h + e) = make_uint4(0u, 0u, 0u, 0u);
-        *reinterpret_cast<uint4*>(sA2l + e) = make_uint4(0u, 0u, 0u, 0u);
-    }
     if (warp == 0) {
         tc::tmem_alloc(&tmem_base, P::kCols);
         tc::tmem_relinquish();
@@ -319,6 +382,8 @@ __global__ void __launch_bounds__(128, 1)
     if (tid == 0) {
         tc::mbar_init(&bar1, 1);
         tc::mbar_init(&bar2, 1);
+        tc::mbar_init(&rdy1, kTcWarps);
+        tc::mbar_init(&rdy2, kTcWarps);
         tc::fence_mbar_init();
         s_abort = 0;
     }
@@ -327,237 +392,407 @@ __global__ void __launch_bounds__(128, 1)
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t td = tmem_base;
-    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
 
-    // descriptors: GEMM 1 (K-major features x K-major coefficients)
-    constexpr uint32_t g1_lbo = 128, g1_sbo = 8u * kPhiPad * P::kE1;
-    constexpr int g1_k = P::kTf32 ? 8 : 16;
-    constexpr int g1_steps = kPhiPad / g1_k;
-    const uint32_t idesc1 = tc::instr_desc(P::kTf32 ? 2 : 1, kTile, P::kNQ);
-    // GEMM 2 (MN-major statistics operand x MN-major BF16 features)
-    constexpr uint32_t a2_lbo = (kTile / 8) * 128, a2_sbo = 128;
-    constexpr uint32_t b2_lbo = (kPhiPad / 8) * 128, b2_sbo = 128;
-    const uint32_t idesc2 = tc::instr_desc(1, kTile, kPhiPad, 1, 1);
+    // ---- work units of this CTA: a static round robin over the CTAs, walked
+    // in the same order by every warp; the next unit's range is loaded one
+    // unit ahead
+    const int n_chunks = ws->n_chunks;
+    int uc = blockIdx.x, pr = -1;
+    int64_t ps0 = 0, pe = 0, uend = 0;   // next unit's start / end; end of the unit being walked
+    auto fetch = [&]() {
+        if (uc < n_chunks) {
+            pr = __ldg(chunk_region + uc);
+            ps0 = __ldg(units + 2 * uc);
+            pe = __ldg(units + 2 * uc + 1);
+        }
+    };
+    auto enter = [&](TcTile& tl) {
+        tl.live = uc < n_chunks;
+        if (!tl.live) return;
+        tl.c = uc;
+        tl.r = (pr >= 0 && pr < ws->desc.R) ? pr : -1;
+        tl.g0 = ps0;
+        uend = tl.r >= 0 ? pe : ps0;
+        tl.n = (int)min((int64_t)kTile, uend - ps0);
+        tl.first = true;
+        uc += gridDim.x;
+        fetch();
+    };
+    // only the walker furthest ahead calls this; the others copy its tiles
+    auto advance = [&](TcTile& tl) {
+        if (!tl.live) return;
+        if (tl.g0 + kTile < uend) {
+            tl.g0 += kTile;
+            tl.n = (int)min((int64_t)kTile, uend - tl.g0);
+            tl.first = false;
+        } else {
+            enter(tl);
+        }
+    };
+    fetch();
 
-    uint32_t ph1 = 0, ph2 = 0;
-    bool g1_pending = false, g2_pending = false;
+    // ---- bounded waits; a timeout anywhere stops every wait of the CTA
     bool aborted = false;
-    int prev_r = -1;
-    float xr0 = 0.f, xr1 = 0.f, xr2 = 0.f;
-
-    // bounded wait for the next completion of `bar`; on success the group is
-    // no longer pending, on timeout it stays pending (drained before exit)
-    auto wait_or_abort = [&](uint64_t* bar, uint32_t& ph, bool& pending) -> bool {
-        const bool ok = tc::mbar_wait_bounded(bar, ph, kTcWaitNs);
-        if (ok) {
+    auto wait_bar = [&](uint64_t* b, uint32_t parity) -> bool {
+        if (tc::mbar_try_wait(b, parity)) return true;
+        const uint64_t t0 = tc::global_ns();
+        while (true) {
+            if (tc::mbar_try_wait_hint(b, parity, 100000u)) return true;   // suspends, no spinning
+            if (*reinterpret_cast<volatile int*>(&s_abort)) return false;
+            if (tc::global_ns() - t0 > kTcWaitNs) {
+                *reinterpret_cast<volatile int*>(&s_abort) = 1;
+                atomicExch(&ws->err, 1);
+                return false;
+            }
+        }
+    };
+    uint32_t ph1 = 0, ph2 = 0, pr1 = 0, pr2 = 0;
+    bool g1_pending = false, g2_pending = false;
+    auto wait_mma = [&](uint64_t* b, uint32_t& ph, bool& pending) {
+        if (!pending) return;
+        if (wait_bar(b, ph)) {
             ph ^= 1u;
             pending = false;
-        } else if (tid == 0) {
-            s_abort = 1;
-            atomicExch(&ws->err, 1);
+        } else {
+            aborted = true;
         }
-        return ok;
+        tc::fence_after_sync();
+    };
+    // this warp's shared-memory writes and TMEM reads are complete: one arrival on b
+    auto signal = [&](uint64_t* b) {
+        tc::fence_smem_to_async();
+        tc::fence_before_sync();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(b);
+    };
+    // barrier of the two warps of a quadrant (they share their 32 samples);
+    // it also makes the abort decision common to both
+    auto sync_pair = [&]() {
+        tc::fence_before_sync();
+        const bool p = aborted || *reinterpret_cast<volatile int*>(&s_abort);
+        switch (quad) {                          // barrier ids 1..4, one per quadrant
+            case 0: aborted = tc::bar_red_or<1, 64>(p); break;
+            case 1: aborted = tc::bar_red_or<2, 64>(p); break;
+            case 2: aborted = tc::bar_red_or<3, 64>(p); break;
+            default: aborted = tc::bar_red_or<4, 64>(p); break;
+        }
+        tc::fence_after_sync();
     };
 
-    for (;;) {
-        if (tid == 0) s_c = atomicAdd(&ws->queue, 1);
-        __syncthreads();
-        const int c = s_c;
-        if (c >= n_chunks || s_abort) break;
-        const int r = chunk_region[c];
-        if (r < 0 || r >= R) {
-            __syncthreads();
-            continue;
-        }
-        const int64_t start = off[r] + ((int64_t)c - chunk_base[r]) * chunk;
-        const int64_t end = min(start + (int64_t)chunk, off[r + 1]);
-        if (r != prev_r) {
-            // coefficient tile of this region (no MMA reads it now: GEMM 1 of
-            // the last tile has completed and GEMM 2 does not use it)
-            prev_r = r;
-            const float* cr = ctab + (int64_t)r * K * 6 * kPhiPad;
-            for (int e = tid; e < P::kNQ * kPhiPad; e += kTile) {
-                const int row = e / kPhiPad, f = e % kPhiPad;
-                store_split<P::kE1>(sC1h, sC1l, tc::kmajor_offset(row, f, kPhiPad, P::kE1), __ldg(cr + e));
-            }
-            xr0 = __ldg(xref + r * 4 + 0);
-            xr1 = __ldg(xref + r * 4 + 1);
-            xr2 = __ldg(xref + r * 4 + 2);
-        }
-        float wsum = 0.f, wll = 0.f;
-        bool first = true;
-        for (int64_t g0 = start; g0 < end; g0 += kTile) {
-            // statistics product of the previous tile must be done with Phi and A2
-            if (g2_pending) {
-                if (!wait_or_abort(&bar2, ph2, g2_pending)) aborted = true;
-                tc::fence_after_sync();
-            }
-            if (__syncthreads_or(aborted)) { aborted = true; break; }
-            // ---- features of sample g0 + tid (zero weight past the end)
-            const int64_t i = g0 + tid;
-            const bool valid = i < end;
-            float x0 = 0.f, x1 = 0.f, x2 = 0.f, w0 = 0.f, w1 = 0.f, w2 = 1.f, wt = 0.f;
-            if (valid) {
-                x0 = __ldg(px + i) - xr0;
-                x1 = __ldg(py + i) - xr1;
-                x2 = __ldg(pz + i) - xr2;
-                w0 = __ldg(ox + i);
-                w1 = __ldg(oy + i);
-                w2 = __ldg(oz + i);
-                wt = __ldg(pw + i);
-            }
-            float phi[kPhiPad] = {1.f, x0, x1, x2, x0 * x0, x0 * x1, x0 * x2, x1 * x1, x1 * x2, x2 * x2,
-                                  w0, w1, w2, w0 * x0, w0 * x1, w0 * x2, w1 * x0, w1 * x1, w1 * x2,
-                                  w2 * x0, w2 * x1, w2 * x2, w0 * w0, w0 * w1, w0 * w2, w1 * w1, w1 * w2,
-                                  w2 * w2, 0.f, 0.f, 0.f, 0.f};
+    // ---- MMA issue: one lane of warp 5 (GEMM 1) and of warp 4 (GEMM 2),
+    // once every warp has signalled the operands
+    constexpr uint32_t g1_sbo = 8u * kPhiPad * P::kE1;
+    constexpr int g1_k = P::kTf32 ? 8 : 16;
+    constexpr uint32_t a2_lbo = (P::kM2 / 8) * 128, b2_lbo = (kPhiPad / 8) * 128;
+    // GEMM 1: K-major features x K-major coefficients (M = 128, N = 6K) into D1[t & 1]
+    auto issue_g1 = [&](int t) {
+        const bool ok = wait_bar(&rdy1, pr1);
+        pr1 ^= 1u;
+        tc::fence_after_sync();
+        if (ok && lane == 0) {
+            const uint64_t a_h = P::kTf32 ? tc::smem_desc(tc::smem_addr(phiT(t & 1)), 128, g1_sbo)
+                                          : tc::smem_desc(tc::smem_addr(phiB(t % P::kNB)), 128, g1_sbo);
+            const uint64_t a_l = tc::desc_add(a_h, P::kTf32 ? P::kHalfT : P::kHalfB);
+            const uint32_t d = td + (uint32_t)(t & 1) * P::kNQ;
+            const uint32_t idesc1 = tc::instr_desc(P::kTf32 ? 2 : 1, kTile, P::kNQ);
+            const uint64_t dC1h = tc::smem_desc(tc::smem_addr(sC1h), 128, g1_sbo);
+            const uint64_t dC1l = tc::desc_add(dC1h, P::kHalfC);
+            int n = 0;
 #pragma unroll
-            for (int fb = 0; fb < kPhiPad; fb += 8) {
-                store8_split_bf16(sPhiBh, sPhiBl, tc::kmajor_offset(tid, fb, kPhiPad, 2), phi + fb);
-                if (P::kTf32) {
+            for (int pass = 0; pass < (P::kSplit1 ? 3 : 1); ++pass) {
+                const uint64_t a = pass == 2 ? a_l : a_h;
+                const uint64_t b = pass == 1 ? dC1l : dC1h;
 #pragma unroll
-                    for (int f = fb; f < fb + 8; ++f)
-                        store_split<4>(sPhi1h, sPhi1l, tc::kmajor_offset(tid, f, kPhiPad, 4), phi[f]);
+                for (int s = 0; s < kPhiPad / g1_k; ++s, ++n) {
+                    if (P::kTf32) tc::mma_tf32(d, tc::desc_add(a, s * 256), tc::desc_add(b, s * 256), idesc1, n > 0);
+                    else tc::mma_f16(d, tc::desc_add(a, s * 256), tc::desc_add(b, s * 256), idesc1, n > 0);
                 }
             }
-            tc::fence_smem_to_async();
-            tc::fence_before_sync();
-            __syncthreads();
-            tc::fence_after_sync();
-            // ---- GEMM 1
-            if (tid == 0) {
-                const uint32_t a_h = tc::smem_addr(sPhi1h), b_h = tc::smem_addr(sC1h);
-                const uint32_t a_l = P::kSplit1 ? tc::smem_addr(sPhi1l) : 0u;
-                const uint32_t b_l = P::kSplit1 ? tc::smem_addr(sC1l) : 0u;
-                const int passes = P::kSplit1 ? 3 : 1;
-                int n = 0;
-                for (int pass = 0; pass < passes; ++pass) {
-                    const uint32_t a = pass == 2 ? a_l : a_h;
-                    const uint32_t b = pass == 1 ? b_l : b_h;
-                    for (int s = 0; s < g1_steps; ++s, ++n) {
-                        const uint64_t ad = tc::smem_desc(a + s * 256, g1_lbo, g1_sbo);
-                        const uint64_t bd = tc::smem_desc(b + s * 256, g1_lbo, g1_sbo);
-                        if (P::kTf32) tc::mma_tf32(td, ad, bd, idesc1, n > 0);
-                        else tc::mma_f16(td, ad, bd, idesc1, n > 0);
-                    }
-                }
-                tc::mma_commit(&bar1);
-            }
-            g1_pending = true;
-            if (!wait_or_abort(&bar1, ph1, g1_pending)) aborted = true;
-            tc::fence_after_sync();
-            if (__syncthreads_or(aborted)) { aborted = true; break; }
-            // ---- per-sample epilogue: theta, g, l_k, log-sum-exp, w r_k
-            float lk[K], gk[K];
-#pragma unroll
-            for (int kb = 0; kb < K; kb += 8) {
-                float v[48];
-                tc::tmem_ld16(td + lane_base + 6 * kb, v);
-                tc::tmem_ld16(td + lane_base + 6 * kb + 16, v + 16);
-                tc::tmem_ld16(td + lane_base + 6 * kb + 32, v + 32);
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const float u = v[6 * j], vv = v[6 * j + 1], cz = v[6 * j + 2];
-                    const float s2 = u * u + vv * vv;
-                    const float rs = rsqrtf(s2);
-                    const float th = atan2_pos(s2 * rs, cz);
-                    const bool off_centre = s2 > 0.f;
-                    const float g = off_centre ? th * rs : 1.f;
-                    float l = v[6 * j + 3] + g * (v[6 * j + 4] + g * v[6 * j + 5]);
-                    if (!off_centre && cz < 0.f) l = -INFINITY;
-                    lk[kb + j] = l;
-                    gk[kb + j] = g;
-                }
-            }
-            float mx = lk[0];
-#pragma unroll
-            for (int k = 1; k < K; ++k) mx = fmaxf(mx, lk[k]);
-            float se = 0.f;
-#pragma unroll
-            for (int k = 0; k < K; ++k) {
-                lk[k] = (mx == -INFINITY) ? 0.f : __expf(lk[k] - mx);
-                se += lk[k];
-            }
-            const float scale = se > 0.f ? wt / se : 0.f;
-            const float li = se > 0.f ? mx + __logf(se) : -INFINITY;
-            wsum += wt;
-            wll += (wt > 0.f) ? wt * li : 0.f;
-            if (loglik != nullptr && valid) loglik[i] = li;
-            // statistics operand: rows k (w r), K + k (w r g), 2K + k (w r g^2)
-#pragma unroll
-            for (int kb = 0; kb < K; kb += 8) {
-                float a8[8], b8[8], c8[8];
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const float wr = lk[kb + j] * scale;
-                    a8[j] = wr;
-                    b8[j] = wr * gk[kb + j];
-                    c8[j] = b8[j] * gk[kb + j];
-                }
-                store8_split_bf16(sA2h, sA2l, tc::mnmajor_offset(kb, tid, kTile), a8);
-                store8_split_bf16(sA2h, sA2l, tc::mnmajor_offset(K + kb, tid, kTile), b8);
-                store8_split_bf16(sA2h, sA2l, tc::mnmajor_offset(2 * K + kb, tid, kTile), c8);
-            }
-            tc::fence_smem_to_async();
-            tc::fence_before_sync();
-            __syncthreads();
-            tc::fence_after_sync();
-            // ---- GEMM 2 (accumulates over the work unit)
-            if (tid == 0) {
-                const uint32_t ah = tc::smem_addr(sA2h), al = tc::smem_addr(sA2l);
-                const uint32_t bh = tc::smem_addr(sPhiBh), bl = tc::smem_addr(sPhiBl);
-                int n = 0;
-                for (int pass = 0; pass < 3; ++pass) {
-                    const uint32_t a = pass == 2 ? al : ah;
-                    const uint32_t b = pass == 1 ? bl : bh;
-                    for (int s = 0; s < kTile / 16; ++s, ++n) {
-                        const uint64_t ad = tc::smem_desc(a + s * 2 * a2_lbo, a2_lbo, a2_sbo);
-                        const uint64_t bd = tc::smem_desc(b + s * 2 * b2_lbo, b2_lbo, b2_sbo);
-                        tc::mma_f16(td + P::kD2, ad, bd, idesc2, (n > 0 || !first) ? 1u : 0u);
-                    }
-                }
-                tc::mma_commit(&bar2);
-            }
-            g2_pending = true;
-            first = false;
+            tc::mma_commit(&bar1);
         }
-        if (__syncthreads_or(aborted)) { aborted = true; break; }
-        // ---- unit statistics: rows 0..3K-1 of D2, plus W and sum w l
-        if (g2_pending) {
-            if (!wait_or_abort(&bar2, ph2, g2_pending)) aborted = true;
-            tc::fence_after_sync();
-        }
-        if (__syncthreads_or(aborted)) { aborted = true; break; }
+        __syncwarp();
+        if (!ok) aborted = true;
+    };
+    // GEMM 2: MN-major statistics operand (M = M2) x MN-major BF16 features
+    // (N = 32), accumulated over the work unit
+    auto issue_g2 = [&](int t, bool restart) {
+        const bool ok = wait_bar(&rdy2, pr2);
+        pr2 ^= 1u;
+        tc::fence_after_sync();
+        if (ok && lane == 0) {
+            const uint64_t bh = tc::smem_desc(tc::smem_addr(phiB(t % P::kNB)), b2_lbo, 128);
+            const uint64_t bl = tc::desc_add(bh, P::kHalfB);
+            const uint32_t idesc2 = tc::instr_desc(1, P::kM2, kPhiPad, 1, 1);
+            const uint64_t dA2h = tc::smem_desc(tc::smem_addr(sA2h), a2_lbo, 128);
+            const uint64_t dA2l = tc::desc_add(dA2h, P::kHalfA);
+            int n = 0;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
-            wll += __shfl_xor_sync(0xffffffffu, wll, o);
+            for (int pass = 0; pass < 3; ++pass) {
+                const uint64_t a = pass == 2 ? dA2l : dA2h;
+                const uint64_t b = pass == 1 ? bl : bh;
+#pragma unroll
+                for (int s = 0; s < kTile / 16; ++s, ++n)
+                    tc::mma_f16(td + P::kD2, tc::desc_add(a, s * 2 * a2_lbo), tc::desc_add(b, s * 2 * b2_lbo),
+                                idesc2, (n > 0 || !restart) ? 1u : 0u);
+            }
+            tc::mma_commit(&bar2);
         }
-        if (lane == 0) {
-            s_red[0][warp] = wsum;
-            s_red[1][warp] = wll;
+        __syncwarp();
+        if (!ok) aborted = true;
+    };
+
+    float* __restrict__ loglik = write_ll ? ws->desc.loglik : nullptr;
+    // Per-thread shared-window addresses of the hot loop (32-bit, fixed for
+    // the whole kernel; buffers and slots are added as byte offsets)
+    const uint32_t sbase = tc::smem_addr(smem);
+    const uint32_t aPhiB = sbase + P::oPhiB + tc::kmajor_offset(smp, 16 * grp, kPhiPad, 2);   // +128: features 8..15
+    const uint32_t aPhiT = sbase + P::oPhiT + tc::kmajor_offset(smp, 16 * grp, kPhiPad, 4);   // +128 per 4 features
+    const uint32_t aA2 = sbase + P::oA2 + tc::mnmajor_offset(3 * KG * grp, smp, P::kM2);     // +128 per 8 rows
+    const uint32_t aStage = sbase + P::oStage + smp * 4;   // + slot 7*128*4 + stream 128*4
+    const uint32_t aML = tc::smem_addr(&s_ml[0][smp]);     // + group 128*8
+    const uint32_t aXr = tc::smem_addr(&s_xr[0][quad][0]); // + slot 64
+    constexpr uint32_t kSlot = 7 * kTile * 4, kStream = kTile * 4;
+    // sample staging ring: slot s holds a tile's 7 streams [7][128] and its
+    // region's reference point.  The two warps of a quadrant copy streams 0-3
+    // (group 0, plus the reference point) and 4-6 (group 1) of their 32
+    // samples; every thread waits for its own copies before the pair barrier
+    // that ends phase B, after which the slot is read (one phase later).
+    auto load = [&](const TcTile& tl, int slot) {
+        const bool valid = tl.live && smp < tl.n;
+        const int64_t i = valid ? tl.g0 + smp : 0;
+        const uint32_t dst = aStage + slot * kSlot;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int q = 4 * grp + j;
+            if (q < 7) tc::cp_async4s(dst + q * kStream, ws->desc.p[q] + i, valid);
         }
-        if (warp * 32 < 3 * K) {
+        if (grp == 0 && lane < 3) {
+            const bool rv = tl.live && tl.r >= 0;
+            tc::cp_async4s(aXr + slot * 64 + lane * 4, xref + (rv ? tl.r * 4 + lane : 0), rv);
+        }
+        tc::cp_async_commit();
+    };
+    auto sample = [&](int slot, int q) { return tc::lds32(aStage + slot * kSlot + q * kStream); };
+    // this group's 16 of the 32 features phi = [1, x', vech(x'x'), w, w (x) x', vech(ww)]
+    auto features = [&](int slot, float* f) {
+        const uint32_t xr = aXr + slot * 64;
+        const float x0 = sample(slot, 0) - tc::lds32(xr), x1 = sample(slot, 1) - tc::lds32(xr + 4),
+                    x2 = sample(slot, 2) - tc::lds32(xr + 8);
+        const float w0 = sample(slot, 3), w1 = sample(slot, 4), w2 = sample(slot, 5);
+        if (grp == 0) {
+            f[0] = 1.f; f[1] = x0; f[2] = x1; f[3] = x2;
+            f[4] = x0 * x0; f[5] = x0 * x1; f[6] = x0 * x2; f[7] = x1 * x1;
+            f[8] = x1 * x2; f[9] = x2 * x2; f[10] = w0; f[11] = w1;
+            f[12] = w2; f[13] = w0 * x0; f[14] = w0 * x1; f[15] = w0 * x2;
+        } else {
+            f[0] = w1 * x0; f[1] = w1 * x1; f[2] = w1 * x2; f[3] = w2 * x0;
+            f[4] = w2 * x1; f[5] = w2 * x2; f[6] = w0 * w0; f[7] = w0 * w1;
+            f[8] = w0 * w2; f[9] = w1 * w1; f[10] = w1 * w2; f[11] = w2 * w2;
+            f[12] = 0.f; f[13] = 0.f; f[14] = 0.f; f[15] = 0.f;
+        }
+    };
+    auto store_b = [&](int b, const float* f) {
+        const uint32_t a = aPhiB + b * P::kPhiB;
+        sts_split_bf16<8>(a, a + P::kHalfB, f);
+        sts_split_bf16<8>(a + 128, a + 128 + P::kHalfB, f + 8);
+    };
+    auto store_t = [&](int b, const float* f) {
+        const uint32_t a = aPhiT + b * P::kPhiT;
+#pragma unroll
+        for (int h = 0; h < 4; ++h) sts_split_tf32<P::kSplit1>(a + 128 * h, a + 128 * h + P::kHalfT, f + 4 * h);
+    };
+    auto load_c1 = [&](int r) {
+        const float* cr = ctab + (int64_t)r * K * 6 * kPhiPad;
+        for (int e = tid; e < P::kNQ * kPhiPad; e += kTcThreads) {
+            const int row = e / kPhiPad, f = e % kPhiPad;
+            store_split<P::kE1>(sC1h, sC1l, tc::kmajor_offset(row, f, kPhiPad, P::kE1), __ldg(cr + e));
+        }
+    };
+    // unit statistics out of D2 (rows (h, j, kk) -> partial row j K + h KG + kk)
+    // and, per quadrant, the unit's W and sum w l (summed by the M-step)
+    float accW = 0.f, accL = 0.f;
+    auto flush = [&](int c) {
+        if (grp == 1 && quad * RPQ < 3 * K) {
             float d[32];
             tc::tmem_ld16(td + lane_base + P::kD2, d);
             tc::tmem_ld16(td + lane_base + P::kD2 + 16, d + 16);
-            if (tid < 3 * K) {
-                float* out = partial + (int64_t)c * ps + tid * kFeat;
+            const int m = quad * RPQ + lane;
+            if (lane < RPQ && m < 3 * K) {
+                const int h = m / (3 * KG), j = (m % (3 * KG)) / KG, kk = m % KG;
+                float* out = partial + (int64_t)c * ps + (j * K + h * KG + kk) * kFeat;
 #pragma unroll
                 for (int f = 0; f < kFeat; ++f) out[f] = d[f];
             }
         }
-        tc::fence_before_sync();
-        __syncthreads();
-        if (tid == 0) {
-            partial[(int64_t)c * ps + 3 * K * kFeat] = s_red[0][0] + s_red[0][1] + s_red[0][2] + s_red[0][3];
-            partial[(int64_t)c * ps + 3 * K * kFeat + 1] = s_red[1][0] + s_red[1][1] + s_red[1][2] + s_red[1][3];
+        if (grp == 0) {
+            float a = accW, b = accL;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                a += __shfl_xor_sync(0xffffffffu, a, o);
+                b += __shfl_xor_sync(0xffffffffu, b, o);
+            }
+            if (lane == 0) {
+                partial[(int64_t)c * ps + 3 * K * kFeat + quad] = a;
+                partial[(int64_t)c * ps + 3 * K * kFeat + 4 + quad] = b;
+            }
+            accW = accL = 0.f;
         }
+    };
+
+    // ---- prologue: tile 0 through its GEMM 1
+    TcTile cur, nxt, nn;
+    enter(cur);
+    if (cur.live) {
+        load(cur, 0);
+        nxt = cur;
+        advance(nxt);
+        load(nxt, 1);
+        if (cur.r >= 0) load_c1(cur.r);
+        float f[16];
+        tc::cp_async_wait<0>();                  // tiles 0 and 1
+        sync_pair();
+        features(0, f);
+        store_b(0, f);
+        if (P::kTf32) store_t(0, f);
+        signal(&rdy1);
+        if (warp == 5) issue_g1(0);
+        g1_pending = true;
     }
-    // drain every product still in flight (after a timeout) before freeing TMEM
-    if (g1_pending && !tc::mbar_wait_bounded(&bar1, ph1, kTcWaitNs) && tid == 0) atomicExch(&ws->err, 1);
-    if (g2_pending && !tc::mbar_wait_bounded(&bar2, ph2, kTcWaitNs) && tid == 0) atomicExch(&ws->err, 1);
+    int t = 0, prev_c = -1;
+    int s0 = 0, s1 = 1, s2 = 2;                   // staging slots of tiles t, t+1, t+2
+    int b1 = 1 % P::kNB;                          // BF16 feature buffer of tile t+1
+    bool a2_ready = false, a2_restart = false;
+    while (cur.live && !aborted) {
+        // ---- phase A
+        nn = nxt;
+        advance(nn);
+        load(nn, s2);                             // waited for at the end of phase B
+        float f[16];
+        if (nxt.live) {
+            features(s1, f);
+            if (!P::kTf32) store_b(b1, f);
+            else store_t((t + 1) & 1, f);
+        }
+        if (a2_ready) {                           // GEMM 2 of the previous tile
+            if (warp == 4) issue_g2(t - 1, a2_restart);
+            g2_pending = true;
+            a2_ready = false;
+        }
+        wait_mma(&bar1, ph1, g1_pending);         // GEMM 1(t)
+        if (nxt.live && nxt.r >= 0 && nxt.r != cur.r) load_c1(nxt.r);
+        // l_k log2(e) of this group's components: TMEM columns 6 (h KG + j) + (u, v, c, T0, T1, T2)
+        float lk[KG], gk[KG];
+        {
+            auto eval1 = [&](const float* q, int j) {
+                const float u = q[0], vv = q[1], cz = q[2];
+                const float s2 = u * u + vv * vv;
+                const float rs = tc::rsqrt_approx(s2);
+                const float th = atan2_pos(s2 * rs, cz);
+                const bool off_centre = s2 > 0.f;
+                const float g = off_centre ? th * rs : 1.f;
+                float l = q[3] + g * (q[4] + g * q[5]);
+                if (!off_centre && cz < 0.f) l = -INFINITY;
+                lk[j] = l;
+                gk[j] = g;
+            };
+            // chunks of 8 components = 48 columns, starting on a multiple of 16
+#pragma unroll
+            for (int cb = 0; cb < KG; cb += 8) {
+                const uint32_t col = (uint32_t)(t & 1) * P::kNQ + 6u * (KG * grp + cb);
+                float v[48];
+                tc::tmem_ld16(td + lane_base + col, v);
+                tc::tmem_ld16(td + lane_base + col + 16, v + 16);
+                tc::tmem_ld16(td + lane_base + col + 32, v + 32);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) eval1(v + 6 * j, cb + j);
+            }
+        }
+        float mg = lk[0];
+#pragma unroll
+        for (int j = 1; j < KG; ++j) mg = fmaxf(mg, lk[j]);
+        float sg = 0.f;
+#pragma unroll
+        for (int j = 0; j < KG; ++j) {
+            lk[j] = mg > -INFINITY ? tc::ex2_approx(lk[j] - mg) : 0.f;   // lk now holds 2^(l_k - m_h)
+            sg += lk[j];
+        }
+        tc::sts64(aML + grp * kTile * 8, __float_as_uint(mg), __float_as_uint(sg));
+        if (P::kTf32 && nxt.live) {
+            if (P::kNB == 2) wait_mma(&bar2, ph2, g2_pending);   // GEMM 2(t-1) reads this buffer
+            features(s1, f);
+            store_b(b1, f);
+        }
+        if (nxt.live) signal(&rdy1);
+        sync_pair();
+        if (aborted) break;
+        // ---- phase B
+        if (nxt.live) {
+            if (warp == 5) issue_g1(t + 1);
+            g1_pending = true;
+        }
+        const float2 m0 = tc::lds64(aML), m1 = tc::lds64(aML + kTile * 8);
+        const float M = fmaxf(m0.x, m1.x);
+        const float e0 = m0.x > -INFINITY ? tc::ex2_approx(m0.x - M) : 0.f;
+        const float e1 = m1.x > -INFINITY ? tc::ex2_approx(m1.x - M) : 0.f;
+        const float se = m0.y * e0 + m1.y * e1;
+        const float own = grp == 0 ? e0 : e1;
+        const int64_t si = cur.g0 + smp;
+        const bool valid = smp < cur.n;
+        const float wt = sample(s0, 6);
+        const bool ok = valid && se > 0.f;
+        const float scale = ok ? wt * own * tc::rcp_approx(se) : 0.f;
+        const float li = se > 0.f ? kLn2 * (M + tc::lg2_approx(se)) : -INFINITY;   // natural log
+        if (grp == 0 && valid && loglik != nullptr) loglik[si] = li;
+        wait_mma(&bar2, ph2, g2_pending);         // GEMM 2(t-1)
+        if (cur.first && prev_c >= 0) flush(prev_c);   // tile t-1 closed unit prev_c
+        if (grp == 0 && valid) {
+            accW += wt;
+            accL += wt > 0.f ? wt * li : 0.f;
+        }
+        // rows of this group: (h, j, kk) -> 3 KG h + KG j + kk, j = 0: w r, 1: w r g, 2: w r g^2
+        {
+            float a[3 * KG];
+#pragma unroll
+            for (int j = 0; j < KG; ++j) {
+                const float wr = ok ? lk[j] * scale : 0.f;
+                a[j] = wr;
+                a[KG + j] = wr * gk[j];
+                a[2 * KG + j] = wr * gk[j] * gk[j];
+            }
+#pragma unroll
+            for (int b = 0; b < 3 * KG; b += 8) sts_split_bf16<8>(aA2 + b * 16, aA2 + b * 16 + P::kHalfA, a + b);
+        }
+        signal(&rdy2);
+        a2_ready = true;
+        a2_restart = cur.first;
+        tc::cp_async_wait<0>();                  // tile t+2's samples, read after the barrier
+        sync_pair();
+        if (aborted) break;
+        prev_c = cur.c;
+        cur = nxt;
+        nxt = nn;
+        ++t;
+        const int sr = s0;
+        s0 = s1;
+        s1 = s2;
+        s2 = sr;
+        b1 = b1 + 1 == P::kNB ? 0 : b1 + 1;
+    }
+    // ---- the last tile's GEMM 2, then its unit
+    if (!aborted && a2_ready) {
+        if (warp == 4) issue_g2(t - 1, a2_restart);
+        g2_pending = true;
+        wait_mma(&bar2, ph2, g2_pending);
+        flush(prev_c);
+    }
+    tc::cp_async_wait<0>();
+    // drain every product still in flight (after a timeout) before TMEM is freed
+    if (g1_pending && !tc::mbar_wait_bounded(&bar1, ph1, kTcWaitNs) && lane == 0) atomicExch(&ws->err, 1);
+    if (g2_pending && !tc::mbar_wait_bounded(&bar2, ph2, kTcWaitNs) && lane == 0) atomicExch(&ws->err, 1);
     tc::fence_before_sync();
     __syncthreads();
+    tc::fence_after_sync();
     if (warp == 0) tc::tmem_dealloc(td, P::kCols);
 }
 
@@ -572,11 +807,13 @@ size_t tc_smem_bytes(int K, int prec) {
 }
 
 int tc_ctas_per_sm(int K, int prec) {
-    const size_t b = tc_smem_bytes(K, prec) + 2048;            // + static shared memory
-    const uint32_t cols = (6 * K + 32 <= 128) ? 128 : 256;
-    int n = (int)((227u * 1024u) / b);
-    n = n < (int)(512 / cols) ? n : (int)(512 / cols);
-    return n < 1 ? 1 : n;
+#define SDMM_TC_CTAS(KK, PP) \
+    if (K == KK && prec == PP) return TcPlan<KK, PP>::kCtas;
+    SDMM_TC_CTAS(16, SDMM_PREC_TC_3XBF16) SDMM_TC_CTAS(16, SDMM_PREC_TC_TF32)
+    SDMM_TC_CTAS(16, SDMM_PREC_TC_3XTF32) SDMM_TC_CTAS(32, SDMM_PREC_TC_3XBF16)
+    SDMM_TC_CTAS(32, SDMM_PREC_TC_TF32) SDMM_TC_CTAS(32, SDMM_PREC_TC_3XTF32)
+#undef SDMM_TC_CTAS
+    return 1;
 }
 
 cudaError_t launch_tc_prepare(cudaStream_t s, int K, int64_t R, const sdmm_state& st, float* ctab,
@@ -587,22 +824,21 @@ cudaError_t launch_tc_prepare(cudaStream_t s, int K, int64_t R, const sdmm_state
 }
 
 template <int K, int PREC>
-static cudaError_t launch_tc_estep_t(cudaStream_t s, int grid, WsHeader* ws, const int64_t* cb,
-                                     const int32_t* cr, const float* ctab, const float* xref, int chunk,
+static cudaError_t launch_tc_estep_t(cudaStream_t s, int grid, WsHeader* ws, const int32_t* cr,
+                                     const int64_t* units, const float* ctab, const float* xref,
                                      float* partial, int ps, int write_ll) {
     const int bytes = TcPlan<K, PREC>::kBytes;
     cudaError_t e = cudaFuncSetAttribute(k_tc_estep<K, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
-    k_tc_estep<K, PREC><<<grid, kTile, bytes, s>>>(ws, cb, cr, ctab, xref, chunk, partial, ps, write_ll);
+    k_tc_estep<K, PREC><<<grid, kTcThreads, bytes, s>>>(ws, cr, units, ctab, xref, partial, ps, write_ll);
     return cudaGetLastError();
 }
 
-cudaError_t launch_tc_estep(cudaStream_t s, int K, int prec, int grid, WsHeader* ws, const int64_t* cb,
-                            const int32_t* cr, const float* ctab, const float* xref, int chunk,
-                            float* partial, int ps, int write_ll) {
-#define SDMM_TC_CASE(KK, PP)                                                                      \
-    if (K == KK && prec == PP)                                                                    \
-        return launch_tc_estep_t<KK, PP>(s, grid, ws, cb, cr, ctab, xref, chunk, partial, ps, write_ll);
+cudaError_t launch_tc_estep(cudaStream_t s, int K, int prec, int grid, WsHeader* ws, const int32_t* cr,
+                            const int64_t* units, const float* ctab, const float* xref, float* partial,
+                            int ps, int write_ll) {
+#define SDMM_TC_CASE(KK, PP) \
+    if (K == KK && prec == PP) return launch_tc_estep_t<KK, PP>(s, grid, ws, cr, units, ctab, xref, partial, ps, write_ll);
     SDMM_TC_CASE(16, SDMM_PREC_TC_3XBF16) SDMM_TC_CASE(16, SDMM_PREC_TC_TF32)
     SDMM_TC_CASE(16, SDMM_PREC_TC_3XTF32) SDMM_TC_CASE(32, SDMM_PREC_TC_3XBF16)
     SDMM_TC_CASE(32, SDMM_PREC_TC_TF32) SDMM_TC_CASE(32, SDMM_PREC_TC_3XTF32)
