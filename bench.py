@@ -222,7 +222,7 @@ def run_gpu(args):
                for r in range(ROUNDS)]
     _, h, _ = syn.region_grid(R_REGIONS)
     prec = {"fp32": api.PREC_FP32, "3xbf16": api.PREC_TC_3XBF16, "tf32": api.PREC_TC_TF32,
-            "3xtf32": api.PREC_TC_3XTF32}[args.precision]
+            "3xtf32": api.PREC_TC_3XTF32, "6xbf16": api.PREC_TC_6XBF16}[args.precision]
     cfg = api.config(K_COMP, precision=prec)
     st = api.MixtureState(R_REGIONS, K_COMP, device=dev)
     api.init_regions(cfg, batches[0], torch.from_numpy(h.astype(np.float64)).to(dev),
@@ -356,7 +356,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--regions", type=int, default=4096, help="regions of the fit workload")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "3xbf16", "tf32", "3xtf32"],
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "3xbf16", "tf32", "3xtf32", "6xbf16"],
                     help="E-step arithmetic: FP32 SIMT or a tensor-core contraction form")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()

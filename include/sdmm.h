@@ -81,7 +81,7 @@ enum { SDMM_ETA_ROBBINS_MONRO = 0, SDMM_ETA_ONE = 1 };
 enum { SDMM_DENSITY_TANGENT = 0, SDMM_DENSITY_SOLID_ANGLE = 1 };
 enum { SDMM_PRIOR_SCALE_SEEN = 0, SDMM_PRIOR_SCALE_ARRAY = 1 };
 enum { SDMM_PREC_FP32 = 0, SDMM_PREC_TC_3XBF16 = 1, SDMM_PREC_TC_TF32 = 2,
-       SDMM_PREC_TC_3XTF32 = 3 };
+       SDMM_PREC_TC_3XTF32 = 3, SDMM_PREC_TC_6XBF16 = 4 };
 
 #define SDMM_MAX_K 32
 /* Floats per component in the derived FP32 tables (see sdmm_state). */
@@ -105,9 +105,11 @@ typedef struct sdmm_config {
                                   tensor cores (K = 16 or 32, tangent
                                   density): per-sample features times a
                                   per-region coefficient matrix in split
-                                  3xBF16, TF32 or split 3xTF32, statistics
-                                  as a second product in split 3xBF16, FP32
-                                  accumulation in TMEM                        */
+                                  3xBF16 (two BF16 pieces, three products),
+                                  TF32, split 3xTF32, or 6xBF16 (three BF16
+                                  pieces, the six products of order <= 2),
+                                  statistics as a second product in split
+                                  3xBF16, FP32 accumulation in TMEM          */
     int32_t chunk;             /* samples per work unit of the fit kernels;
                                   0 = library heuristic; else a multiple of
                                   256 in [256, 65536]                        */

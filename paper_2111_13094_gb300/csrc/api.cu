@@ -61,7 +61,7 @@ sdmm_status check_config(const sdmm_config* cfg) {
         return fail(SDMM_ERR_INVALID_ARG, "estep_density %d", cfg->estep_density);
     if (cfg->prior_scale_mode != SDMM_PRIOR_SCALE_SEEN && cfg->prior_scale_mode != SDMM_PRIOR_SCALE_ARRAY)
         return fail(SDMM_ERR_INVALID_ARG, "prior_scale_mode %d", cfg->prior_scale_mode);
-    if (cfg->precision < SDMM_PREC_FP32 || cfg->precision > SDMM_PREC_TC_3XTF32)
+    if (cfg->precision < SDMM_PREC_FP32 || cfg->precision > SDMM_PREC_TC_6XBF16)
         return fail(SDMM_ERR_INVALID_ARG, "precision %d", cfg->precision);
     if (cfg->precision != SDMM_PREC_FP32 && !(cfg->K == 16 || cfg->K == 32))
         return fail(SDMM_ERR_UNSUPPORTED, "tensor-core precision needs K = 16 or 32 (K = %d)", cfg->K);

@@ -257,23 +257,30 @@ constexpr int kTcStatic = 4096;                // static shared memory of k_tc_e
 
 template <int K, int PREC>
 struct TcPlan {
-    static constexpr bool kTf32 = PREC != SDMM_PREC_TC_3XBF16;     // GEMM 1 in TF32
-    static constexpr bool kSplit1 = PREC != SDMM_PREC_TC_TF32;      // GEMM 1 split (3 products)
+    static constexpr bool kTf32 = PREC == SDMM_PREC_TC_TF32 || PREC == SDMM_PREC_TC_3XTF32;   // GEMM 1 in TF32
+    static constexpr bool kSplit1 = PREC != SDMM_PREC_TC_TF32;      // GEMM 1 split (3 or 6 products)
+    static constexpr bool kThree = PREC == SDMM_PREC_TC_6XBF16;     // BF16 in three pieces
     static constexpr int kE1 = kTf32 ? 4 : 2;                       // GEMM 1 element size
     static constexpr int kNQ = 6 * K;                               // GEMM 1 columns
     static constexpr int kKG = K / kTcGroups;                       // components per warp group
     static constexpr int kM2 = (3 * K <= 64) ? 64 : 128;            // GEMM 2 rows (3K used)
     static constexpr int kHalfB = kTile * kPhiPad * 2;              // BF16 feature tile (hi or lo)
     static constexpr int kHalfT = kTile * kPhiPad * 4;              // TF32 feature tile (hi or lo)
-    static constexpr int kPhiB = 2 * kHalfB;                        // hi + lo
+    static constexpr int kPhiB = (kThree ? 3 : 2) * kHalfB;         // hi + lo (+ third piece)
     static constexpr int kPhiT = kTf32 ? (kSplit1 ? 2 : 1) * kHalfT : 0;
     static constexpr int kHalfC = kNQ * kPhiPad * kE1;              // coefficient tile (hi or lo)
-    static constexpr int kC1 = (kSplit1 ? 2 : 1) * kHalfC;
+    static constexpr int kC1 = (kThree ? 3 : kSplit1 ? 2 : 1) * kHalfC;
     static constexpr int kHalfA = kM2 * kTile * 2;                  // statistics operand (hi or lo)
     static constexpr int kA2 = 2 * kHalfA;
     static constexpr int kStage = 7 * kTile * 4;                    // one tile's samples (7 streams)
     static constexpr int kRest = 2 * kPhiT + kC1 + kA2 + 3 * kStage;
-    static constexpr int kNB = 3 * kPhiB + kRest + kTcStatic <= 227 * 1024 ? 3 : 2;
+    // BF16 feature buffers: three when that leaves room for two CTAs per SM
+    // (or for one), else two (the late store waits for GEMM 2(t-1))
+    static constexpr bool fits2(int b) { return (b + kTcStatic + 1024) * 2 <= 228 * 1024; }
+    static constexpr int kNB = fits2(3 * kPhiB + kRest) ? 3
+                               : fits2(2 * kPhiB + kRest) ? 2
+                               : 3 * kPhiB + kRest + kTcStatic <= 227 * 1024 ? 3 : 2;
+    static constexpr bool kEarlyB = !kTf32 && kNB == 3;             // BF16 features stored before GEMM 1(t) ends
     static constexpr int oPhiB = 0;
     static constexpr int oPhiT = kNB * kPhiB;
     static constexpr int oC1 = oPhiT + 2 * kPhiT;
@@ -282,9 +289,9 @@ struct TcPlan {
     static constexpr int kBytes = oStage + 3 * kStage;
     static constexpr uint32_t kD2 = 2 * kNQ;                        // D1[0], D1[1], then D2
     static constexpr uint32_t kCols = kD2 + 32 <= 256 ? 256 : 512;
-    static constexpr int kCtas = (kBytes + kTcStatic + 1024) * 2 <= 228 * 1024 && kCols * 2 <= 512 ? 2 : 1;
+    static constexpr int kCtas = fits2(kBytes) && kCols * 2 <= 512 ? 2 : 1;
     static_assert(kBytes + kTcStatic <= 227 * 1024, "shared memory plan too large");
-    static_assert(kTf32 || kNB == 3, "GEMM 1 in BF16 reads the triple-buffered features early");
+    static_assert(kTf32 || kEarlyB || kThree, "two-buffer BF16 plans are planned for the 6xBF16 form only");
     static_assert(kD2 + 32 <= 512, "TMEM plan too large");
 };
 
@@ -321,6 +328,26 @@ __device__ __forceinline__ void sts_split_bf16(uint32_t hi, uint32_t lo, const f
         tc::sts64(hi, h[0], h[1]);
         tc::sts64(lo, l[0], l[1]);
     }
+}
+// three BF16 pieces of 8 consecutive values: p0 = bf16(v), p1 = bf16(v - p0),
+// p2 = bf16(v - p0 - p1), so that v = p0 + p1 + p2 to about 2^-24 relative
+__device__ __forceinline__ void sts_split3_bf16(uint32_t a0, uint32_t a1, uint32_t a2, const float* v) {
+    uint32_t p0[4], p1[4], p2[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+        const float2 hf = __bfloat1622float2(h);
+        const float r0 = v[2 * i] - hf.x, r1 = v[2 * i + 1] - hf.y;
+        const __nv_bfloat162 m = __floats2bfloat162_rn(r0, r1);
+        const float2 mf = __bfloat1622float2(m);
+        const __nv_bfloat162 l = __floats2bfloat162_rn(r0 - mf.x, r1 - mf.y);
+        p0[i] = *reinterpret_cast<const uint32_t*>(&h);
+        p1[i] = *reinterpret_cast<const uint32_t*>(&m);
+        p2[i] = *reinterpret_cast<const uint32_t*>(&l);
+    }
+    tc::sts128(a0, p0[0], p0[1], p0[2], p0[3]);
+    tc::sts128(a1, p1[0], p1[1], p1[2], p1[3]);
+    tc::sts128(a2, p2[0], p2[1], p2[2], p2[3]);
 }
 // hi (and, if LO, lo) TF32 parts of 4 consecutive values (16-byte stores)
 template <bool LO>
@@ -491,18 +518,21 @@ __global__ void __launch_bounds__(kTcThreads, TcPlan<K, PREC>::kCtas)
         pr1 ^= 1u;
         tc::fence_after_sync();
         if (ok && lane == 0) {
-            const uint64_t a_h = P::kTf32 ? tc::smem_desc(tc::smem_addr(phiT(t & 1)), 128, g1_sbo)
-                                          : tc::smem_desc(tc::smem_addr(phiB(t % P::kNB)), 128, g1_sbo);
-            const uint64_t a_l = tc::desc_add(a_h, P::kTf32 ? P::kHalfT : P::kHalfB);
+            const uint64_t a0 = P::kTf32 ? tc::smem_desc(tc::smem_addr(phiT(t & 1)), 128, g1_sbo)
+                                         : tc::smem_desc(tc::smem_addr(phiB(t % P::kNB)), 128, g1_sbo);
+            constexpr uint32_t a_piece = P::kTf32 ? P::kHalfT : P::kHalfB;
             const uint32_t d = td + (uint32_t)(t & 1) * P::kNQ;
             const uint32_t idesc1 = tc::instr_desc(P::kTf32 ? 2 : 1, kTile, P::kNQ);
-            const uint64_t dC1h = tc::smem_desc(tc::smem_addr(sC1h), 128, g1_sbo);
-            const uint64_t dC1l = tc::desc_add(dC1h, P::kHalfC);
+            const uint64_t b0 = tc::smem_desc(tc::smem_addr(sC1h), 128, g1_sbo);
+            // products of pieces (i of the features, j of the coefficients):
+            // split forms keep (0,0) (0,1) (1,0); three pieces also (0,2) (1,1) (2,0)
+            constexpr int np = P::kThree ? 6 : P::kSplit1 ? 3 : 1;
+            constexpr int pi_[6] = {0, 0, 1, 0, 1, 2}, pj_[6] = {0, 1, 0, 2, 1, 0};
             int n = 0;
 #pragma unroll
-            for (int pass = 0; pass < (P::kSplit1 ? 3 : 1); ++pass) {
-                const uint64_t a = pass == 2 ? a_l : a_h;
-                const uint64_t b = pass == 1 ? dC1l : dC1h;
+            for (int pass = 0; pass < np; ++pass) {
+                const uint64_t a = tc::desc_add(a0, pi_[pass] * a_piece);
+                const uint64_t b = tc::desc_add(b0, pj_[pass] * P::kHalfC);
 #pragma unroll
                 for (int s = 0; s < kPhiPad / g1_k; ++s, ++n) {
                     if (P::kTf32) tc::mma_tf32(d, tc::desc_add(a, s * 256), tc::desc_add(b, s * 256), idesc1, n > 0);
@@ -594,8 +624,13 @@ __global__ void __launch_bounds__(kTcThreads, TcPlan<K, PREC>::kCtas)
     };
     auto store_b = [&](int b, const float* f) {
         const uint32_t a = aPhiB + b * P::kPhiB;
-        sts_split_bf16<8>(a, a + P::kHalfB, f);
-        sts_split_bf16<8>(a + 128, a + 128 + P::kHalfB, f + 8);
+        if constexpr (P::kThree) {
+            sts_split3_bf16(a, a + P::kHalfB, a + 2 * P::kHalfB, f);
+            sts_split3_bf16(a + 128, a + 128 + P::kHalfB, a + 128 + 2 * P::kHalfB, f + 8);
+        } else {
+            sts_split_bf16<8>(a, a + P::kHalfB, f);
+            sts_split_bf16<8>(a + 128, a + 128 + P::kHalfB, f + 8);
+        }
     };
     auto store_t = [&](int b, const float* f) {
         const uint32_t a = aPhiT + b * P::kPhiT;
@@ -606,7 +641,19 @@ __global__ void __launch_bounds__(kTcThreads, TcPlan<K, PREC>::kCtas)
         const float* cr = ctab + (int64_t)r * K * 6 * kPhiPad;
         for (int e = tid; e < P::kNQ * kPhiPad; e += kTcThreads) {
             const int row = e / kPhiPad, f = e % kPhiPad;
-            store_split<P::kE1>(sC1h, sC1l, tc::kmajor_offset(row, f, kPhiPad, P::kE1), __ldg(cr + e));
+            const uint32_t o = tc::kmajor_offset(row, f, kPhiPad, P::kE1);
+            const float v = __ldg(cr + e);
+            if constexpr (P::kThree) {
+                const __nv_bfloat16 h = __float2bfloat16_rn(v);
+                const float r0 = v - __bfloat162float(h);
+                const __nv_bfloat16 m = __float2bfloat16_rn(r0);
+                *reinterpret_cast<__nv_bfloat16*>(sC1h + o) = h;
+                *reinterpret_cast<__nv_bfloat16*>(sC1h + P::kHalfC + o) = m;
+                *reinterpret_cast<__nv_bfloat16*>(sC1h + 2 * P::kHalfC + o) =
+                    __float2bfloat16_rn(r0 - __bfloat162float(m));
+            } else {
+                store_split<P::kE1>(sC1h, sC1l, o, v);
+            }
         }
     };
     // unit statistics out of D2 (rows (h, j, kk) -> partial row j K + h KG + kk)
@@ -671,8 +718,8 @@ __global__ void __launch_bounds__(kTcThreads, TcPlan<K, PREC>::kCtas)
         float f[16];
         if (nxt.live) {
             features(s1, f);
-            if (!P::kTf32) store_b(b1, f);
-            else store_t((t + 1) & 1, f);
+            if (P::kEarlyB) store_b(b1, f);
+            else if (P::kTf32) store_t((t + 1) & 1, f);
         }
         if (a2_ready) {                           // GEMM 2 of the previous tile
             if (warp == 4) issue_g2(t - 1, a2_restart);
@@ -718,7 +765,7 @@ __global__ void __launch_bounds__(kTcThreads, TcPlan<K, PREC>::kCtas)
             sg += lk[j];
         }
         tc::sts64(aML + grp * kTile * 8, __float_as_uint(mg), __float_as_uint(sg));
-        if (P::kTf32 && nxt.live) {
+        if (!P::kEarlyB && nxt.live) {
             if (P::kNB == 2) wait_mma(&bar2, ph2, g2_pending);   // GEMM 2(t-1) reads this buffer
             features(s1, f);
             store_b(b1, f);
@@ -802,6 +849,7 @@ size_t tc_smem_bytes(int K, int prec) {
     SDMM_TC_BYTES(16, SDMM_PREC_TC_3XBF16) SDMM_TC_BYTES(16, SDMM_PREC_TC_TF32)
     SDMM_TC_BYTES(16, SDMM_PREC_TC_3XTF32) SDMM_TC_BYTES(32, SDMM_PREC_TC_3XBF16)
     SDMM_TC_BYTES(32, SDMM_PREC_TC_TF32) SDMM_TC_BYTES(32, SDMM_PREC_TC_3XTF32)
+    SDMM_TC_BYTES(16, SDMM_PREC_TC_6XBF16) SDMM_TC_BYTES(32, SDMM_PREC_TC_6XBF16)
 #undef SDMM_TC_BYTES
     return 0;
 }
@@ -812,6 +860,7 @@ int tc_ctas_per_sm(int K, int prec) {
     SDMM_TC_CTAS(16, SDMM_PREC_TC_3XBF16) SDMM_TC_CTAS(16, SDMM_PREC_TC_TF32)
     SDMM_TC_CTAS(16, SDMM_PREC_TC_3XTF32) SDMM_TC_CTAS(32, SDMM_PREC_TC_3XBF16)
     SDMM_TC_CTAS(32, SDMM_PREC_TC_TF32) SDMM_TC_CTAS(32, SDMM_PREC_TC_3XTF32)
+    SDMM_TC_CTAS(16, SDMM_PREC_TC_6XBF16) SDMM_TC_CTAS(32, SDMM_PREC_TC_6XBF16)
 #undef SDMM_TC_CTAS
     return 1;
 }
@@ -842,6 +891,7 @@ cudaError_t launch_tc_estep(cudaStream_t s, int K, int prec, int grid, WsHeader*
     SDMM_TC_CASE(16, SDMM_PREC_TC_3XBF16) SDMM_TC_CASE(16, SDMM_PREC_TC_TF32)
     SDMM_TC_CASE(16, SDMM_PREC_TC_3XTF32) SDMM_TC_CASE(32, SDMM_PREC_TC_3XBF16)
     SDMM_TC_CASE(32, SDMM_PREC_TC_TF32) SDMM_TC_CASE(32, SDMM_PREC_TC_3XTF32)
+    SDMM_TC_CASE(16, SDMM_PREC_TC_6XBF16) SDMM_TC_CASE(32, SDMM_PREC_TC_6XBF16)
 #undef SDMM_TC_CASE
     return cudaErrorInvalidValue;
 }
