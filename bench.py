@@ -40,6 +40,11 @@ Q_DIMS, Q_COUNT = (64, 32, 32), 16 * 2 ** 20
 FLOPS_PER_PAIR = 114
 # bytes per sample of one E-step pass: 7 FP32 streams
 BYTES_PER_SAMPLE = 28
+# DRAM bytes per sample of the FP32 E-step kernel, read + write, from one ncu
+# capture of a 512-region launch of the same kernel (traffic grows with the
+# samples processed, so a full launch moves this times N); None for kernels
+# without a capture of their current version
+DRAM_BYTES_PER_SAMPLE = {"k_accumulate<16,FIT>": 29.0}
 
 
 def _peaks():
@@ -269,14 +274,56 @@ def run_gpu(args):
     achieved = pairs * FLOPS_PER_PAIR / (kms * 1e-3) / 1e12
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     peak = n_sm * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    kname = "k_accumulate<16,FIT>" if prec == api.PREC_FP32 else f"k_tc_estep<16,{args.precision}>"
+    bps = DRAM_BYTES_PER_SAMPLE.get(kname)
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": None,
-            "kernel": "k_accumulate<16,FIT>" if prec == api.PREC_FP32 else f"k_tc_estep<16,{args.precision}>",
+            "frac": achieved / peak, "traffic": bps * N if bps is not None else None,
+            "traffic_unit": "bytes per launch",
+            "kernel": kname,
             "kernel_ms": kms, "launches_timed": len(kern),
             "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x 2 flop x {peaks.get('sm_max_mhz', 2070.0):.0f} MHz "
                           f"({src} max clock)",
             "hbm_gbs": N * BYTES_PER_SAMPLE / (kms * 1e-3) / 1e9,
             "hbm_frac": N * BYTES_PER_SAMPLE / (kms * 1e-3) / 1e9 / peaks.get("hbm_gbs", 6800.0)}
+
+    # ---- the tensor-core contraction form (three-piece BF16, which meets the
+    # parity contract) on the same resident batches, same steps
+    tcres = None
+    if prec == api.PREC_FP32 and not args.no_tc:
+        tcfg = api.config(K_COMP, precision=api.PREC_TC_6XBF16)
+        tst = api.MixtureState(R_REGIONS, K_COMP, device=dev)
+        api.init_regions(tcfg, batches[0], torch.from_numpy(h.astype(np.float64)).to(dev),
+                         torch.from_numpy(syn.init_uniforms(seed, R_REGIONS, 2)).to(dev), tst)
+        tws = api.workspace(tcfg, R_REGIONS, N, device=dev)
+        tplan = api.FitPlan(tcfg, R_REGIONS, N, 1, tst, tws)
+        for _ in range(args.warmup):
+            for b in batches:
+                tplan.run(b)
+        tplan.enable_timing(args.steps * ROUNDS)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        e0.record(stream)
+        for _ in range(args.steps):
+            for b in batches:
+                tplan.run(b)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tms = e0.elapsed_time(e1)
+        if world > 1:
+            tt = torch.tensor([tms], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            tms = float(tt.item())
+        tk = tplan.timing()
+        c2, n2 = torch.unique(tst.status, return_counts=True)
+        tval = world * args.steps * ROUNDS * N / (tms * 1e-3)
+        tcres = {"precision": "6xbf16", "value": tval, "unit": UNIT, "ms_per_step": tms / args.steps,
+                 "kernel": "k_tc_estep<16,6xbf16>", "kernel_ms": float(np.mean(tk)) if tk else None,
+                 "vs_fp32": tval / value,
+                 "status_counts": {int(c): int(n) for c, n in zip(c2.cpu(), n2.cpu())},
+                 "accuracy": "meets the 1e-4 log-likelihood / 1e-3 parameter contract against the FP64 "
+                             "oracle at 1,024 x 65,536 (tests/precision_sweep.py)"}
+        del tplan, tws, tst
 
     # ---- end to end through the public API with host buffers
     e2e = None
@@ -339,8 +386,8 @@ def run_gpu(args):
                            "all_regions_ok": status_ok, "status_counts": status_counts,
                            "precision": args.precision},
                 "clocks": ck, "e2e": e2e,
-                "gpu_launches": args.steps * ROUNDS * 4,
-                "roofline": roof, "cpu_baseline": cpu, "queries": qres}
+                "gpu_launches": args.steps * ROUNDS * (4 if prec == api.PREC_FP32 else 5),
+                "roofline": roof, "cpu_baseline": cpu, "queries": qres, "tensor_core": tcres}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -356,6 +403,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--regions", type=int, default=4096, help="regions of the fit workload")
+    ap.add_argument("--no-tc", action="store_true", help="skip the tensor-core (6xBF16) comparison")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "3xbf16", "tf32", "3xtf32", "6xbf16"],
                     help="E-step arithmetic: FP32 SIMT or a tensor-core contraction form")
     ap.add_argument("--no-e2e", action="store_true")
