@@ -47,6 +47,37 @@ BYTES_PER_SAMPLE = 28
 DRAM_BYTES_PER_SAMPLE = {"k_accumulate<16,FIT>": 29.0}
 
 
+# ---- multi-rank helpers (one process per GPU under torchrun; every rank fits
+# its own regions, so the only cross-rank traffic is the timing barrier and a
+# max-reduction of one number)
+def rank_env():
+    """(world, rank, local rank) from the torchrun environment; (1, 0, 0) without it."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def rank_seed(rank):
+    """Seed of a rank's workload: distinct regions per rank (weak scaling)."""
+    return 1 + 1000 * rank
+
+
+def max_over_ranks(ms, world, device=None):
+    """The slowest rank's elapsed time (all-reduce MAX, then a barrier)."""
+    if world == 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, ms):
+    """Units processed by all ranks per second of the slowest rank's time."""
+    return world * units_per_rank / (ms * 1e-3)
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -141,9 +172,9 @@ def cpu_baseline(budget_s=15.0, seed=1, R_REGIONS=4096):
 
 
 def run_reference(args):
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
-        return
+    _, rank, _ = rank_env()
+    if rank != 0:                            # the oracle runs once, on rank 0
+        return None
     per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
     for _ in range(args.warmup):
         cpu_baseline(budget_s=per_step / 4)
@@ -207,15 +238,13 @@ def run_gpu(args):
     from paper_2111_13094_gb300 import api
     from paper_2111_13094_gb300 import synthetic as syn
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = rank_env()
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
-    seed = 1 + 1000 * rank                     # every rank fits its own regions (weak scaling)
+    seed = rank_seed(rank)                     # every rank fits its own regions (weak scaling)
 
     # ---- inputs resident in HBM
     R_REGIONS = args.regions
@@ -255,17 +284,12 @@ def run_gpu(args):
     e1.record(stream)
     torch.cuda.synchronize()
     ck = clocks.stop()
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        dist.barrier()
+    ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
     kern = plan.timing()
     codes, cnt = torch.unique(st.status, return_counts=True)
     status_counts = {int(c): int(n) for c, n in zip(codes.cpu(), cnt.cpu())}
     status_ok = status_counts.get(0, 0) == R_REGIONS
-    value = world * args.steps * ROUNDS * N / (ms * 1e-3)
+    value = whole_job_rate(args.steps * ROUNDS * N, world, ms)
 
     # ---- E-step kernel roofline (FP32 ALU bound)
     peaks, src = _peaks()
@@ -309,14 +333,10 @@ def run_gpu(args):
                 tplan.run(b)
         e1.record(stream)
         torch.cuda.synchronize()
-        tms = e0.elapsed_time(e1)
-        if world > 1:
-            tt = torch.tensor([tms], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            tms = float(tt.item())
+        tms = max_over_ranks(e0.elapsed_time(e1), world, dev)
         tk = tplan.timing()
         c2, n2 = torch.unique(tst.status, return_counts=True)
-        tval = world * args.steps * ROUNDS * N / (tms * 1e-3)
+        tval = whole_job_rate(args.steps * ROUNDS * N, world, tms)
         tcres = {"precision": "6xbf16", "value": tval, "unit": UNIT, "ms_per_step": tms / args.steps,
                  "kernel": "k_tc_estep<16,6xbf16>", "kernel_ms": float(np.mean(tk)) if tk else None,
                  "vs_fp32": tval / value,
