@@ -82,6 +82,7 @@ enum { SDMM_DENSITY_TANGENT = 0, SDMM_DENSITY_SOLID_ANGLE = 1 };
 enum { SDMM_PRIOR_SCALE_SEEN = 0, SDMM_PRIOR_SCALE_ARRAY = 1 };
 enum { SDMM_PREC_FP32 = 0, SDMM_PREC_TC_3XBF16 = 1, SDMM_PREC_TC_TF32 = 2,
        SDMM_PREC_TC_3XTF32 = 3, SDMM_PREC_TC_6XBF16 = 4 };
+enum { SDMM_COV_FIRST_ORDER = 0, SDMM_COV_TWO_PASS = 1 };
 
 #define SDMM_MAX_K 32
 /* Floats per component in the derived FP32 tables (see sdmm_state). */
@@ -115,6 +116,17 @@ typedef struct sdmm_config {
                                   256 in [256, 65536]                        */
     int32_t ctas_per_sm;       /* resident CTAs per SM of the persistent fit
                                   kernels; 0 = library default, else 1..4     */
+    int32_t cov_update;        /* SDMM_COV_*: the covariance of the new mean's
+                                  chart from the first-order chart change of
+                                  the averaged statistics (Sec. 3.4, default),
+                                  or the accurate update (Sec. 3.2 Eq.
+                                  tangent-space-sigma-update): a second pass
+                                  over the batch measures it in the new chart
+                                  with the same responsibilities.  The
+                                  accurate update is defined for plain EM
+                                  (eta_mode = SDMM_ETA_ONE; the batch is the
+                                  statistic) and runs on the FP32 SIMT path   */
+    int32_t reserved_;         /* zero                                        */
     double eta_alpha;          /* 0.5 (Sec. 4.3)                              */
     double eta_beta;           /* 0.1 (Sec. 4.3)                              */
     double prior_q;            /* Dirichlet prior q = prior_q / K; paper 1    */

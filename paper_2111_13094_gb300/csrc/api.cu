@@ -71,6 +71,12 @@ sdmm_status check_config(const sdmm_config* cfg) {
         return fail(SDMM_ERR_INVALID_ARG, "chunk %d: 0 or a multiple of 256 in [256, 65536]", cfg->chunk);
     if (cfg->ctas_per_sm < 0 || cfg->ctas_per_sm > 4)
         return fail(SDMM_ERR_INVALID_ARG, "ctas_per_sm %d: 0..4", cfg->ctas_per_sm);
+    if (cfg->cov_update != SDMM_COV_FIRST_ORDER && cfg->cov_update != SDMM_COV_TWO_PASS)
+        return fail(SDMM_ERR_INVALID_ARG, "cov_update %d", cfg->cov_update);
+    if (cfg->cov_update == SDMM_COV_TWO_PASS && cfg->precision != SDMM_PREC_FP32)
+        return fail(SDMM_ERR_UNSUPPORTED, "the two-pass covariance update runs on the FP32 SIMT path");
+    if (cfg->cov_update == SDMM_COV_TWO_PASS && cfg->eta_mode != SDMM_ETA_ONE)
+        return fail(SDMM_ERR_UNSUPPORTED, "the two-pass covariance update is defined for eta_mode = ETA_ONE");
     const double v[6] = {cfg->eta_alpha, cfg->eta_beta, cfg->prior_q, cfg->prior_a,
                          cfg->prior_B_pos, cfg->prior_B_dir};
     for (double x : v)
@@ -113,8 +119,8 @@ int choose_chunk(const sdmm_config* cfg, int64_t N) {
 }
 
 struct Layout {
-    size_t header, chunk_base, chunk_region, partial, ctab, xref, units, total;
-    int chunk, ps;
+    size_t header, chunk_base, chunk_region, partial, ctab, xref, units, chart2, partial2, total;
+    int chunk, ps, ps2;
     int64_t max_chunks;
 };
 
@@ -145,6 +151,15 @@ Layout layout(const sdmm_config* cfg, int64_t R, int64_t N, int chunk) {
         L.units = o;
         o = align_up(o + sizeof(int64_t) * 2 * (size_t)L.max_chunks);
     }
+    L.chart2 = L.partial2 = o;
+    L.ps2 = 0;
+    if (cfg->cov_update == SDMM_COV_TWO_PASS) {   // second pass: new charts and their moments
+        L.ps2 = ((15 * cfg->K) + 3) & ~3;
+        L.chart2 = o;
+        o = align_up(o + sizeof(float) * (size_t)R * cfg->K * kChart);
+        L.partial2 = o;
+        o = align_up(o + sizeof(float) * (size_t)L.max_chunks * L.ps2);
+    }
     L.total = o;
     return L;
 }
@@ -157,6 +172,8 @@ struct WsPtrs {
     float* ctab;
     float* xref;
     int64_t* units;     // tensor-core path only, else null
+    float* chart2;      // two-pass covariance update only, else null
+    float* partial2;
 };
 
 WsPtrs ws_ptrs(void* ws, const Layout& L) {
@@ -164,7 +181,9 @@ WsPtrs ws_ptrs(void* ws, const Layout& L) {
     return WsPtrs{reinterpret_cast<WsHeader*>(b + L.header), reinterpret_cast<int64_t*>(b + L.chunk_base),
                   reinterpret_cast<int32_t*>(b + L.chunk_region), reinterpret_cast<float*>(b + L.partial),
                   reinterpret_cast<float*>(b + L.ctab), reinterpret_cast<float*>(b + L.xref),
-                  L.units < L.total ? reinterpret_cast<int64_t*>(b + L.units) : nullptr};
+                  L.units < L.total ? reinterpret_cast<int64_t*>(b + L.units) : nullptr,
+                  L.ps2 ? reinterpret_cast<float*>(b + L.chart2) : nullptr,
+                  L.ps2 ? reinterpret_cast<float*>(b + L.partial2) : nullptr};
 }
 
 sdmm_status check_ws(void* ws, size_t bytes, const Layout& L) {
@@ -221,8 +240,16 @@ sdmm_status enqueue_fit(const FitLaunch& f, cudaStream_t s, std::vector<cudaEven
                       "accumulate");
         }
         if (evs) SDMM_CUDA(cudaEventRecordWithFlags((*evs)[2 * it + 1], s, cudaEventRecordExternal), "event");
+        if (f.w.partial2 != nullptr) {   // accurate covariance update: second pass in the new charts
+            SDMM_CUDA(launch_new_charts(s, f.R, f.w.hdr, f.w.cb, f.w.partial, f.L.ps, f.cfg, f.st, f.w.chart2),
+                      "new_charts");
+            SDMM_CUDA(launch_accumulate(s, MODE_TWO, KP, std::max(1, sm_count()), f.w.hdr, f.w.cb, f.w.cr,
+                                        f.st.etab, f.cfg.K, f.L.chunk, f.cfg.estep_density, f.w.partial2,
+                                        f.L.ps2, 0, f.w.chart2),
+                      "accumulate_two");
+        }
         SDMM_CUDA(launch_reduce_mstep(s, f.R, f.w.hdr, f.w.cb, f.w.partial, f.L.ps, f.cfg, f.st, it,
-                                      tcore ? f.w.xref : nullptr),
+                                      tcore ? f.w.xref : nullptr, f.w.partial2, f.L.ps2),
                   "reduce_mstep");
     }
     return SDMM_OK;

@@ -100,14 +100,21 @@ __global__ void __launch_bounds__(1024) k_build_chunks(WsHeader* ws, int64_t* ch
 // MODE_FIT  accumulates w r [1, d, d d^T]          (Sec. 3.2 Eq. em-ss-computation)
 // MODE_GRAD accumulates w r [1, z, z y^T], y = L^-1 d, z = L^-T y (adjoint)
 // Both also accumulate W = sum w and sum w l_i.
+// MODE_TWO  (second pass of the accurate covariance update, Sec. 3.2
+//           Eq. tangent-space-sigma-update) keeps the responsibilities of the
+//           current parameters but measures d' = (x - mu'^x, log_{mu'}(w)) in
+//           the chart of each component's new mean mu' (chart2 records) and
+//           accumulates only w r d' d'^T.
 constexpr int kWarps = 8;
 
 template <int KP, int MODE>
-__global__ void __launch_bounds__(kWarps * 32, 2)
+__global__ void __launch_bounds__(kWarps * 32, MODE == MODE_TWO ? 1 : 2)
     k_accumulate(WsHeader* __restrict__ ws, const int64_t* __restrict__ chunk_base,
                  const int32_t* __restrict__ chunk_region, const float* __restrict__ etab, int K,
-                 int chunk, int density, float* __restrict__ partial, int ps, int write_ll) {
+                 int chunk, int density, float* __restrict__ partial, int ps, int write_ll,
+                 const float* __restrict__ chart2) {
     constexpr int SPI = 32 / KP;
+    constexpr int NS = MODE == MODE_TWO ? 15 : kStat;   // statistics per component
     constexpr int RED = KP * kStat + 4;
     __shared__ __align__(16) float sbuf[kWarps][32][8];
     __shared__ float red[kWarps][RED];
@@ -128,6 +135,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2)
     const int64_t R = ws->desc.R;
 
     float prm[kE];
+    float c2[MODE == MODE_TWO ? kChart : 1];
     float lmax = 0.f;
     int prev_r = -1;
     for (;;) {
@@ -160,6 +168,23 @@ __global__ void __launch_bounds__(kWarps * 32, 2)
                 for (int q = 0; q < kE; ++q) prm[q] = 0.f;
                 prm[11] = 1.f;
                 prm[27] = -INFINITY;
+            }
+            if (MODE == MODE_TWO) {
+                if (k < K) {
+                    const float4* src = reinterpret_cast<const float4*>(chart2 + ((int64_t)r * K + k) * kChart);
+#pragma unroll
+                    for (int q = 0; q < kChart / 4; ++q) {
+                        const float4 v = __ldg(src + q);
+                        c2[4 * q + 0] = v.x;
+                        c2[4 * q + 1] = v.y;
+                        c2[4 * q + 2] = v.z;
+                        c2[4 * q + 3] = v.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < kChart; ++q) c2[q] = 0.f;
+                    c2[11] = 1.f;
+                }
             }
             // upper bound of every component's log-density in this region:
             // l_k = c5_k - q/2 <= c5_k (tangent density), so exp(l - lmax) <= 1
@@ -238,6 +263,31 @@ __global__ void __launch_bounds__(kWarps * 32, 2)
                 wsum += wt;
                 wll += (wt > 0.f) ? wt * li : 0.f;
                 if (loglik != nullptr && k == 0 && j < n) loglik[g + j] = li;
+                if (MODE == MODE_TWO) {
+                    // the sample in the chart of the new mean: same log map, new centre
+                    const float u2 = c2[3] * sb.x + c2[4] * sb.y + c2[5] * sb.z;
+                    const float v2 = c2[6] * sb.x + c2[7] * sb.y + c2[8] * sb.z;
+                    const float cz2 = c2[9] * sb.x + c2[10] * sb.y + c2[11] * sb.z;
+                    const float s22 = u2 * u2 + v2 * v2;
+                    const float rs2 = rsqrtf(s22);
+                    const float th2 = atan2_pos(s22 * rs2, cz2);
+                    const bool oc2 = s22 > 0.f;
+                    const float g2 = oc2 ? th2 * rs2 : 1.f;
+                    float dn[5];
+                    dn[0] = (sa.x - c2[0]) - c2[12];
+                    dn[1] = (sa.y - c2[1]) - c2[13];
+                    dn[2] = (sa.z - c2[2]) - c2[14];
+                    dn[3] = g2 * u2;
+                    dn[4] = g2 * v2;
+                    const float wr2 = (!oc2 && cz2 < 0.f) ? 0.f : wr;   // cut locus of the new chart
+#pragma unroll
+                    for (int a2 = 0; a2 < 5; ++a2) {
+                        const float wa = wr2 * dn[a2];
+#pragma unroll
+                        for (int b2 = 0; b2 <= a2; ++b2) acc[pk(a2, b2)] += wa * dn[b2];
+                    }
+                    continue;
+                }
                 float x[5];
                 if (MODE == MODE_FIT) {
 #pragma unroll
@@ -266,20 +316,20 @@ __global__ void __launch_bounds__(kWarps * 32, 2)
 #pragma unroll
         for (int o = KP; o < 32; o <<= 1) {
 #pragma unroll
-            for (int s = 0; s < kStat; ++s) acc[s] += __shfl_xor_sync(0xffffffffu, acc[s], o);
+            for (int s = 0; s < NS; ++s) acc[s] += __shfl_xor_sync(0xffffffffu, acc[s], o);
             wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
             wll += __shfl_xor_sync(0xffffffffu, wll, o);
         }
         if (h == 0 && k < K) {
 #pragma unroll
-            for (int s = 0; s < kStat; ++s) red[warp][k * kStat + s] = acc[s];
+            for (int s = 0; s < NS; ++s) red[warp][k * NS + s] = acc[s];
         }
-        if (lane == 0) {
-            red[warp][K * kStat] = wsum;
-            red[warp][K * kStat + 1] = wll;
+        if (MODE != MODE_TWO && lane == 0) {
+            red[warp][K * NS] = wsum;
+            red[warp][K * NS + 1] = wll;
         }
         __syncthreads();
-        const int nv = K * kStat + 2;
+        const int nv = K * NS + (MODE == MODE_TWO ? 0 : 2);
         for (int v = threadIdx.x; v < nv; v += kWarps * 32) {
             float s = 0.f;
 #pragma unroll
@@ -347,18 +397,62 @@ __device__ inline void features_to_stats(const double* Fa, const double* Fb, con
         }
 }
 
+// Second-pass charts of the accurate covariance update: per component the
+// batch mean offset m = s1 / s0 of the first pass (FP64 sums of the unit
+// partials), the new mean (mu^x + m^x, exp_{mu^w}(m^nu), Eq. tangent-space-
+// mu-update) and its chart rows, as kChart floats: mu^x hi, t, b, mu^w,
+// mu^x lo.  Also re-arms the work queue for the second pass.
+__global__ void __launch_bounds__(128) k_new_charts(WsHeader* __restrict__ ws,
+                                                    const int64_t* __restrict__ chunk_base,
+                                                    const float* __restrict__ partial, int ps,
+                                                    sdmm_config cfg, sdmm_state st,
+                                                    float* __restrict__ chart2) {
+    const int64_t r = blockIdx.x;
+    const int K = cfg.K;
+    const int tid = threadIdx.x;
+    __shared__ double s_st[SDMM_MAX_K * kStat];
+    if (r == 0 && tid == 0) ws->queue = 0;
+    const int64_t nc = ws->n_chunks;
+    reduce_partials(partial, ps, min(chunk_base[r], nc), min(chunk_base[r + 1], nc), K * kStat, s_st);
+    __syncthreads();
+    if (tid < K) {
+        const int64_t rk = r * K + tid;
+        const double s0 = s_st[tid * kStat];
+        double m[5], nmx[3], omw[3], nmw[3], t[3], b[3];
+        for (int c = 0; c < 5; ++c) m[c] = (s0 > 0.0 && isfinite(s0)) ? s_st[tid * kStat + 1 + c] / s0 : 0.0;
+        for (int c = 0; c < 3; ++c) {
+            nmx[c] = st.mu_x[rk * 3 + c] + m[c];
+            omw[c] = st.mu_w[rk * 3 + c];
+        }
+        exp_map_f64(omw, m + 3, nmw);
+        basis_f64(nmw, t, b);
+        float* o = chart2 + rk * kChart;
+        for (int c = 0; c < 3; ++c) {
+            const float hi = (float)nmx[c];
+            o[c] = hi;
+            o[12 + c] = (float)(nmx[c] - (double)hi);
+            o[3 + c] = (float)t[c];
+            o[6 + c] = (float)b[c];
+            o[9 + c] = (float)nmw[c];
+        }
+        o[15] = 0.f;
+    }
+}
+
 template <bool FEAT>
 __global__ void __launch_bounds__(128) k_reduce_mstep(WsHeader* __restrict__ ws,
                                                       const int64_t* __restrict__ chunk_base,
                                                       const float* __restrict__ partial, int ps,
                                                       sdmm_config cfg, sdmm_state st, int iter,
-                                                      const float* __restrict__ xref) {
+                                                      const float* __restrict__ xref,
+                                                      const float* __restrict__ partial2, int ps2) {
     const int64_t r = blockIdx.x;
     const int K = cfg.K;
     const int tid = threadIdx.x;
     __shared__ double s_st[SDMM_MAX_K * kStat + 2];
     __shared__ double s_feat[FEAT ? 3 * SDMM_MAX_K * kFeat + 8 : 1];
     __shared__ double s_S0[SDMM_MAX_K];
+    __shared__ double s_two[SDMM_MAX_K * 15];    // second-pass moments (accurate update)
     __shared__ int s_code[SDMM_MAX_K];
     __shared__ int s_skip;
 
@@ -403,6 +497,7 @@ __global__ void __launch_bounds__(128) k_reduce_mstep(WsHeader* __restrict__ ws,
     } else {
         reduce_partials(partial, ps, c0, c1, K * kStat + 2, s_st);
     }
+    if (partial2 != nullptr) reduce_partials(partial2, ps2, c0, c1, K * 15, s_two);
     __syncthreads();
     const double W = s_st[K * kStat];
     if (tid == 0) {
@@ -453,26 +548,32 @@ __global__ void __launch_bounds__(128) k_reduce_mstep(WsHeader* __restrict__ ws,
                 nmx[c] = omx[c] + m[c];
             }
             exp_map_f64(omw, m + 3, nmw);                 // Eq. tangent-space-mu-update
-            // centred second moment in the old chart ...
-            double C[15];
-            for (int i = 0; i < 5; ++i)
-                for (int j = 0; j <= i; ++j) C[pk(i, j)] = hS2[pk(i, j)] - hS0 * m[i] * m[j];
-            // ... moved to the new chart: T C T^T, T = blockdiag(I3, J) (Sec. 3.4)
-            double J[4];
-            chart_jacobian_f64(omw, m + 3, nmw, J);
-            for (int i = 0; i < 3; ++i)
-                for (int j = 0; j <= i; ++j) nS2[pk(i, j)] = C[pk(i, j)];
-            for (int ia = 0; ia < 2; ++ia)
-                for (int j = 0; j < 3; ++j)
-                    nS2[pk(3 + ia, j)] = J[ia * 2 + 0] * C[pk(3, j)] + J[ia * 2 + 1] * C[pk(4, j)];
-            const double c33 = C[pk(3, 3)], c43 = C[pk(4, 3)], c44 = C[pk(4, 4)];
-            for (int ia = 0; ia < 2; ++ia)
-                for (int ib = 0; ib <= ia; ++ib) {
-                    const double a0 = J[ia * 2 + 0], a1 = J[ia * 2 + 1];
-                    const double b0 = J[ib * 2 + 0], b1 = J[ib * 2 + 1];
-                    nS2[pk(3 + ia, 3 + ib)] =
-                        a0 * (c33 * b0 + c43 * b1) + a1 * (c43 * b0 + c44 * b1);
-                }
+            if (partial2 != nullptr) {
+                // accurate update (Eq. tangent-space-sigma-update): the second
+                // pass measured the batch in the new chart, centred at the new mean
+                for (int p = 0; p < 15; ++p) nS2[p] = s_two[tid * 15 + p] * invW;
+            } else {
+                // centred second moment in the old chart ...
+                double C[15];
+                for (int i = 0; i < 5; ++i)
+                    for (int j = 0; j <= i; ++j) C[pk(i, j)] = hS2[pk(i, j)] - hS0 * m[i] * m[j];
+                // ... moved to the new chart: T C T^T, T = blockdiag(I3, J) (Sec. 3.4)
+                double J[4];
+                chart_jacobian_f64(omw, m + 3, nmw, J);
+                for (int i = 0; i < 3; ++i)
+                    for (int j = 0; j <= i; ++j) nS2[pk(i, j)] = C[pk(i, j)];
+                for (int ia = 0; ia < 2; ++ia)
+                    for (int j = 0; j < 3; ++j)
+                        nS2[pk(3 + ia, j)] = J[ia * 2 + 0] * C[pk(3, j)] + J[ia * 2 + 1] * C[pk(4, j)];
+                const double c33 = C[pk(3, 3)], c43 = C[pk(4, 3)], c44 = C[pk(4, 4)];
+                for (int ia = 0; ia < 2; ++ia)
+                    for (int ib = 0; ib <= ia; ++ib) {
+                        const double a0 = J[ia * 2 + 0], a1 = J[ia * 2 + 1];
+                        const double b0 = J[ib * 2 + 0], b1 = J[ib * 2 + 1];
+                        nS2[pk(3 + ia, 3 + ib)] =
+                            a0 * (c33 * b0 + c43 * b1) + a1 * (c43 * b0 + c44 * b1);
+                    }
+            }
             // MAP covariance (Sec. 4.3)
             const double Bd[5] = {a * cfg.prior_B_pos, a * cfg.prior_B_pos, a * cfg.prior_B_pos,
                                   a * cfg.prior_B_dir, a * cfg.prior_B_dir};
@@ -739,11 +840,12 @@ __global__ void k_prepare(int K, int64_t R, sdmm_state st, const double* __restr
 template <int MODE>
 static cudaError_t launch_acc_mode(int KP, dim3 grid, cudaStream_t s, WsHeader* ws,
                                    const int64_t* cb, const int32_t* cr, const float* etab, int K,
-                                   int chunk, int density, float* partial, int ps, int write_ll) {
+                                   int chunk, int density, float* partial, int ps, int write_ll,
+                                   const float* chart2) {
 #define SDMM_ACC_CASE(P)                                                                       \
     case P:                                                                                    \
         k_accumulate<P, MODE><<<grid, kWarps * 32, 0, s>>>(ws, cb, cr, etab, K, chunk, density, \
-                                                          partial, ps, write_ll);              \
+                                                          partial, ps, write_ll, chart2);      \
         break;
     switch (KP) {
         SDMM_ACC_CASE(1)
@@ -771,21 +873,35 @@ cudaError_t launch_build_chunks(cudaStream_t s, WsHeader* ws, int64_t* cb, int32
 
 cudaError_t launch_accumulate(cudaStream_t s, int mode, int KP, int grid, WsHeader* ws,
                               const int64_t* cb, const int32_t* cr, const float* etab, int K,
-                              int chunk, int density, float* partial, int ps, int write_ll) {
+                              int chunk, int density, float* partial, int ps, int write_ll,
+                              const float* chart2) {
     if (mode == MODE_FIT)
         return launch_acc_mode<MODE_FIT>(KP, dim3(grid), s, ws, cb, cr, etab, K, chunk, density,
-                                         partial, ps, write_ll);
+                                         partial, ps, write_ll, nullptr);
+    if (mode == MODE_TWO)
+        return launch_acc_mode<MODE_TWO>(KP, dim3(grid), s, ws, cb, cr, etab, K, chunk, density,
+                                         partial, ps, 0, chart2);
     return launch_acc_mode<MODE_GRAD>(KP, dim3(grid), s, ws, cb, cr, etab, K, chunk, density,
-                                      partial, ps, write_ll);
+                                      partial, ps, write_ll, nullptr);
+}
+
+cudaError_t launch_new_charts(cudaStream_t s, int64_t R, WsHeader* ws, const int64_t* cb,
+                              const float* partial, int ps, const sdmm_config& cfg,
+                              const sdmm_state& st, float* chart2) {
+    k_new_charts<<<(unsigned)R, 128, 0, s>>>(ws, cb, partial, ps, cfg, st, chart2);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_reduce_mstep(cudaStream_t s, int64_t R, WsHeader* ws, const int64_t* cb,
                                 const float* partial, int ps, const sdmm_config& cfg,
-                                const sdmm_state& st, int iter, const float* xref) {
+                                const sdmm_state& st, int iter, const float* xref,
+                                const float* partial2, int ps2) {
     if (xref != nullptr)
-        k_reduce_mstep<true><<<(unsigned)R, 128, 0, s>>>(ws, cb, partial, ps, cfg, st, iter, xref);
+        k_reduce_mstep<true><<<(unsigned)R, 128, 0, s>>>(ws, cb, partial, ps, cfg, st, iter, xref,
+                                                         partial2, ps2);
     else
-        k_reduce_mstep<false><<<(unsigned)R, 128, 0, s>>>(ws, cb, partial, ps, cfg, st, iter, xref);
+        k_reduce_mstep<false><<<(unsigned)R, 128, 0, s>>>(ws, cb, partial, ps, cfg, st, iter, xref,
+                                                          partial2, ps2);
     return cudaGetLastError();
 }
 

@@ -7,7 +7,9 @@
 
 namespace sdmm {
 
-enum { MODE_FIT = 0, MODE_GRAD = 1 };
+enum { MODE_FIT = 0, MODE_GRAD = 1, MODE_TWO = 2 };
+// new-chart records of the two-pass covariance update: floats per component
+constexpr int kChart = 16;
 enum { OP_CONDITION = 0, OP_SAMPLE = 1, OP_PDF = 2 };
 
 struct GridF {
@@ -22,10 +24,15 @@ cudaError_t launch_build_chunks(cudaStream_t s, WsHeader* ws, int64_t* cb, int32
                                 int chunk, int min_samples, int64_t max_chunks);
 cudaError_t launch_accumulate(cudaStream_t s, int mode, int KP, int grid, WsHeader* ws,
                               const int64_t* cb, const int32_t* cr, const float* etab, int K,
-                              int chunk, int density, float* partial, int ps, int write_ll);
+                              int chunk, int density, float* partial, int ps, int write_ll,
+                              const float* chart2 = nullptr);
+cudaError_t launch_new_charts(cudaStream_t s, int64_t R, WsHeader* ws, const int64_t* cb,
+                              const float* partial, int ps, const sdmm_config& cfg,
+                              const sdmm_state& st, float* chart2);
 cudaError_t launch_reduce_mstep(cudaStream_t s, int64_t R, WsHeader* ws, const int64_t* cb,
                                 const float* partial, int ps, const sdmm_config& cfg,
-                                const sdmm_state& st, int iter, const float* xref);
+                                const sdmm_state& st, int iter, const float* xref,
+                                const float* partial2 = nullptr, int ps2 = 0);
 // contraction form on the tensor cores
 size_t tc_smem_bytes(int K, int prec);
 

@@ -131,9 +131,62 @@ def objective_adjoint(seed=30, R=1024, M=16384, K=16, check=3, reps=10):
             "oracle_samples_per_s": check * M / t_or, **err}
 
 
+def covariance_updates(seed=40, R=1024, M=16384, K=16, check=3, steps=3, reps=5):
+    """First-order vs accurate two-pass covariance update (plain EM): GPU time
+    of an EM step and the covariance error of each against the oracle's
+    two-pass update (the accurate reference) on checked regions."""
+    truth = syn.batched_truth(seed, R, K=K, parallax=True)
+    counts = np.full(R, M, dtype=np.int64)
+    N = R * M
+    offsets = syn.offsets_from_counts(counts)
+    dev = torch.device("cuda")
+    samples = syn.draw_torch(seed, truth, counts, device=dev)
+    batch = api.SampleBatch(samples, torch.from_numpy(offsets).to(dev))
+    _, h, _ = syn.region_grid(R)
+    regions = np.sort(np.random.default_rng([seed, 9]).choice(R, size=check, replace=False))
+    sub = np.concatenate([samples[:, offsets[r]:offsets[r + 1]].cpu().numpy() for r in regions], axis=1)
+    sub_off = syn.offsets_from_counts(counts[regions])
+    o0 = orc.State(check, K)
+    orc.init_regions(orc.config(K), sub_off, sub, h[regions], syn.init_uniforms(seed, R, K // 8)[regions], o0)
+    ref = o0.copy()
+    orc.fit_regions(orc.config(K, eta_mode=1, cov_update=1), sub_off, sub, steps, ref)
+    idx = torch.from_numpy(regions).to(dev)
+    out = {"config": f"covariance update, {R} regions x {M} samples, K = {K}, plain EM, {steps} steps"}
+    for name, mode in (("first_order", 0), ("two_pass", 1)):
+        cfg = api.config(K, eta_mode=api.ETA_ONE, cov_update=mode)
+        st = api.MixtureState(R, K, device=dev)
+        api.init_regions(cfg, batch, torch.from_numpy(h.astype(np.float64)).to(dev),
+                         torch.from_numpy(syn.init_uniforms(seed, R, K // 8)).to(dev), st)
+        for f in orc.State.FIELDS:
+            getattr(st, f)[idx] = torch.from_numpy(getattr(o0, f)).to(dev)
+        api.prepare(cfg, st)
+        ws = api.workspace(cfg, R, N, device=dev)
+        snap = {f: getattr(st, f).clone() for f in orc.State.FIELDS}
+        api.fit_regions(cfg, batch, steps, st, ws)
+        torch.cuda.synchronize()
+        g = host(st)
+        err_L = block_err(g.L[regions], ref.L)
+        e0, e1 = _events()
+        times = []
+        for _ in range(reps):
+            for f in orc.State.FIELDS:
+                getattr(st, f).copy_(snap[f])
+            api.prepare(cfg, st)
+            torch.cuda.synchronize()
+            e0.record()
+            api.fit_regions(cfg, batch, 1, st, ws)
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        out[name] = {"step_ms": float(np.median(times)), "L_error_vs_two_pass_oracle": err_L}
+    out["time_ratio"] = out["two_pass"]["step_ms"] / out["first_order"]["step_ms"]
+    return out
+
+
 def main():
     a = single_region()
     b = objective_adjoint()
+    c = covariance_updates()
     print("| config | GPU | error vs oracle | oracle (1 core) |")
     print("|---|---|---|---|")
     print(f"| {a['config']} | {a['gpu_ms']:.2f} ms ({a['sample_iterations_per_s']:.3e} sample-it/s) | "
@@ -143,7 +196,10 @@ def main():
           f"({b['samples_per_s_backward']:.3e} samples/s) | F {b['F']:.1e}, grad delta {b['g_delta']:.1e}, "
           f"grad L {b['g_L']:.1e}, grad logit {b['g_logit']:.1e} | "
           f"{b['oracle_s_per_region']:.2f} s per region ({b['oracle_samples_per_s']:.3e} samples/s) |")
-    print(json.dumps({"single_region": a, "objective": b}))
+    for name in ("first_order", "two_pass"):
+        print(f"| {c['config']}: {name} | {c[name]['step_ms']:.2f} ms per EM step | "
+              f"L vs the accurate (two-pass) oracle {c[name]['L_error_vs_two_pass_oracle']:.1e} | — |")
+    print(json.dumps({"single_region": a, "objective": b, "covariance_updates": c}))
 
 
 if __name__ == "__main__":

@@ -69,3 +69,11 @@ def test_host_validation_errors(lib):
     g = _lib.Grid()
     assert lib.sdmm_condition(ctypes.byref(cfg), None, 1, 1, None, None, ctypes.byref(g), None, None, None, None) == 1
     assert lib.sdmm_fit_plan_destroy(None) == 0
+    # the accurate (two-pass) covariance update: plain EM on the FP32 SIMT path only
+    assert lib.sdmm_fit_workspace_size(ctypes.byref(api.config(16, cov_update=2)), 1, 10, ctypes.byref(n)) == 1
+    assert lib.sdmm_fit_workspace_size(ctypes.byref(api.config(16, cov_update=1)), 1, 10, ctypes.byref(n)) == 4
+    assert b"eta_mode" in lib.sdmm_last_error()
+    assert lib.sdmm_fit_workspace_size(ctypes.byref(api.config(16, cov_update=1, eta_mode=1, precision=4)),
+                                       1, 10, ctypes.byref(n)) == 4
+    assert lib.sdmm_fit_workspace_size(ctypes.byref(api.config(16, cov_update=1, eta_mode=1)), 1, 10,
+                                       ctypes.byref(n)) == 0
