@@ -435,6 +435,91 @@ sdmm_status sdmm_fit_regions_noalloc(const sdmm_config *cfg,
                                      sdmm_state *st, float *loglik_out,
                                      sdmm_stream stream);
 
+/*
+ * ---- The spatial kD-tree of the regions (Sec. 4.2 "Refinement of the
+ * spatial kD-tree", Sec. 4.3 "Initialization").
+ *
+ * Positions are normalised to [0,1]^3 (the scene's bounding box, Sec. 4.3).
+ * The tree is a device array of nodes; node 0 is the root.  A leaf node has
+ * axis -1 and the index of its region in `leaf`; an internal node sends
+ * x[axis] < split to `left` and the rest to left + 1.  Leaves are numbered in
+ * tree order (left before right), so once samples are sorted by leaf the
+ * samples of leaf r form the r-th contiguous segment (the region offsets of
+ * sdmm_fit_regions).  The counts are host fields updated by the calls;
+ * capacities are the lengths of the arrays.
+ */
+typedef struct sdmm_kdtree {
+    int32_t *axis;       /* [cap_nodes] split axis 0..2, or -1 for a leaf   */
+    double *split;       /* [cap_nodes] split position                      */
+    int32_t *left;       /* [cap_nodes] first child (the second: left + 1)  */
+    int32_t *leaf;       /* [cap_nodes] region index of a leaf node         */
+    int32_t n_nodes;     /* nodes in use (host field)                       */
+    int32_t n_leaves;    /* leaves = regions (host field)                   */
+    int32_t cap_nodes;
+    int32_t cap_leaves;
+} sdmm_kdtree;
+
+/* Sample streams written by the tree calls (device, caller-owned): N floats
+   each and offsets[cap_leaves + 1]; R and N are set by the call. */
+typedef struct sdmm_sample_buffers {
+    float *px, *py, *pz, *ox, *oy, *oz, *w;
+    int64_t *offsets;
+    int64_t R;
+    int64_t N;
+} sdmm_sample_buffers;
+
+/* The pre-subdivision of Sec. 4.3: every axis split at the centre of its cell,
+   x then y then z, `levels` times (3: the paper's 8 x 8 x 8 cells).  Needs
+   cap_nodes >= 2^(3 levels + 1) - 1 and cap_leaves >= 8^levels; levels 0..7.
+   Leaf r is the cell whose Morton code (bits x y z, most significant first)
+   is r.  Synchronous on `stream`. */
+sdmm_status sdmm_kdtree_grid(sdmm_kdtree *t, int32_t levels, sdmm_stream stream);
+
+/* Region of Q points (device SoA) by descent from the root; writes leaf[Q]
+   (int32).  Asynchronous. */
+sdmm_status sdmm_kdtree_lookup(const sdmm_kdtree *t, int64_t Q, const float *px,
+                               const float *py, const float *pz, int32_t *leaf,
+                               sdmm_stream stream);
+
+/* Workspace bytes of sdmm_kdtree_bin / sdmm_kdtree_refine for N samples with
+   this tree's capacities (N < 2^31). */
+sdmm_status sdmm_kdtree_workspace_size(const sdmm_kdtree *t, int64_t N, size_t *bytes);
+
+/* Binning (Sec. 4.2: each leaf collects the vertices located within it): the
+   N samples of `in` (any order; in->offsets and in->R are ignored) sorted by
+   leaf into `out`, stably (original order within a leaf), with
+   out->offsets[n_leaves + 1].  Synchronous on `stream` (one 4-byte read-back
+   per tree level). */
+sdmm_status sdmm_kdtree_bin(const sdmm_kdtree *t, const sdmm_samples *in,
+                            sdmm_sample_buffers *out, void *workspace,
+                            size_t ws_bytes, sdmm_stream stream);
+
+/* Refinement (Sec. 4.2): every leaf holding more than c samples is split along
+   the axis of largest positional variance at the mean position along it,
+   recursively, until no leaf holds more than c or a split would leave one
+   side empty (the paper uses c = 16000).  Mean and variance come from exact
+   fixed-point sums (x clamped to [0,1], in units of 2^-32), so the planes do
+   not depend on summation order.  `in` holds the samples sorted by the
+   current leaves (in->R = t->n_leaves, in->offsets); `out` receives them
+   sorted by the new leaves (stable) with out->offsets; leaf_parent[cap_leaves]
+   (int64) receives for every new leaf the leaf of the input it lies in (copy
+   its mixture with sdmm_gather_regions, as the paper copies the parent's).
+   The tree is updated in place: split leaves become internal nodes, new
+   nodes are appended, leaves are renumbered in tree order.  At most 64 split
+   rounds (tree levels) per call; SDMM_ERR_WORKSPACE if the capacities would
+   be exceeded (the tree is then left as before the failing round).
+   Synchronous on `stream`. */
+sdmm_status sdmm_kdtree_refine(sdmm_kdtree *t, int64_t c, const sdmm_samples *in,
+                               sdmm_sample_buffers *out, int64_t *leaf_parent,
+                               void *workspace, size_t ws_bytes, sdmm_stream stream);
+
+/* out region r <- in region src[r] for r < R_out: parameters, averaged
+   statistics, Wbar, n_seen, step_j, status and the derived tables (K
+   components each).  `in` and `out` must not overlap.  Asynchronous. */
+sdmm_status sdmm_gather_regions(int32_t K, int64_t R_out, const int64_t *src,
+                                const sdmm_state *in, sdmm_state *out,
+                                sdmm_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

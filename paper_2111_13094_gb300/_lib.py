@@ -23,7 +23,8 @@ SYMBOLS = ["sdmm_config_default", "sdmm_last_error", "sdmm_version", "sdmm_fit_w
            "sdmm_sample", "sdmm_pdf", "sdmm_objective", "sdmm_objective_backward",
            "sdmm_fit_plan_create", "sdmm_fit_plan_run", "sdmm_fit_plan_enable_timing",
            "sdmm_fit_plan_timing", "sdmm_fit_plan_destroy", "sdmm_autotune",
-           "sdmm_fit_regions_noalloc", "sdmm_tc_selftest"]
+           "sdmm_fit_regions_noalloc", "sdmm_tc_selftest", "sdmm_kdtree_grid", "sdmm_kdtree_lookup",
+           "sdmm_kdtree_workspace_size", "sdmm_kdtree_bin", "sdmm_kdtree_refine", "sdmm_gather_regions"]
 
 SDMM_NOALLOC_SCRATCH_BYTES = 16 * 1024 * 1024
 
@@ -46,6 +47,17 @@ class State(ctypes.Structure):
 
 
 class Samples(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_void_p) for n in ("px", "py", "pz", "ox", "oy", "oz", "w", "offsets")] + \
+               [("R", ctypes.c_int64), ("N", ctypes.c_int64)]
+
+
+class KdTree(ctypes.Structure):
+    _fields_ = [("axis", ctypes.c_void_p), ("split", ctypes.c_void_p), ("left", ctypes.c_void_p),
+                ("leaf", ctypes.c_void_p), ("n_nodes", ctypes.c_int32), ("n_leaves", ctypes.c_int32),
+                ("cap_nodes", ctypes.c_int32), ("cap_leaves", ctypes.c_int32)]
+
+
+class SampleBuffers(ctypes.Structure):
     _fields_ = [(n, ctypes.c_void_p) for n in ("px", "py", "pz", "ox", "oy", "oz", "w", "offsets")] + \
                [("R", ctypes.c_int64), ("N", ctypes.c_int64)]
 
@@ -91,6 +103,13 @@ def _declare(L):
                           ctypes.POINTER(_I32), ctypes.POINTER(ctypes.c_float)],
         "sdmm_fit_regions_noalloc": [_PC, _PSm, _I32, _P, _PS, _P, _P],
         "sdmm_tc_selftest": [_I32, _I32, _I32, _P, _P, _P, _I32, _P, _P],
+        "sdmm_kdtree_grid": [ctypes.POINTER(KdTree), _I32, _P],
+        "sdmm_kdtree_lookup": [ctypes.POINTER(KdTree), _I64, _P, _P, _P, _P, _P],
+        "sdmm_kdtree_workspace_size": [ctypes.POINTER(KdTree), _I64, ctypes.POINTER(ctypes.c_size_t)],
+        "sdmm_kdtree_bin": [ctypes.POINTER(KdTree), _PSm, ctypes.POINTER(SampleBuffers), _P, ctypes.c_size_t, _P],
+        "sdmm_kdtree_refine": [ctypes.POINTER(KdTree), _I64, _PSm, ctypes.POINTER(SampleBuffers), _P, _P,
+                               ctypes.c_size_t, _P],
+        "sdmm_gather_regions": [_I32, _I64, _P, _PS, _PS, _P],
     }
     for name, args in sig.items():
         f = getattr(L, name)

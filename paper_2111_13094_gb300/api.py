@@ -13,7 +13,7 @@ from dataclasses import dataclass
 import torch
 
 from . import _lib
-from ._lib import check
+from ._lib import SdmmError, check  # noqa: F401  (SdmmError: raised by every call)
 
 __all__ = ["config", "MixtureState", "SampleBatch", "Grid", "workspace", "workspace_bytes",
            "init_regions", "fit_regions", "fit_regions_noalloc", "prepare", "condition", "sample", "pdf", "objective",
@@ -112,6 +112,86 @@ class SampleBatch:
         base = s.data_ptr()
         st = s.stride(0) * s.element_size()
         return _lib.Samples(*[base + i * st for i in range(7)], self.offsets.data_ptr(), self.R, self.N)
+
+
+class KdTree:
+    """The spatial kD-tree of the regions (Sec. 4.2, Sec. 4.3) on the device:
+    node arrays with capacity `cap_nodes`, at most `cap_leaves` leaves."""
+
+    def __init__(self, cap_nodes: int, cap_leaves: int, device="cuda"):
+        self.axis = torch.full((cap_nodes,), -1, dtype=torch.int32, device=device)
+        self.split = torch.zeros(cap_nodes, dtype=torch.float64, device=device)
+        self.left = torch.full((cap_nodes,), -1, dtype=torch.int32, device=device)
+        self.leaf = torch.full((cap_nodes,), -1, dtype=torch.int32, device=device)
+        self._c = _lib.KdTree(self.axis.data_ptr(), self.split.data_ptr(), self.left.data_ptr(),
+                              self.leaf.data_ptr(), 0, 0, int(cap_nodes), int(cap_leaves))
+
+    @property
+    def n_nodes(self):
+        return self._c.n_nodes
+
+    @property
+    def n_leaves(self):
+        return self._c.n_leaves
+
+    def grid(self, levels: int, stream=None):
+        """Pre-subdivision: 2^levels cells per axis (3: the paper's 8 x 8 x 8)."""
+        check(_lib.load().sdmm_kdtree_grid(ctypes.byref(self._c), int(levels), _stream(stream)), "sdmm_kdtree_grid")
+        return self
+
+    def lookup(self, pos: torch.Tensor, stream=None) -> torch.Tensor:
+        """Leaf of each point; pos: float32 (3, Q)."""
+        pos = pos.contiguous()
+        Q = pos.shape[1]
+        out = torch.empty(Q, dtype=torch.int32, device=pos.device)
+        st = pos.stride(0) * pos.element_size()
+        b = pos.data_ptr()
+        check(_lib.load().sdmm_kdtree_lookup(ctypes.byref(self._c), Q, b, b + st, b + 2 * st, _ptr(out),
+                                             _stream(stream)), "sdmm_kdtree_lookup")
+        return out
+
+    def _run(self, samples: torch.Tensor, offsets, c, stream):
+        samples = samples.contiguous()
+        N = samples.shape[1]
+        n = ctypes.c_size_t()
+        check(_lib.load().sdmm_kdtree_workspace_size(ctypes.byref(self._c), N, ctypes.byref(n)),
+              "sdmm_kdtree_workspace_size")
+        ws = torch.empty(max(1, n.value), dtype=torch.uint8, device=samples.device)
+        out = torch.empty_like(samples)
+        out_off = torch.empty(self._c.cap_leaves + 1, dtype=torch.int64, device=samples.device)
+        base, st = out.data_ptr(), out.stride(0) * out.element_size()
+        ob = _lib.SampleBuffers(*[base + i * st for i in range(7)], out_off.data_ptr(), 0, 0)
+        sb, sst = samples.data_ptr(), samples.stride(0) * samples.element_size()
+        off = offsets if offsets is not None else torch.zeros(2, dtype=torch.int64, device=samples.device)
+        si = _lib.Samples(*[sb + i * sst for i in range(7)], off.data_ptr(),
+                          self._c.n_leaves if offsets is not None else 1, N)
+        return out, out_off, ob, si, ws
+
+    def bin(self, samples: torch.Tensor, stream=None) -> "SampleBatch":
+        """Samples (7, N) in any order, sorted by leaf (stable), with the leaf offsets."""
+        out, out_off, ob, si, ws = self._run(samples, None, None, stream)
+        check(_lib.load().sdmm_kdtree_bin(ctypes.byref(self._c), ctypes.byref(si), ctypes.byref(ob), _ptr(ws),
+                                          ws.numel(), _stream(stream)), "sdmm_kdtree_bin")
+        return SampleBatch(out, out_off[: ob.R + 1].clone())
+
+    def refine(self, batch: "SampleBatch", c: int = 16000, stream=None):
+        """Split every leaf holding more than c samples (Sec. 4.2); returns the
+        samples sorted by the new leaves and, per new leaf, the leaf it came from."""
+        out, out_off, ob, si, ws = self._run(batch.samples, batch.offsets, c, stream)
+        parent = torch.empty(self._c.cap_leaves, dtype=torch.int64, device=out.device)
+        check(_lib.load().sdmm_kdtree_refine(ctypes.byref(self._c), int(c), ctypes.byref(si), ctypes.byref(ob),
+                                             _ptr(parent), _ptr(ws), ws.numel(), _stream(stream)),
+              "sdmm_kdtree_refine")
+        return SampleBatch(out, out_off[: ob.R + 1].clone()), parent[: ob.R].clone()
+
+
+def gather_regions(state: "MixtureState", src: torch.Tensor, stream=None) -> "MixtureState":
+    """A new state whose region r is a copy of region src[r] of `state`."""
+    src = src.to(torch.int64).contiguous()
+    out = MixtureState(src.numel(), state.K, device=state.pi.device)
+    check(_lib.load().sdmm_gather_regions(state.K, src.numel(), _ptr(src), ctypes.byref(state.c()),
+                                          ctypes.byref(out.c()), _stream(stream)), "sdmm_gather_regions")
+    return out
 
 
 def Grid(lo, hi, dims) -> _lib.Grid:

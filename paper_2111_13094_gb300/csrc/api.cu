@@ -717,4 +717,213 @@ sdmm_status sdmm_autotune(const sdmm_config* cfg, const sdmm_samples* s, const s
     return SDMM_OK;
 }
 
+
+// ===========================================================================
+// Spatial kD-tree (Sec. 4.2, Sec. 4.3)
+}  // extern "C"
+
+namespace {
+
+struct KdLayout {
+    size_t perm[2], seg_off[2], seg_node[2], seg_parent[2], seg_axis, seg_split, seg_flag, seg_new, seg_sum,
+        seg_left, tile_seg, tile_start, tile_left, tile_prefix, first_tile, counters, total;
+    int64_t max_tiles;
+};
+
+KdLayout kd_layout(const sdmm_kdtree* t, int64_t N) {
+    KdLayout L{};
+    const size_t S = (size_t)t->cap_leaves + 1;
+    L.max_tiles = N / 1024 + (int64_t)t->cap_leaves + 1;
+    const size_t T = (size_t)L.max_tiles;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o = align_up(o + bytes);
+        return at;
+    };
+    for (int b = 0; b < 2; ++b) {
+        L.perm[b] = take(sizeof(int32_t) * (size_t)N);
+        L.seg_off[b] = take(sizeof(int64_t) * (S + 1));
+        L.seg_node[b] = take(sizeof(int32_t) * S);
+        L.seg_parent[b] = take(sizeof(int64_t) * S);
+    }
+    L.seg_axis = take(sizeof(int32_t) * S);
+    L.seg_split = take(sizeof(double) * S);
+    L.seg_flag = take(sizeof(int32_t) * S);
+    L.seg_new = take(sizeof(int32_t) * S);
+    L.seg_sum = take(sizeof(unsigned long long) * 6 * S);
+    L.seg_left = take(sizeof(unsigned long long) * S);
+    L.tile_seg = take(sizeof(int32_t) * T);
+    L.tile_start = take(sizeof(int64_t) * T);
+    L.tile_left = take(sizeof(int32_t) * T);
+    L.tile_prefix = take(sizeof(int64_t) * T);
+    L.first_tile = take(sizeof(int32_t) * S);
+    L.counters = take(sizeof(int32_t) * 4);
+    L.total = o;
+    return L;
+}
+
+KdWork kd_work(void* ws, const KdLayout& L) {
+    char* b = static_cast<char*>(ws);
+    KdWork w{};
+    for (int i = 0; i < 2; ++i) {
+        w.perm[i] = reinterpret_cast<int32_t*>(b + L.perm[i]);
+        w.seg_off[i] = reinterpret_cast<int64_t*>(b + L.seg_off[i]);
+        w.seg_node[i] = reinterpret_cast<int32_t*>(b + L.seg_node[i]);
+        w.seg_parent[i] = reinterpret_cast<int64_t*>(b + L.seg_parent[i]);
+    }
+    w.seg_axis = reinterpret_cast<int32_t*>(b + L.seg_axis);
+    w.seg_split = reinterpret_cast<double*>(b + L.seg_split);
+    w.seg_flag = reinterpret_cast<int32_t*>(b + L.seg_flag);
+    w.seg_new = reinterpret_cast<int32_t*>(b + L.seg_new);
+    w.seg_sum = reinterpret_cast<unsigned long long*>(b + L.seg_sum);
+    w.seg_left = reinterpret_cast<unsigned long long*>(b + L.seg_left);
+    w.tile_seg = reinterpret_cast<int32_t*>(b + L.tile_seg);
+    w.tile_start = reinterpret_cast<int64_t*>(b + L.tile_start);
+    w.tile_left = reinterpret_cast<int32_t*>(b + L.tile_left);
+    w.tile_prefix = reinterpret_cast<int64_t*>(b + L.tile_prefix);
+    w.first_tile = reinterpret_cast<int32_t*>(b + L.first_tile);
+    w.counters = reinterpret_cast<int32_t*>(b + L.counters);
+    w.max_tiles = L.max_tiles;
+    return w;
+}
+
+sdmm_status kd_check(const sdmm_kdtree* t) {
+    if (!t || !t->axis || !t->split || !t->left || !t->leaf) return fail(SDMM_ERR_INVALID_ARG, "kD-tree arrays are NULL");
+    if (t->n_nodes < 1 || t->n_nodes > t->cap_nodes || t->n_leaves < 1 || t->n_leaves > t->cap_leaves)
+        return fail(SDMM_ERR_INVALID_ARG, "kD-tree counts %d nodes / %d leaves exceed capacities %d / %d",
+                    t->n_nodes, t->n_leaves, t->cap_nodes, t->cap_leaves);
+    return SDMM_OK;
+}
+
+sdmm_status kd_streams(const sdmm_samples* in, const sdmm_sample_buffers* out) {
+    if (!in || !out) return fail(SDMM_ERR_INVALID_ARG, "samples are NULL");
+    if (in->N < 0 || in->N >= (int64_t(1) << 31)) return fail(SDMM_ERR_INVALID_ARG, "N = %lld: 0 <= N < 2^31", (long long)in->N);
+    if (in->N > 0 && (!in->px || !in->py || !in->pz || !in->ox || !in->oy || !in->oz || !in->w))
+        return fail(SDMM_ERR_INVALID_ARG, "input streams are NULL");
+    if (!out->px || !out->py || !out->pz || !out->ox || !out->oy || !out->oz || !out->w || !out->offsets)
+        return fail(SDMM_ERR_INVALID_ARG, "output streams are NULL");
+    return SDMM_OK;
+}
+
+BatchDesc desc_of(const sdmm_samples* s) {
+    BatchDesc d{};
+    d.p[0] = s->px; d.p[1] = s->py; d.p[2] = s->pz; d.p[3] = s->ox; d.p[4] = s->oy; d.p[5] = s->oz; d.p[6] = s->w;
+    return d;
+}
+
+BatchDesc desc_of(const sdmm_sample_buffers* s) {
+    BatchDesc d{};
+    d.p[0] = s->px; d.p[1] = s->py; d.p[2] = s->pz; d.p[3] = s->ox; d.p[4] = s->oy; d.p[5] = s->oz; d.p[6] = s->w;
+    return d;
+}
+
+}  // namespace
+
+extern "C" {
+
+sdmm_status sdmm_kdtree_grid(sdmm_kdtree* t, int32_t levels, sdmm_stream stream) {
+    if (!t || !t->axis || !t->split || !t->left || !t->leaf) return fail(SDMM_ERR_INVALID_ARG, "kD-tree arrays are NULL");
+    if (levels < 0 || levels > 7) return fail(SDMM_ERR_INVALID_ARG, "levels %d: 0..7", levels);
+    const int64_t nodes = (int64_t(1) << (3 * levels + 1)) - 1, leaves = int64_t(1) << (3 * levels);
+    if (nodes > t->cap_nodes || leaves > t->cap_leaves)
+        return fail(SDMM_ERR_WORKSPACE, "grid of %lld nodes / %lld leaves exceeds capacities %d / %d",
+                    (long long)nodes, (long long)leaves, t->cap_nodes, t->cap_leaves);
+    SDMM_CUDA(launch_kd_grid(stream, levels, t->axis, t->split, t->left, t->leaf), "kd_grid");
+    SDMM_CUDA(cudaStreamSynchronize(stream), "kd_grid");
+    t->n_nodes = (int32_t)nodes;
+    t->n_leaves = (int32_t)leaves;
+    return SDMM_OK;
+}
+
+sdmm_status sdmm_kdtree_lookup(const sdmm_kdtree* t, int64_t Q, const float* px, const float* py, const float* pz,
+                               int32_t* leaf, sdmm_stream stream) {
+    sdmm_status e = kd_check(t);
+    if (e) return e;
+    if (Q < 0) return fail(SDMM_ERR_INVALID_ARG, "Q < 0");
+    if (Q > 0 && (!px || !py || !pz || !leaf)) return fail(SDMM_ERR_INVALID_ARG, "points/leaf are NULL");
+    SDMM_CUDA(launch_kd_lookup(stream, t->axis, t->split, t->left, t->leaf, t->n_nodes, Q, px, py, pz, leaf),
+              "kd_lookup");
+    return SDMM_OK;
+}
+
+sdmm_status sdmm_kdtree_workspace_size(const sdmm_kdtree* t, int64_t N, size_t* bytes) {
+    if (!t || !bytes) return fail(SDMM_ERR_INVALID_ARG, "NULL argument");
+    if (N < 0 || N >= (int64_t(1) << 31)) return fail(SDMM_ERR_INVALID_ARG, "N = %lld: 0 <= N < 2^31", (long long)N);
+    if (t->cap_leaves < 1 || t->cap_nodes < 1) return fail(SDMM_ERR_INVALID_ARG, "capacities must be positive");
+    *bytes = kd_layout(t, N).total;
+    return SDMM_OK;
+}
+
+static sdmm_status kd_run(sdmm_kdtree* t, int binning, int64_t c, const sdmm_samples* in, sdmm_sample_buffers* out,
+                          int64_t* leaf_parent, void* ws, size_t ws_bytes, sdmm_stream stream) {
+    const KdLayout L = kd_layout(t, in->N);
+    if (!ws) return fail(SDMM_ERR_INVALID_ARG, "workspace is NULL");
+    if (reinterpret_cast<uintptr_t>(ws) % kAlign) return fail(SDMM_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    if (ws_bytes < L.total) return fail(SDMM_ERR_WORKSPACE, "workspace %zu bytes < required %zu", ws_bytes, L.total);
+    const KdWork w = kd_work(ws, L);
+    const int64_t N = in->N;
+    const int32_t S0 = binning ? 1 : t->n_leaves;
+    SDMM_CUDA(launch_kd_prepare(stream, w, binning, t->axis, t->leaf, t->n_nodes, S0, in->offsets, N), "kd_prepare");
+    int32_t *perm = nullptr, S = 0;
+    int64_t *seg_off = nullptr, *seg_parent = nullptr;
+    int overflow = 0;
+    int32_t n_nodes = t->n_nodes, n_leaves = t->n_leaves;
+    SDMM_CUDA(kd_rounds(stream, w, binning, c, t->axis, t->split, t->left, t->leaf, &n_nodes, &n_leaves,
+                        t->cap_nodes, t->cap_leaves, S0, N, in->px, in->py, in->pz, &perm, &seg_off, &seg_parent,
+                        &S, &overflow),
+              "kd_rounds");
+    t->n_nodes = n_nodes;
+    t->n_leaves = n_leaves;
+    if (overflow)
+        return fail(SDMM_ERR_WORKSPACE, "kD-tree capacities (%d nodes, %d leaves) too small", t->cap_nodes,
+                    t->cap_leaves);
+    if (binning && S != t->n_leaves)
+        return fail(SDMM_ERR_INVALID_ARG, "binning reached %d of %d leaves (tree deeper than 64 levels?)", S,
+                    t->n_leaves);
+    SDMM_CUDA(launch_kd_gather(stream, N, perm, desc_of(in), desc_of(out)), "kd_gather");
+    SDMM_CUDA(cudaMemcpyAsync(out->offsets, seg_off, sizeof(int64_t) * ((size_t)S + 1), cudaMemcpyDeviceToDevice,
+                              stream),
+              "kd_offsets");
+    if (leaf_parent)
+        SDMM_CUDA(cudaMemcpyAsync(leaf_parent, seg_parent, sizeof(int64_t) * (size_t)S, cudaMemcpyDeviceToDevice,
+                                  stream),
+                  "kd_parent");
+    SDMM_CUDA(cudaStreamSynchronize(stream), "kd_run");
+    out->R = S;
+    out->N = N;
+    return SDMM_OK;
+}
+
+sdmm_status sdmm_kdtree_bin(const sdmm_kdtree* t, const sdmm_samples* in, sdmm_sample_buffers* out, void* ws,
+                            size_t ws_bytes, sdmm_stream stream) {
+    sdmm_status e = kd_check(t);
+    if (!e) e = kd_streams(in, out);
+    if (e) return e;
+    // the tree is not modified by binning
+    sdmm_kdtree tt = *t;
+    return kd_run(&tt, 1, -1, in, out, nullptr, ws, ws_bytes, stream);
+}
+
+sdmm_status sdmm_kdtree_refine(sdmm_kdtree* t, int64_t c, const sdmm_samples* in, sdmm_sample_buffers* out,
+                               int64_t* leaf_parent, void* ws, size_t ws_bytes, sdmm_stream stream) {
+    sdmm_status e = kd_check(t);
+    if (!e) e = kd_streams(in, out);
+    if (e) return e;
+    if (c < 1) return fail(SDMM_ERR_INVALID_ARG, "c = %lld must be >= 1", (long long)c);
+    if (!in->offsets || in->R != t->n_leaves)
+        return fail(SDMM_ERR_INVALID_ARG, "in->R = %lld must equal the tree's %d leaves", (long long)in->R, t->n_leaves);
+    if (!leaf_parent) return fail(SDMM_ERR_INVALID_ARG, "leaf_parent is NULL");
+    return kd_run(t, 0, c, in, out, leaf_parent, ws, ws_bytes, stream);
+}
+
+sdmm_status sdmm_gather_regions(int32_t K, int64_t R_out, const int64_t* src, const sdmm_state* in,
+                                sdmm_state* out, sdmm_stream stream) {
+    if (K < 1 || K > SDMM_MAX_K) return fail(SDMM_ERR_INVALID_ARG, "K = %d", K);
+    if (R_out < 0 || (R_out > 0 && (!src || !in || !out))) return fail(SDMM_ERR_INVALID_ARG, "NULL argument");
+    if (R_out == 0) return SDMM_OK;
+    SDMM_CUDA(launch_gather_state(stream, K, R_out, src, *in, *out), "gather_regions");
+    return SDMM_OK;
+}
+
 }  // extern "C"

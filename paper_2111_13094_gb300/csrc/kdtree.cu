@@ -1,0 +1,586 @@
+// kdtree.cu -- the spatial kD-tree of the regions on the GPU (Sec. 4.2
+// "Refinement of the spatial kD-tree", Sec. 4.3 "Initialization"):
+//
+//  k_kd_grid        regular pre-subdivision, heap-numbered nodes
+//  k_kd_lookup      leaf of each point by descent
+//  binning and refinement, both as rounds of stable segment partitions:
+//    k_kd_tiles     tiles of 1,024 samples, none spanning two segments
+//    k_kd_stats     fixed-point position sums of the segments to split
+//    k_kd_plan      split plane of each segment (tree node, or mean along the
+//                   axis of largest variance)
+//    k_kd_count     per tile: samples left of the plane
+//    k_kd_scan      which segments split, their new indices, tile prefixes
+//    k_kd_scatter   stable partition of every split segment
+//    k_kd_segments  new segments, new tree nodes, parents of the new leaves
+//  k_kd_gather      the sample streams in the final order
+//  k_gather_state   mixture states copied from the parent regions
+//
+// Leaves are numbered in tree order (left before right), so a leaf's
+// samples are the leaf-th contiguous segment once sorted.  Means and
+// variances come from exact integer sums of q = floor(clamp(x, 0, 1) 2^32)
+// and q2 = floor(clamp(x, 0, 1)^2 2^32): every implementation places the
+// plane identically, and atomics on integers keep the rounds deterministic.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace sdmm {
+
+constexpr int kKdTile = 1024;
+constexpr double kTwo32 = 4294967296.0;
+
+// ---------------------------------------------------------------------------
+// Pre-subdivision: every axis split at the centre of its cell, x then y then
+// z, `levels` times.  Heap numbering: children of node n are 2n+1 and 2n+2,
+// the leaves (depth 3 levels) are the last level, left to right.
+__global__ void k_kd_grid(int levels, int32_t* axis, double* split, int32_t* left, int32_t* leaf) {
+    const int depth_max = 3 * levels;
+    const int64_t n_nodes = (int64_t(1) << (depth_max + 1)) - 1;
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= n_nodes) return;
+    int d = 0;
+    while (((int64_t(1) << (d + 1)) - 1) <= n) ++d;           // depth of node n
+    const int64_t p = n - ((int64_t(1) << d) - 1);              // position within its level
+    double lo[3] = {0.0, 0.0, 0.0}, hi[3] = {1.0, 1.0, 1.0};
+    for (int l = 0; l < d; ++l) {                               // the path from the root
+        const int a = l % 3;
+        const double mid = 0.5 * (lo[a] + hi[a]);
+        if ((p >> (d - 1 - l)) & 1) lo[a] = mid;
+        else hi[a] = mid;
+    }
+    if (d == depth_max) {
+        axis[n] = -1;
+        split[n] = 0.0;
+        left[n] = -1;
+        leaf[n] = (int32_t)p;
+    } else {
+        const int a = d % 3;
+        axis[n] = a;
+        split[n] = 0.5 * (lo[a] + hi[a]);
+        left[n] = (int32_t)(2 * n + 1);
+        leaf[n] = -1;
+    }
+}
+
+__global__ void k_kd_lookup(const int32_t* __restrict__ axis, const double* __restrict__ split,
+                            const int32_t* __restrict__ left, const int32_t* __restrict__ leaf, int max_depth,
+                            int64_t Q, const float* __restrict__ px, const float* __restrict__ py,
+                            const float* __restrict__ pz, int32_t* __restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Q) return;
+    const float x[3] = {px[i], py[i], pz[i]};
+    int n = 0;
+    for (int d = 0; d <= max_depth && axis[n] >= 0; ++d) {      // bounded by the tree's node count
+        const int a = axis[n];
+        n = (double)x[a] < split[n] ? left[n] : left[n] + 1;
+    }
+    out[i] = axis[n] < 0 ? leaf[n] : -1;
+}
+
+// ---------------------------------------------------------------------------
+// Rounds of segment partitions.  State of a round (workspace, see api.cu):
+//   seg_off[S+1] (int64), seg_node[S], seg_parent[S]    the current segments
+//   perm[N]                                             sample order (int32)
+// Per segment: flag (split or not), axis, plane, left count; per tile: its
+// segment, first sample, left count and its exclusive prefix in the segment.
+struct KdRound {
+    const int64_t* seg_off;
+    const int32_t* seg_node;
+    const int64_t* seg_parent;
+    int32_t S;
+    int32_t* seg_axis;
+    double* seg_split;
+    int32_t* seg_flag;           // 1: the segment splits this round
+    int32_t* seg_new;            // new index of the segment (its left part)
+    unsigned long long* seg_sum; // [S][6] fixed-point sums (refinement only)
+    unsigned long long* seg_left;
+    int32_t* tile_seg;
+    int64_t* tile_start;
+    int32_t* tile_left;
+    int64_t* tile_prefix;
+    int32_t* counters;           // [0] tiles, [1] splits
+};
+
+// Tiles: ceil(M_s / 1024) per segment (empty segments get none), in segment
+// order.  One CTA of 1024 threads, int64 block scan over the segments.
+__global__ void __launch_bounds__(1024) k_kd_tiles(KdRound k, int64_t max_tiles) {
+    __shared__ int64_t s_warp[32];
+    __shared__ int64_t s_carry;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_carry = 0;
+    __syncthreads();
+    for (int base = 0; base < k.S; base += 1024) {
+        const int s = base + tid;
+        int64_t nt = 0;
+        if (s < k.S) nt = (k.seg_off[s + 1] - k.seg_off[s] + kKdTile - 1) / kKdTile;
+        int64_t v = nt;
+        for (int d = 1; d < 32; d <<= 1) {
+            const int64_t u = __shfl_up_sync(0xffffffffu, v, d);
+            if (lane >= d) v += u;
+        }
+        if (lane == 31) s_warp[warp] = v;
+        __syncthreads();
+        if (warp == 0) {
+            int64_t w = s_warp[lane];
+            for (int d = 1; d < 32; d <<= 1) {
+                const int64_t u = __shfl_up_sync(0xffffffffu, w, d);
+                if (lane >= d) w += u;
+            }
+            s_warp[lane] = w;
+        }
+        __syncthreads();
+        const int64_t first = s_carry + v - nt + (warp > 0 ? s_warp[warp - 1] : 0);
+        if (s < k.S)
+            for (int64_t j = 0; j < nt && first + j < max_tiles; ++j) {
+                k.tile_seg[first + j] = s;
+                k.tile_start[first + j] = k.seg_off[s] + j * kKdTile;
+            }
+        __syncthreads();
+        if (tid == 1023) s_carry = first + nt;
+        __syncthreads();
+    }
+    if (tid == 0) k.counters[0] = (int32_t)min(s_carry, max_tiles);
+}
+
+__device__ __forceinline__ void fixed_point(float x, unsigned long long& q, unsigned long long& q2) {
+    const double xc = fmin(fmax((double)x, 0.0), 1.0);
+    q = (unsigned long long)floor(xc * kTwo32);
+    q2 = (unsigned long long)floor(__dmul_rn(xc, xc) * kTwo32);
+}
+
+// fixed-point sums of the samples of segments holding more than c of them
+__global__ void __launch_bounds__(kKdTile) k_kd_stats(KdRound k, const int32_t* __restrict__ perm,
+                                                     const float* __restrict__ px, const float* __restrict__ py,
+                                                     const float* __restrict__ pz, int64_t c) {
+    __shared__ unsigned long long s_red[32][6];
+    const int t = blockIdx.x;
+    if (t >= k.counters[0]) return;
+    const int s = k.tile_seg[t];
+    const int64_t M = k.seg_off[s + 1] - k.seg_off[s];
+    if (M <= c) return;                                        // (uniform per CTA)
+    const int64_t i = k.tile_start[t] + threadIdx.x;
+    unsigned long long v[6] = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull};
+    if (i < k.seg_off[s + 1]) {
+        const int32_t j = perm[i];
+        fixed_point(px[j], v[0], v[3]);
+        fixed_point(py[j], v[1], v[4]);
+        fixed_point(pz[j], v[2], v[5]);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+        if (lane == 0) s_red[warp][q] = v[q];
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        unsigned long long a = 0ull;
+        for (int w = 0; w < kKdTile / 32; ++w) a += s_red[w][threadIdx.x];
+        atomicAdd(k.seg_sum + (int64_t)s * 6 + threadIdx.x, a);
+    }
+}
+
+// Split plane of every segment.  Binning (c < 0): the segment's tree node
+// (leaves keep their segment).  Refinement: more than c samples -> the mean
+// along the axis of largest variance (lowest axis on ties), from the sums.
+__global__ void k_kd_plan(KdRound k, const int32_t* __restrict__ tree_axis, const double* __restrict__ tree_split,
+                          int64_t c) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= k.S) return;
+    const int64_t M = k.seg_off[s + 1] - k.seg_off[s];
+    int a = -1;
+    double pl = 0.0;
+    if (c < 0) {
+        a = tree_axis[k.seg_node[s]];
+        pl = a >= 0 ? tree_split[k.seg_node[s]] : 0.0;
+    } else if (M > c) {
+        double best = -1.0;
+        for (int q = 0; q < 3; ++q) {
+            const double S1 = (double)k.seg_sum[(int64_t)s * 6 + q];
+            const double S2 = (double)k.seg_sum[(int64_t)s * 6 + 3 + q];
+            const double mean = __ddiv_rn(__ddiv_rn(S1, (double)M), kTwo32);
+            const double var = __dsub_rn(__ddiv_rn(__ddiv_rn(S2, (double)M), kTwo32), __dmul_rn(mean, mean));
+            if (var > best) {
+                best = var;
+                a = q;
+                pl = mean;
+            }
+        }
+    }
+    k.seg_axis[s] = a;
+    k.seg_split[s] = pl;
+    k.seg_left[s] = 0ull;
+}
+
+// per tile: samples strictly left of the plane (x[axis] < split)
+__global__ void __launch_bounds__(kKdTile) k_kd_count(KdRound k, const int32_t* __restrict__ perm,
+                                                     const float* __restrict__ px, const float* __restrict__ py,
+                                                     const float* __restrict__ pz) {
+    __shared__ int s_red[32];
+    const int t = blockIdx.x;
+    if (t >= k.counters[0]) return;
+    const int s = k.tile_seg[t];
+    const int a = k.seg_axis[s];
+    const int64_t i = k.tile_start[t] + threadIdx.x;
+    int f = 0;
+    if (a >= 0 && i < k.seg_off[s + 1]) {
+        const int32_t j = perm[i];
+        const float x = a == 0 ? px[j] : (a == 1 ? py[j] : pz[j]);
+        f = (double)x < k.seg_split[s] ? 1 : 0;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int n = __popc(__ballot_sync(0xffffffffu, f));
+    if (lane == 0) s_red[warp] = n;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int tot = 0;
+        for (int w = 0; w < kKdTile / 32; ++w) tot += s_red[w];
+        k.tile_left[t] = tot;
+        if (a >= 0) atomicAdd(k.seg_left + s, (unsigned long long)tot);
+    }
+}
+
+// Which segments split (binning: every internal node; refinement: both
+// sides non-empty), their new indices, and the exclusive prefix of each
+// tile's left count within its segment.  One CTA of 1024 threads.
+__global__ void __launch_bounds__(1024) k_kd_scan(KdRound k, int binning) {
+    __shared__ int32_t s_warp[32];
+    __shared__ int32_t s_carry;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_carry = 0;
+    __syncthreads();
+    for (int base = 0; base < k.S; base += 1024) {
+        const int s = base + tid;
+        int f = 0;
+        if (s < k.S && k.seg_axis[s] >= 0) {
+            const int64_t M = k.seg_off[s + 1] - k.seg_off[s];
+            const int64_t L = (int64_t)k.seg_left[s];
+            f = binning ? 1 : (L > 0 && L < M ? 1 : 0);
+        }
+        int v = f;
+        for (int d = 1; d < 32; d <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, v, d);
+            if (lane >= d) v += u;
+        }
+        if (lane == 31) s_warp[warp] = v;
+        __syncthreads();
+        if (warp == 0) {
+            int w = s_warp[lane];
+            for (int d = 1; d < 32; d <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, w, d);
+                if (lane >= d) w += u;
+            }
+            s_warp[lane] = w;
+        }
+        __syncthreads();
+        const int before = s_carry + v - f + (warp > 0 ? s_warp[warp - 1] : 0);
+        if (s < k.S) {
+            k.seg_flag[s] = f;
+            k.seg_new[s] = s + before;
+        }
+        __syncthreads();
+        if (tid == 1023) s_carry = before + f;
+        __syncthreads();
+    }
+    if (tid == 0) k.counters[1] = s_carry;
+    __syncthreads();
+    // tile prefixes (tiles of a segment are consecutive)
+    const int nt = k.counters[0];
+    __shared__ int64_t s_run;
+    __shared__ int64_t s_w64[32];
+    if (tid == 0) s_run = 0;
+    __syncthreads();
+    for (int base = 0; base < nt; base += 1024) {
+        const int t = base + tid;
+        int64_t c = t < nt ? k.tile_left[t] : 0;
+        int64_t v = c;
+        for (int d = 1; d < 32; d <<= 1) {
+            const int64_t u = __shfl_up_sync(0xffffffffu, v, d);
+            if (lane >= d) v += u;
+        }
+        if (lane == 31) s_w64[warp] = v;
+        __syncthreads();
+        if (warp == 0) {
+            int64_t w = s_w64[lane];
+            for (int d = 1; d < 32; d <<= 1) {
+                const int64_t u = __shfl_up_sync(0xffffffffu, w, d);
+                if (lane >= d) w += u;
+            }
+            s_w64[lane] = w;
+        }
+        __syncthreads();
+        const int64_t excl = s_run + v - c + (warp > 0 ? s_w64[warp - 1] : 0);
+        if (t < nt) k.tile_prefix[t] = excl;          // global exclusive prefix
+        __syncthreads();
+        if (tid == 1023) s_run = excl + c;
+        __syncthreads();
+    }
+}
+
+// Stable partition: within a split segment, left samples first (in order),
+// then the right ones (in order); other segments are copied.
+__global__ void __launch_bounds__(kKdTile) k_kd_scatter(KdRound k, const int32_t* __restrict__ perm_in,
+                                                       int32_t* __restrict__ perm_out,
+                                                       const float* __restrict__ px, const float* __restrict__ py,
+                                                       const float* __restrict__ pz, const int32_t* __restrict__ first_tile) {
+    __shared__ int s_warp[32];
+    const int t = blockIdx.x;
+    if (t >= k.counters[0]) return;
+    const int s = k.tile_seg[t];
+    const int64_t o0 = k.seg_off[s], o1 = k.seg_off[s + 1];
+    const int64_t i = k.tile_start[t] + threadIdx.x;
+    const bool in = i < o1;
+    const int32_t j = in ? perm_in[i] : 0;
+    if (!k.seg_flag[s]) {
+        if (in) perm_out[i] = j;
+        return;                                               // (uniform per CTA)
+    }
+    const int a = k.seg_axis[s];
+    int f = 0;
+    if (in) {
+        const float x = a == 0 ? px[j] : (a == 1 ? py[j] : pz[j]);
+        f = (double)x < k.seg_split[s] ? 1 : 0;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned bal = __ballot_sync(0xffffffffu, f);
+    const int rank_w = __popc(bal & ((1u << lane) - 1u));
+    if (lane == 0) s_warp[warp] = __popc(bal);
+    __syncthreads();
+    int before = 0;
+    for (int w = 0; w < warp; ++w) before += s_warp[w];
+    const int lrank = before + rank_w;                        // left samples before i in the tile
+    const int64_t lpre = k.tile_prefix[t] - k.tile_prefix[first_tile[s]];   // left samples of earlier tiles
+    const int64_t L = (int64_t)k.seg_left[s];
+    const int64_t pos_in_seg = i - o0;
+    if (in) {
+        int64_t dst;
+        if (f) dst = o0 + lpre + lrank;
+        else dst = o0 + L + (pos_in_seg - (lpre + lrank));
+        perm_out[dst] = j;
+    }
+}
+
+// first tile of every segment (for the prefix offsets above); -1 if empty
+__global__ void k_kd_first_tile(KdRound k, int32_t* first_tile) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= k.counters[0]) return;
+    const int s = k.tile_seg[t];
+    if (t == 0 || k.tile_seg[t - 1] != s) first_tile[s] = t;
+}
+
+// New segments; refinement also writes the tree (two new leaf nodes per
+// split, appended from node n_nodes on) and leaf indices of kept leaves.
+__global__ void k_kd_segments(KdRound k, int binning, int32_t* tree_axis, double* tree_split, int32_t* tree_left,
+                              int32_t* tree_leaf, int32_t n_nodes, int64_t* seg_off_out, int32_t* seg_node_out,
+                              int64_t* seg_parent_out, int64_t N) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= k.S) return;
+    const int ns = k.seg_new[s];
+    const int32_t node = k.seg_node[s];
+    const int64_t off = k.seg_off[s];
+    const int64_t par = k.seg_parent[s];
+    if (k.seg_flag[s]) {
+        const int64_t L = (int64_t)k.seg_left[s];
+        int32_t l;
+        if (binning) {
+            l = tree_left[node];
+        } else {
+            l = n_nodes + 2 * (ns - s);
+            tree_axis[node] = k.seg_axis[s];
+            tree_split[node] = k.seg_split[s];
+            tree_left[node] = l;
+            tree_leaf[node] = -1;
+            tree_axis[l] = -1;
+            tree_axis[l + 1] = -1;
+            tree_split[l] = tree_split[l + 1] = 0.0;
+            tree_left[l] = tree_left[l + 1] = -1;
+            tree_leaf[l] = ns;
+            tree_leaf[l + 1] = ns + 1;
+        }
+        seg_node_out[ns] = l;
+        seg_node_out[ns + 1] = l + 1;
+        seg_off_out[ns] = off;
+        seg_off_out[ns + 1] = off + L;
+        seg_parent_out[ns] = par;
+        seg_parent_out[ns + 1] = par;
+    } else {
+        if (!binning) tree_leaf[node] = ns;
+        seg_node_out[ns] = node;
+        seg_off_out[ns] = off;
+        seg_parent_out[ns] = par;
+    }
+    if (s == k.S - 1) seg_off_out[ns + 1 + k.seg_flag[s]] = N;
+}
+
+// leaf -> node of every leaf node (initial segments of a refinement)
+__global__ void k_kd_leaf_nodes(const int32_t* __restrict__ axis, const int32_t* __restrict__ leaf, int32_t n_nodes,
+                                int32_t* seg_node) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n < n_nodes && axis[n] < 0) seg_node[leaf[n]] = n;
+}
+
+__global__ void k_kd_iota(int32_t* perm, int64_t N, int64_t* parent, int32_t S) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) perm[i] = (int32_t)i;
+    if (parent != nullptr && i < S) parent[i] = i;
+}
+
+__global__ void k_kd_gather(int64_t N, const int32_t* __restrict__ perm, BatchDesc in, BatchDesc out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int32_t j = perm[i];
+#pragma unroll
+    for (int q = 0; q < 7; ++q) const_cast<float*>(out.p[q])[i] = in.p[q][j];
+}
+
+// Mixture states of new regions copied from their source regions (the
+// parent leaf's mixture is copied into both children, Sec. 4.2).
+__global__ void k_gather_state(int K, int64_t R_out, const int64_t* __restrict__ src, sdmm_state in,
+                               sdmm_state out) {
+    const int64_t r = blockIdx.x;
+    if (r >= R_out) return;
+    const int64_t q = src[r];
+    for (int e = threadIdx.x; e < K; e += blockDim.x) {
+        const int64_t a = r * K + e, b = q * K + e;
+        out.pi[a] = in.pi[b];
+        out.S0[a] = in.S0[b];
+        for (int c = 0; c < 3; ++c) {
+            out.mu_x[a * 3 + c] = in.mu_x[b * 3 + c];
+            out.mu_w[a * 3 + c] = in.mu_w[b * 3 + c];
+        }
+        for (int p = 0; p < 15; ++p) {
+            out.L[a * 15 + p] = in.L[b * 15 + p];
+            out.S2[a * 15 + p] = in.S2[b * 15 + p];
+        }
+        for (int p = 0; p < kE; ++p) out.etab[a * kE + p] = in.etab[b * kE + p];
+        for (int p = 0; p < kQ; ++p) out.qtab[a * kQ + p] = in.qtab[b * kQ + p];
+    }
+    if (threadIdx.x == 0) {
+        out.Wbar[r] = in.Wbar[q];
+        out.n_seen[r] = in.n_seen[q];
+        out.step_j[r] = in.step_j[q];
+        out.status[r] = in.status[q];
+    }
+}
+
+// ---------------------------------------------------------------------------
+cudaError_t launch_kd_grid(cudaStream_t s, int levels, int32_t* axis, double* split, int32_t* left,
+                           int32_t* leaf) {
+    const int64_t n = (int64_t(1) << (3 * levels + 1)) - 1;
+    k_kd_grid<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(levels, axis, split, left, leaf);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_kd_lookup(cudaStream_t s, const int32_t* axis, const double* split, const int32_t* left,
+                             const int32_t* leaf, int max_depth, int64_t Q, const float* px, const float* py,
+                             const float* pz, int32_t* out) {
+    if (Q == 0) return cudaSuccess;
+    k_kd_lookup<<<(unsigned)((Q + 255) / 256), 256, 0, s>>>(axis, split, left, leaf, max_depth, Q, px, py, pz,
+                                                           out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_state(cudaStream_t s, int K, int64_t R_out, const int64_t* src, const sdmm_state& in,
+                                const sdmm_state& out) {
+    if (R_out == 0) return cudaSuccess;
+    k_gather_state<<<(unsigned)R_out, 32, 0, s>>>(K, R_out, src, in, out);
+    return cudaGetLastError();
+}
+
+// One binning or refinement pass over all rounds (host loop; one 4-byte
+// read-back per round).  ws layout in KdWork (api.cu).
+cudaError_t kd_rounds(cudaStream_t st, const KdWork& w, int binning, int64_t c, int32_t* tree_axis,
+                      double* tree_split, int32_t* tree_left, int32_t* tree_leaf, int32_t* n_nodes,
+                      int32_t* n_leaves, int32_t cap_nodes, int32_t cap_leaves, int32_t S0, int64_t N,
+                      const float* px, const float* py, const float* pz, int32_t** perm_final,
+                      int64_t** seg_off_final, int64_t** seg_parent_final, int32_t* S_final, int* overflow) {
+    int32_t S = S0;
+    int cur = 0;
+    *overflow = 0;
+    for (int round = 0; round < 64; ++round) {
+        KdRound k{};
+        k.seg_off = w.seg_off[cur];
+        k.seg_node = w.seg_node[cur];
+        k.seg_parent = w.seg_parent[cur];
+        k.S = S;
+        k.seg_axis = w.seg_axis;
+        k.seg_split = w.seg_split;
+        k.seg_flag = w.seg_flag;
+        k.seg_new = w.seg_new;
+        k.seg_sum = w.seg_sum;
+        k.seg_left = w.seg_left;
+        k.tile_seg = w.tile_seg;
+        k.tile_start = w.tile_start;
+        k.tile_left = w.tile_left;
+        k.tile_prefix = w.tile_prefix;
+        k.counters = w.counters;
+        const int64_t max_tiles = w.max_tiles;
+        cudaError_t e;
+        k_kd_tiles<<<1, 1024, 0, st>>>(k, max_tiles);
+        if (!binning) {
+            if ((e = cudaMemsetAsync(w.seg_sum, 0, sizeof(unsigned long long) * 6 * (size_t)S, st)) != cudaSuccess)
+                return e;
+            k_kd_stats<<<(unsigned)max_tiles, kKdTile, 0, st>>>(k, w.perm[cur & 1], px, py, pz, c);
+        }
+        k_kd_plan<<<(S + 255) / 256, 256, 0, st>>>(k, tree_axis, tree_split, binning ? -1 : c);
+        k_kd_count<<<(unsigned)max_tiles, kKdTile, 0, st>>>(k, w.perm[cur & 1], px, py, pz);
+        k_kd_scan<<<1, 1024, 0, st>>>(k, binning);
+        k_kd_first_tile<<<(unsigned)((max_tiles + 255) / 256), 256, 0, st>>>(k, w.first_tile);
+        int32_t splits = 0;
+        if ((e = cudaMemcpyAsync(&splits, w.counters + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+            return e;
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (splits == 0) break;
+        if (S + splits > cap_leaves || (!binning && *n_nodes + 2 * splits > cap_nodes)) {
+            *overflow = 1;
+            return cudaSuccess;
+        }
+        k_kd_scatter<<<(unsigned)max_tiles, kKdTile, 0, st>>>(k, w.perm[cur & 1], w.perm[(cur + 1) & 1], px, py, pz,
+                                                             w.first_tile);
+        k_kd_segments<<<(S + 255) / 256, 256, 0, st>>>(k, binning, tree_axis, tree_split, tree_left, tree_leaf,
+                                                      *n_nodes, w.seg_off[cur ^ 1], w.seg_node[cur ^ 1],
+                                                      w.seg_parent[cur ^ 1], N);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (!binning) {
+            *n_nodes += 2 * splits;
+            *n_leaves += splits;
+        }
+        S += splits;
+        cur ^= 1;
+    }
+    *perm_final = w.perm[cur & 1];
+    *seg_off_final = w.seg_off[cur];
+    *seg_parent_final = w.seg_parent[cur];
+    *S_final = S;
+    return cudaSuccess;
+}
+
+cudaError_t launch_kd_prepare(cudaStream_t st, const KdWork& w, int binning, const int32_t* tree_axis,
+                              const int32_t* tree_leaf, int32_t n_nodes, int32_t S0, const int64_t* offsets_in,
+                              int64_t N) {
+    k_kd_iota<<<(unsigned)((std::max<int64_t>(N, S0) + 255) / 256), 256, 0, st>>>(w.perm[0], N, w.seg_parent[0], S0);
+    if (binning) {
+        // one segment: the root with every sample
+        const int64_t off[2] = {0, N};
+        const int32_t root = 0;
+        cudaError_t e;
+        if ((e = cudaMemcpyAsync(w.seg_off[0], off, sizeof(off), cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
+        if ((e = cudaMemcpyAsync(w.seg_node[0], &root, sizeof(root), cudaMemcpyHostToDevice, st)) != cudaSuccess)
+            return e;
+        return cudaStreamSynchronize(st);
+    }
+    cudaError_t e = cudaMemcpyAsync(w.seg_off[0], offsets_in, sizeof(int64_t) * (S0 + 1), cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return e;
+    k_kd_leaf_nodes<<<(n_nodes + 255) / 256, 256, 0, st>>>(tree_axis, tree_leaf, n_nodes, w.seg_node[0]);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_kd_gather(cudaStream_t st, int64_t N, const int32_t* perm, const BatchDesc& in,
+                             const BatchDesc& out) {
+    if (N == 0) return cudaSuccess;
+    k_kd_gather<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(N, perm, in, out);
+    return cudaGetLastError();
+}
+
+}  // namespace sdmm
