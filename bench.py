@@ -345,6 +345,30 @@ def run_gpu(args):
                              "oracle at 1,024 x 65,536 (tests/precision_sweep.py)"}
         del tplan, tws, tst
 
+    # ---- the spatial kD-tree on this round's samples: binning into the
+    # pre-subdivided 8 x 8 x 8 grid, then refinement with c = 16,000 (Sec. 4.2)
+    kdres = None
+    if not args.no_kdtree:
+        tree = api.KdTree(1 << 20, 1 << 19, device=dev)
+        raw = batches[0].samples
+        times = []
+        for rep in range(3):
+            tree.grid(3)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            kb = tree.bin(raw)
+            t1 = time.perf_counter()
+            kr, kp = tree.refine(kb, c=16000)
+            t2 = time.perf_counter()
+            times.append((t1 - t0, t2 - t1))
+        tb = float(np.median([a for a, _ in times])) * 1e3
+        tr = float(np.median([b for _, b in times])) * 1e3
+        kdres = {"samples": N, "bin_ms": tb, "refine_ms": tr, "leaves_after": tree.n_leaves,
+                 "nodes_after": tree.n_nodes, "c": 16000,
+                 "bin_samples_per_s": N / (tb * 1e-3), "refine_samples_per_s": N / (tr * 1e-3),
+                 "note": "host wall time of the synchronous calls (one 4-byte read-back per tree level)"}
+        del tree, kb, kr, kp
+
     # ---- end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
@@ -407,7 +431,8 @@ def run_gpu(args):
                            "precision": args.precision},
                 "clocks": ck, "e2e": e2e,
                 "gpu_launches": args.steps * ROUNDS * (4 if prec == api.PREC_FP32 else 5),
-                "roofline": roof, "cpu_baseline": cpu, "queries": qres, "tensor_core": tcres}
+                "roofline": roof, "cpu_baseline": cpu, "queries": qres, "tensor_core": tcres,
+                "kdtree": kdres}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -424,6 +449,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--regions", type=int, default=4096, help="regions of the fit workload")
     ap.add_argument("--no-tc", action="store_true", help="skip the tensor-core (6xBF16) comparison")
+    ap.add_argument("--no-kdtree", action="store_true", help="skip the kD-tree binning/refinement timing")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "3xbf16", "tf32", "3xtf32", "6xbf16"],
                     help="E-step arithmetic: FP32 SIMT or a tensor-core contraction form")
     ap.add_argument("--no-e2e", action="store_true")
