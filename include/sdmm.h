@@ -436,6 +436,47 @@ sdmm_status sdmm_fit_regions_noalloc(const sdmm_config *cfg,
                                      sdmm_stream stream);
 
 /*
+ * ---- Product sampling with a BSDF mixture (Sec. 3.5 "Product Sampling from
+ * Mixed-Orientation Gaussians", Eq. product-distribution; Sec. 4.1 "Pruning
+ * before product sampling").
+ *
+ * Each query carries J BSDF lobes, already conditioned and rotated by the
+ * caller into the frame of the radiance mixtures: weight w (>= 0), unit mean
+ * direction mu (3 floats) and the packed lower Cholesky factor (l00, l10, l11)
+ * of the lobe's covariance in its own chart (the Duff basis of mu, as for the
+ * radiance components).  Only the two lobes of largest weight are used (lower
+ * index on ties).  Every (radiance component k, lobe j) pair is formed in the
+ * chart of mu_k with the lobe's covariance moved by J = J_log_{mu_k}(mu_j)
+ * J_exp_{mu_j}(0); the product of the two Gaussians there is one Gaussian of
+ * weight pi'_k w_j N(m_k; log_{mu_k}(mu_j), S1 + J S2 J^T).  A lobe at the
+ * antipode of mu_k makes no pair.
+ */
+typedef struct sdmm_bsdf_lobes {
+    const float *w;      /* [Q*J] lobe weights                              */
+    const float *mu;     /* [Q*J*3] unit mean directions                    */
+    const float *L;      /* [Q*J*3] (l00, l10, l11) in the lobe's chart     */
+    int32_t J;           /* lobes per query, 1..8                           */
+} sdmm_bsdf_lobes;
+
+/* One direction per query from the product mixture: the pair by inverse CDF
+   on u0 (pairs ordered by component, then lobe index), a Gaussian draw in its
+   chart (Box-Muller on 1 - u1, u2), |nu| >= pi discarded (valid = 0, pdf 0),
+   omega = exp_{mu_k}(nu); pdf_out = the product mixture's density on the
+   sphere at omega.  Uniforms as in sdmm_sample. */
+sdmm_status sdmm_product_sample(const sdmm_config *cfg, const sdmm_state *st, int64_t R,
+                                int64_t Q, const float *qx, const int32_t *region,
+                                const sdmm_grid *grid, const sdmm_bsdf_lobes *bsdf,
+                                uint64_t seed, const float *uniforms, float *dir_out,
+                                float *pdf_out, uint8_t *valid_out, sdmm_stream stream);
+
+/* Density on the sphere of the product mixture at given unit directions
+   (dir[3Q]): the sum over pairs of weight N(log_{mu_k}(omega)) / sinc. */
+sdmm_status sdmm_product_pdf(const sdmm_config *cfg, const sdmm_state *st, int64_t R,
+                             int64_t Q, const float *qx, const int32_t *region,
+                             const sdmm_grid *grid, const sdmm_bsdf_lobes *bsdf,
+                             const float *dir, float *pdf_out, sdmm_stream stream);
+
+/*
  * ---- The spatial kD-tree of the regions (Sec. 4.2 "Refinement of the
  * spatial kD-tree", Sec. 4.3 "Initialization").
  *

@@ -24,7 +24,8 @@ SYMBOLS = ["sdmm_config_default", "sdmm_last_error", "sdmm_version", "sdmm_fit_w
            "sdmm_fit_plan_create", "sdmm_fit_plan_run", "sdmm_fit_plan_enable_timing",
            "sdmm_fit_plan_timing", "sdmm_fit_plan_destroy", "sdmm_autotune",
            "sdmm_fit_regions_noalloc", "sdmm_tc_selftest", "sdmm_kdtree_grid", "sdmm_kdtree_lookup",
-           "sdmm_kdtree_workspace_size", "sdmm_kdtree_bin", "sdmm_kdtree_refine", "sdmm_gather_regions"]
+           "sdmm_kdtree_workspace_size", "sdmm_kdtree_bin", "sdmm_kdtree_refine", "sdmm_gather_regions",
+           "sdmm_product_sample", "sdmm_product_pdf"]
 
 SDMM_NOALLOC_SCRATCH_BYTES = 16 * 1024 * 1024
 
@@ -60,6 +61,10 @@ class KdTree(ctypes.Structure):
 class SampleBuffers(ctypes.Structure):
     _fields_ = [(n, ctypes.c_void_p) for n in ("px", "py", "pz", "ox", "oy", "oz", "w", "offsets")] + \
                [("R", ctypes.c_int64), ("N", ctypes.c_int64)]
+
+
+class BsdfLobes(ctypes.Structure):
+    _fields_ = [("w", ctypes.c_void_p), ("mu", ctypes.c_void_p), ("L", ctypes.c_void_p), ("J", ctypes.c_int32)]
 
 
 class Grid(ctypes.Structure):
@@ -110,6 +115,9 @@ def _declare(L):
         "sdmm_kdtree_refine": [ctypes.POINTER(KdTree), _I64, _PSm, ctypes.POINTER(SampleBuffers), _P, _P,
                                ctypes.c_size_t, _P],
         "sdmm_gather_regions": [_I32, _I64, _P, _PS, _PS, _P],
+        "sdmm_product_sample": [_PC, _PS, _I64, _I64, _P, _P, _PG, ctypes.POINTER(BsdfLobes), ctypes.c_uint64, _P,
+                                _P, _P, _P, _P],
+        "sdmm_product_pdf": [_PC, _PS, _I64, _I64, _P, _P, _PG, ctypes.POINTER(BsdfLobes), _P, _P, _P],
     }
     for name, args in sig.items():
         f = getattr(L, name)

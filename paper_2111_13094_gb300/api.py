@@ -280,6 +280,47 @@ def sample(cfg, state: MixtureState, qx, region=None, grid=None, seed=0, uniform
     return d, p, v
 
 
+def _lobes(bsdf_w, bsdf_mu, bsdf_L):
+    w = bsdf_w.to(torch.float32).contiguous()
+    mu = bsdf_mu.to(torch.float32).contiguous()
+    L = bsdf_L.to(torch.float32).contiguous()
+    if w.dim() != 2 or mu.shape != (*w.shape, 3) or L.shape != (*w.shape, 3):
+        raise ValueError("BSDF lobes: w (Q, J), mu (Q, J, 3), L (Q, J, 3)")
+    return (w, mu, L), _lib.BsdfLobes(w.data_ptr(), mu.data_ptr(), L.data_ptr(), w.shape[1])
+
+
+def product_sample(cfg, state: MixtureState, qx, bsdf_w, bsdf_mu, bsdf_L, region=None, grid=None, seed=0,
+                   uniforms=None, stream=None):
+    """Directions from the product of each query's conditioned radiance
+    mixture and its BSDF lobes (Sec. 3.5; the two largest lobes, Sec. 4.1):
+    (dir (Q, 3), pdf (Q,), valid (Q,) uint8)."""
+    qx = qx.contiguous()
+    Q = qx.shape[0]
+    keep, lobes = _lobes(bsdf_w, bsdf_mu, bsdf_L)
+    d = torch.empty(Q, 3, dtype=torch.float32, device=qx.device)
+    p = torch.empty(Q, dtype=torch.float32, device=qx.device)
+    v = torch.empty(Q, dtype=torch.uint8, device=qx.device)
+    check(_lib.load().sdmm_product_sample(ctypes.byref(cfg), ctypes.byref(state.c()), state.R, Q, _ptr(qx),
+                                          _ptr(region), _grid_arg(grid), ctypes.byref(lobes), int(seed),
+                                          _ptr(uniforms), _ptr(d), _ptr(p), _ptr(v), _stream(stream)),
+          "sdmm_product_sample")
+    return d, p, v
+
+
+def product_pdf(cfg, state: MixtureState, qx, dirs, bsdf_w, bsdf_mu, bsdf_L, region=None, grid=None, stream=None):
+    """Density on the sphere of the product mixture at the given directions."""
+    qx = qx.contiguous()
+    dirs = dirs.contiguous()
+    Q = qx.shape[0]
+    keep, lobes = _lobes(bsdf_w, bsdf_mu, bsdf_L)
+    p = torch.empty(Q, dtype=torch.float32, device=qx.device)
+    check(_lib.load().sdmm_product_pdf(ctypes.byref(cfg), ctypes.byref(state.c()), state.R, Q, _ptr(qx),
+                                       _ptr(region), _grid_arg(grid), ctypes.byref(lobes), _ptr(dirs), _ptr(p),
+                                       _stream(stream)),
+          "sdmm_product_pdf")
+    return p
+
+
 def pdf(cfg, state: MixtureState, qx, dirs, region=None, grid=None, out=None, stream=None):
     Q = qx.shape[0]
     p = out if out is not None else torch.empty(Q, dtype=torch.float32, device=qx.device)

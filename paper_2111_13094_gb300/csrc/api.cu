@@ -425,6 +425,45 @@ sdmm_status sdmm_sample(const sdmm_config* cfg, const sdmm_state* st, int64_t R,
     return SDMM_OK;
 }
 
+static sdmm_status bsdf_check(const sdmm_bsdf_lobes* b, int64_t Q) {
+    if (!b) return fail(SDMM_ERR_INVALID_ARG, "bsdf is NULL");
+    if (b->J < 1 || b->J > 8) return fail(SDMM_ERR_INVALID_ARG, "J = %d BSDF lobes: 1..8", b->J);
+    if (Q > 0 && (!b->w || !b->mu || !b->L)) return fail(SDMM_ERR_INVALID_ARG, "BSDF arrays are NULL");
+    return SDMM_OK;
+}
+
+sdmm_status sdmm_product_sample(const sdmm_config* cfg, const sdmm_state* st, int64_t R, int64_t Q,
+                                const float* qx, const int32_t* region, const sdmm_grid* grid,
+                                const sdmm_bsdf_lobes* bsdf, uint64_t seed, const float* uniforms,
+                                float* dir_out, float* pdf_out, uint8_t* valid_out, sdmm_stream stream) {
+    GridF g;
+    sdmm_status e = query_common(cfg, st, R, Q, qx, region, grid, &g);
+    if (!e) e = bsdf_check(bsdf, Q);
+    if (e) return e;
+    if (Q > 0 && (!dir_out || !pdf_out || !valid_out)) return fail(SDMM_ERR_INVALID_ARG, "outputs are NULL");
+    if (Q == 0) return SDMM_OK;
+    SDMM_CUDA(launch_product(stream, OP_SAMPLE, pow2_ceil(cfg->K), query_grid(Q), st->qtab, cfg->K, R, Q, qx, region,
+                             g, bsdf->w, bsdf->mu, bsdf->L, bsdf->J, seed, uniforms, nullptr, dir_out, pdf_out,
+                             valid_out),
+              "product_sample");
+    return SDMM_OK;
+}
+
+sdmm_status sdmm_product_pdf(const sdmm_config* cfg, const sdmm_state* st, int64_t R, int64_t Q, const float* qx,
+                             const int32_t* region, const sdmm_grid* grid, const sdmm_bsdf_lobes* bsdf,
+                             const float* dir, float* pdf_out, sdmm_stream stream) {
+    GridF g;
+    sdmm_status e = query_common(cfg, st, R, Q, qx, region, grid, &g);
+    if (!e) e = bsdf_check(bsdf, Q);
+    if (e) return e;
+    if (Q > 0 && (!dir || !pdf_out)) return fail(SDMM_ERR_INVALID_ARG, "dir/pdf_out are NULL");
+    if (Q == 0) return SDMM_OK;
+    SDMM_CUDA(launch_product(stream, OP_PDF, pow2_ceil(cfg->K), query_grid(Q), st->qtab, cfg->K, R, Q, qx, region, g,
+                             bsdf->w, bsdf->mu, bsdf->L, bsdf->J, 0, nullptr, dir, nullptr, pdf_out, nullptr),
+              "product_pdf");
+    return SDMM_OK;
+}
+
 sdmm_status sdmm_pdf(const sdmm_config* cfg, const sdmm_state* st, int64_t R, int64_t Q,
                      const float* qx, const int32_t* region, const sdmm_grid* grid, const float* dir,
                      float* pdf_out, sdmm_stream stream) {

@@ -216,4 +216,25 @@ struct WsHeader {
     int32_t pad_[13];
 };
 
+// Philox4x32-10: J. K. Salmon et al., "Parallel Random Numbers: As Easy as
+// 1, 2, 3", SC'11.  Ten rounds of two 32x32->64 multiplies mixed with the other
+// counter words and a Weyl-sequence key.
+__device__ inline uint4 philox4x32_10(uint4 c, uint2 k) {
+    constexpr uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    constexpr uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+    for (int i = 0; i < 10; ++i) {
+        if (i > 0) {
+            k.x += W0;
+            k.y += W1;
+        }
+        const uint32_t lo0 = M0 * c.x, hi0 = __umulhi(M0, c.x);
+        const uint32_t lo1 = M1 * c.z, hi1 = __umulhi(M1, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+__device__ inline float u24(uint32_t x) { return (float)(x >> 8) * (1.0f / 16777216.0f); }
+
 }  // namespace sdmm

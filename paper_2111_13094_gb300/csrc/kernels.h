@@ -97,4 +97,10 @@ cudaError_t launch_kd_gather(cudaStream_t st, int64_t N, const int32_t* perm, co
 cudaError_t launch_gather_state(cudaStream_t s, int K, int64_t R_out, const int64_t* src, const sdmm_state& in,
                                 const sdmm_state& out);
 
+// ---- product sampling with a BSDF mixture (product.cu)
+cudaError_t launch_product(cudaStream_t s, int op, int KP, int grid, const float* qtab, int K, int64_t R, int64_t Q,
+                           const float* qx, const int32_t* region, const GridF& g, const float* bw, const float* bmu,
+                           const float* bL, int J, uint64_t seed, const float* uni, const float* dir_in, float* dout,
+                           float* pout, uint8_t* vout);
+
 }  // namespace sdmm

@@ -301,3 +301,29 @@ def grid_region(qx, dims):
     d = np.asarray(dims)
     ijk = np.clip(np.floor(np.asarray(qx, np.float64) * d).astype(np.int64), 0, d - 1)
     return (ijk[:, 0] + d[0] * (ijk[:, 1] + d[1] * ijk[:, 2])).astype(np.int32)
+
+
+def bsdf_lobes(seed, Q, J=3):
+    """Per-query BSDF mixtures of J lobes for product sampling.
+
+    Lobe 0 is wide (a diffuse-like lobe about a random normal, std U(0.6, 0.9)
+    rad), lobe 1 narrow (a glossy lobe about a random direction in the normal's
+    hemisphere, std U(0.03, 0.3) rad), further lobes random with std
+    U(0.05, 0.6) rad; weights U(0.05, 1).  Returns float32 (w (Q, J),
+    mu (Q, J, 3), L (Q, J, 3)) with L the lower-triangular factor
+    (l00, l10, l11) of each lobe's covariance in its own chart.
+    """
+    rng = np.random.default_rng([seed, 7])
+    n = _unit(rng, Q)
+    mu = _unit(rng, Q * J).reshape(Q, J, 3)
+    sd = rng.uniform(0.05, 0.6, size=(Q, J, 2))
+    sd[:, 0] = rng.uniform(0.6, 0.9, size=(Q, 2))
+    mu[:, 0] = n
+    if J > 1:
+        r = mu[:, 1]
+        r = np.where((np.sum(r * n, axis=1) < 0)[:, None], -r, r)
+        mu[:, 1] = r
+        sd[:, 1] = rng.uniform(0.03, 0.3, size=(Q, 2))
+    L = np.stack([sd[..., 0], 0.3 * rng.normal(size=(Q, J)) * sd[..., 1], sd[..., 1]], axis=2)
+    w = rng.uniform(0.05, 1.0, size=(Q, J))
+    return w.astype(np.float32), mu.astype(np.float32), L.astype(np.float32)

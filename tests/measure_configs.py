@@ -183,10 +183,41 @@ def covariance_updates(seed=40, R=1024, M=16384, K=16, check=3, steps=3, reps=5)
     return out
 
 
+def estep_density(seed=50, R=1024, M=16384, K=16, reps=10):
+    """Cost of the change of variables in the E-step: one EM step with the
+    chart density p^t (paper) and with the solid-angle density p^t / sinc."""
+    truth = syn.batched_truth(seed, R, K=K)
+    counts = np.full(R, M, dtype=np.int64)
+    N = R * M
+    dev = torch.device("cuda")
+    samples = syn.draw_torch(seed, truth, counts, device=dev)
+    batch = api.SampleBatch(samples, torch.from_numpy(syn.offsets_from_counts(counts)).to(dev))
+    _, h, _ = syn.region_grid(R)
+    out = {"config": f"E-step density, {R} regions x {M} samples, K = {K}"}
+    for name, dens in (("chart", api.DENSITY_TANGENT), ("solid_angle", api.DENSITY_SOLID_ANGLE)):
+        cfg = api.config(K, estep_density=dens)
+        st = api.MixtureState(R, K, device=dev)
+        api.init_regions(cfg, batch, torch.from_numpy(h.astype(np.float64)).to(dev),
+                         torch.from_numpy(syn.init_uniforms(seed, R, K // 8)).to(dev), st)
+        ws = api.workspace(cfg, R, N, device=dev)
+        plan = api.FitPlan(cfg, R, N, 1, st, ws)
+        for _ in range(3):
+            plan.run(batch)
+        plan.enable_timing(reps)
+        for _ in range(reps):
+            plan.run(batch)
+        torch.cuda.synchronize()
+        out[name] = {"estep_ms": float(np.mean(plan.timing()))}
+        del plan, ws, st
+    out["ratio"] = out["solid_angle"]["estep_ms"] / out["chart"]["estep_ms"]
+    return out
+
+
 def main():
     a = single_region()
     b = objective_adjoint()
     c = covariance_updates()
+    d = estep_density()
     print("| config | GPU | error vs oracle | oracle (1 core) |")
     print("|---|---|---|---|")
     print(f"| {a['config']} | {a['gpu_ms']:.2f} ms ({a['sample_iterations_per_s']:.3e} sample-it/s) | "
@@ -199,7 +230,9 @@ def main():
     for name in ("first_order", "two_pass"):
         print(f"| {c['config']}: {name} | {c[name]['step_ms']:.2f} ms per EM step | "
               f"L vs the accurate (two-pass) oracle {c[name]['L_error_vs_two_pass_oracle']:.1e} | — |")
-    print(json.dumps({"single_region": a, "objective": b, "covariance_updates": c}))
+    print(f"| {d['config']} | chart {d['chart']['estep_ms']:.2f} ms, solid angle {d['solid_angle']['estep_ms']:.2f} ms "
+          f"per E-step ({d['ratio']:.2f}x) | (parity: tests/test_gpu_fit.py) | — |")
+    print(json.dumps({"single_region": a, "objective": b, "covariance_updates": c, "estep_density": d}))
 
 
 if __name__ == "__main__":
