@@ -24,7 +24,7 @@ constexpr float kTwoPiF = 6.28318530717958647692f;
 // Duff et al.'s branchless basis (rows t, b of R_mu), FP32
 __device__ __forceinline__ void basis_f32(float m0, float m1, float m2, float t[3], float b[3]) {
     const float sgn = copysignf(1.f, m2);
-    const float a = -1.f / (sgn + m2);
+    const float a = __fdividef(-1.f, sgn + m2);
     const float c = m0 * m1 * a;
     t[0] = 1.f + sgn * m0 * m0 * a;
     t[1] = sgn * c;
@@ -34,17 +34,18 @@ __device__ __forceinline__ void basis_f32(float m0, float m1, float m2, float t[
     b[2] = -m1;
 }
 
-// One (component, lobe) pair in the component's chart: Cholesky factor of P,
+// One (component, lobe) pair in the component's chart: the product's
+// Cholesky factor C = [[1/i0, 0], [p10, 1/i1]] (kept as reciprocal diagonals),
 // mean and log weight (log pi' + log w + log N(m; nu2, S1 + S2')).
 struct Pair {
-    float m0, m1, p00, p10, p11, ln, lw;
+    float m0, m1, i0, p10, i1, ln, lw;
 };
 
 __device__ inline Pair make_pair(const float* P, float cm0, float cm1, float lcpi, float wj, const float* mu2,
                                  const float* L2) {
     Pair o;
     o.m0 = o.m1 = 0.f;
-    o.p00 = o.p11 = 1.f;
+    o.i0 = o.i1 = 1.f;
     o.p10 = o.ln = 0.f;
     o.lw = -INFINITY;
     // the lobe's mean in the mu_k chart
@@ -52,24 +53,24 @@ __device__ inline Pair make_pair(const float* P, float cm0, float cm1, float lcp
     const float v = P[6] * mu2[0] + P[7] * mu2[1] + P[8] * mu2[2];
     const float c = P[9] * mu2[0] + P[10] * mu2[1] + P[11] * mu2[2];
     const float s2 = u * u + v * v;
-    const float s = sqrtf(s2);
+    const float rs = rsqrtf(s2);
+    const float s = s2 > 0.f ? s2 * rs : 0.f;
     const float th = atan2_pos(s, c);
     if ((s2 == 0.f && c < 0.f) || th >= kPiF || !(wj > 0.f)) return o;   // antipode / no weight
-    const float g = s > 0.f ? th / s : 1.f;
+    const float g = s2 > 0.f ? th * rs : 1.f;
     // d g / d c along the sphere: (theta c - s) / s^3, its series below 0.05 rad
-    const float h = th < 0.05f ? -1.f / 3.f - (2.f / 15.f) * th * th : (th * c - s) / (s2 * s);
+    const float h = th < 0.05f ? -1.f / 3.f - (2.f / 15.f) * th * th : (th * c - s) * (rs * rs * rs);
     const float n0 = g * u, n1 = g * v;
     // J = J_log(mu2) [t2 b2]: tangent directions of the lobe's chart seen in the mu_k chart
     float t2[3], b2[3];
     basis_f32(mu2[0], mu2[1], mu2[2], t2, b2);
     float J[2][2];
-    const float* cols[2] = {t2, b2};
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
-        const float* e = cols[q];
-        const float ta = P[3] * e[0] + P[4] * e[1] + P[5] * e[2];
-        const float tb = P[6] * e[0] + P[7] * e[1] + P[8] * e[2];
-        const float tc = P[9] * e[0] + P[10] * e[1] + P[11] * e[2];
+        const float e0 = q == 0 ? t2[0] : b2[0], e1 = q == 0 ? t2[1] : b2[1], e2 = q == 0 ? t2[2] : b2[2];
+        const float ta = P[3] * e0 + P[4] * e1 + P[5] * e2;
+        const float tb = P[6] * e0 + P[7] * e1 + P[8] * e2;
+        const float tc = P[9] * e0 + P[10] * e1 + P[11] * e2;
         J[0][q] = g * ta + u * tc * h;
         J[1][q] = g * tb + v * tc * h;
     }
@@ -82,11 +83,11 @@ __device__ inline Pair make_pair(const float* P, float cm0, float cm1, float lcp
     const float S00 = a00 + b00, S01 = a01 + b01, S11 = a11 + b11;
     const float det = S00 * S11 - S01 * S01;
     if (!(det > 0.f)) return o;
-    const float id = 1.f / det;
+    const float id = __fdividef(1.f, det);
     const float i00 = S11 * id, i01 = -S01 * id, i11 = S00 * id;
     const float d0 = cm0 - n0, d1 = cm1 - n1;
     const float q = d0 * (i00 * d0 + i01 * d1) + d1 * (i01 * d0 + i11 * d1);
-    o.lw = lcpi + __logf(wj) - 0.5f * q - __logf(kTwoPiF) - 0.5f * __logf(det);
+    o.lw = lcpi - 0.5f * q - __logf(kTwoPiF) + __logf(wj * rsqrtf(det));
     // P = S1 Si S2', mean = S2' Si m + S1 Si nu2
     const float X00 = i00 * b00 + i01 * b01, X01 = i00 * b01 + i01 * b11;   // Si S2'
     const float X10 = i01 * b00 + i11 * b01, X11 = i01 * b01 + i11 * b11;
@@ -96,22 +97,22 @@ __device__ inline Pair make_pair(const float* P, float cm0, float cm1, float lcp
     const float z0 = i00 * n0 + i01 * n1, z1 = i01 * n0 + i11 * n1;          // Si nu2
     o.m0 = b00 * y0 + b01 * y1 + a00 * z0 + a01 * z1;
     o.m1 = b01 * y0 + b11 * y1 + a01 * z0 + a11 * z1;
-    o.p00 = sqrtf(P00);
-    o.p10 = P01 / o.p00;
-    o.p11 = sqrtf(fmaxf(P11 - o.p10 * o.p10, 1e-30f));
-    o.ln = -__logf(kTwoPiF) - __logf(o.p00 * o.p11);
+    o.i0 = rsqrtf(P00);
+    o.p10 = P01 * o.i0;
+    o.i1 = rsqrtf(fmaxf(P11 - o.p10 * o.p10, 1e-30f));
+    o.ln = __logf(o.i0 * o.i1) - __logf(kTwoPiF);
     return o;
 }
 
 // log of the pair's chart density at nu (without the weight)
 __device__ __forceinline__ float pair_logpdf(const Pair& p, float nu0, float nu1) {
-    const float y0 = (nu0 - p.m0) / p.p00;
-    const float y1 = (nu1 - p.m1 - p.p10 * y0) / p.p11;
+    const float y0 = (nu0 - p.m0) * p.i0;
+    const float y1 = (nu1 - p.m1 - p.p10 * y0) * p.i1;
     return p.ln - 0.5f * (y0 * y0 + y1 * y1);
 }
 
 template <int KP, int OP>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 3)
     k_product(const float* __restrict__ qtab, int K, int64_t R, int64_t Q, const float* __restrict__ qx,
               const int32_t* __restrict__ region, GridF grid, const float* __restrict__ bw,
               const float* __restrict__ bmu, const float* __restrict__ bL, int J, uint64_t seed,
@@ -213,7 +214,7 @@ __global__ void __launch_bounds__(256)
             float se = ec;
 #pragma unroll
             for (int o = KP / 2; o > 0; o >>= 1) se += __shfl_xor_sync(FULL, se, o);
-            const float lcpi = (se > 0.f && ec > 0.f && k < K) ? __logf(ec / se) : -INFINITY;   // log pi'_k
+            const float lcpi = (se > 0.f && ec > 0.f && k < K) ? (lw - mx) - __logf(se) : -INFINITY;   // log pi'_k
             // ---- the two BSDF lobes of largest weight, in increasing index
             const int64_t qi = g + j;
             const int64_t qb = ok ? qi : 0;
@@ -278,13 +279,20 @@ __global__ void __launch_bounds__(256)
                 if (k == kk) {
                     // inside the lane: pair a unless the threshold lies past it
                     const bool use_b = !(thr < cum - eb) || !(ea > 0.f);
-                    const Pair& p = (use_b && eb > 0.f) ? pr[1] : pr[0];
+                    const bool pb = use_b && eb > 0.f;
+                    Pair p;
+                    p.m0 = pb ? pr[1].m0 : pr[0].m0;
+                    p.m1 = pb ? pr[1].m1 : pr[0].m1;
+                    p.i0 = pb ? pr[1].i0 : pr[0].i0;
+                    p.p10 = pb ? pr[1].p10 : pr[0].p10;
+                    p.i1 = pb ? pr[1].i1 : pr[0].i1;
                     const float rad = sqrtf(-2.f * logf(1.f - b1));
                     float sn, cs;
                     sincospif(2.f * b2, &sn, &cs);
                     const float g0 = rad * cs, g1 = rad * sn;
-                    const float n0 = p.m0 + p.p00 * g0;
-                    const float n1 = p.m1 + p.p10 * g0 + p.p11 * g1;
+                    const float z0 = __fdividef(g0, p.i0);
+                    const float n0 = p.m0 + z0;
+                    const float n1 = p.m1 + p.p10 * g0 + __fdividef(g1, p.i1);
                     const float rn = sqrtf(n0 * n0 + n1 * n1);
                     vv = rn < kPiF ? 1.f : 0.f;
                     float sr, cr;

@@ -1,8 +1,10 @@
 """GPU timings and errors against the FP64 oracle for the single-region
-fit (65,536 samples, K = 16, 20 plain EM iterations) and for the MAP
-objective and its adjoint (1,024 regions x 16,384 samples, K = 16).
+fit (65,536 samples, K = 16, 20 plain EM iterations), the MAP objective and
+its adjoint (1,024 regions x 16,384 samples, K = 16), the covariance
+updates, the E-step density, and GPU timings of guided and product queries.
 
-    python tests/measure_configs.py
+    python tests/measure_configs.py                 # everything
+    python tests/measure_configs.py product --queries 1048576
 
 Test infrastructure (it runs the oracle): prints a markdown table and one
 JSON line.  Checked regions start from the oracle's own initialisation and
@@ -213,7 +215,44 @@ def estep_density(seed=50, R=1024, M=16384, K=16, reps=10):
     return out
 
 
+def product_queries(seed=60, Q=1 << 24, K=16, J=3, dims=(64, 32, 32), reps=10):
+    """Guided queries with and without the BSDF product on the same positions
+    (grid lookup, one Philox draw per query): GPU time per batch."""
+    dev = torch.device("cuda")
+    cfg = api.config(K)
+    pi, mu_x, mu_w, L = syn.random_mixtures(seed, dims, K)
+    st = api.MixtureState(int(np.prod(dims)), K, device=dev)
+    st.set_params(torch.from_numpy(pi), torch.from_numpy(mu_x), torch.from_numpy(mu_w), torch.from_numpy(L))
+    api.prepare(cfg, st)
+    qx = torch.from_numpy(syn.query_points(seed, Q)).to(dev)
+    bw, bmu, bL = (torch.from_numpy(a).to(dev) for a in syn.bsdf_lobes(seed, Q, J))
+    grid = api.Grid((0, 0, 0), (1, 1, 1), dims)
+    e0, e1 = _events()
+    out = {"config": f"{Q} queries, {int(np.prod(dims))} grid regions, K = {K}, {J} BSDF lobes"}
+    for name, fn in (("plain", lambda: api.sample(cfg, st, qx, grid=grid, seed=7)),
+                     ("product", lambda: api.product_sample(cfg, st, qx, bw, bmu, bL, grid=grid, seed=7))):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out[name] = {"ms": ms, "queries_per_s": Q / (ms * 1e-3)}
+    return out
+
+
 def main():
+    import argparse
+    ap = argparse.ArgumentParser()
+    ap.add_argument("which", nargs="*", default=[])
+    ap.add_argument("--queries", type=int, default=1 << 24)
+    args = ap.parse_args()
+    if args.which == ["product"]:
+        print(json.dumps(product_queries(Q=args.queries)))
+        return
     a = single_region()
     b = objective_adjoint()
     c = covariance_updates()
