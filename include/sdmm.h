@@ -353,6 +353,23 @@ sdmm_status sdmm_fit_plan_create(const sdmm_config *cfg, int64_t R,
 sdmm_status sdmm_fit_plan_run(sdmm_fit_plan *plan, const sdmm_samples *s,
                               const double *prior_scale, float *loglik_out,
                               sdmm_stream stream);
+/* Batches from host memory (Sec. 4.2: the renderer produces each round's
+   samples on the host).  sdmm_fit_plan_run_host copies the seven sample
+   arrays and the offsets of `host_batch` (host pointers; pinned memory for
+   asynchronous copies) into one of two slots of `staging` (device,
+   caller-owned, 256-byte aligned, sdmm_fit_plan_staging_size bytes) on a copy
+   stream owned by the plan, then replays the plan on `stream` once the copy
+   is done.  Consecutive runs alternate the slots, so the copy of the next
+   batch overlaps the replay of the previous one; a slot is rewritten only
+   after the replay that read it.  The host arrays must stay unchanged until
+   `stream` has passed the run.  Device pointers in `host_batch` are
+   rejected (SDMM_ERR_INVALID_ARG); a small or misaligned staging buffer gives
+   SDMM_ERR_WORKSPACE. */
+sdmm_status sdmm_fit_plan_staging_size(const sdmm_fit_plan *plan, size_t *bytes_out);
+sdmm_status sdmm_fit_plan_run_host(sdmm_fit_plan *plan, const sdmm_samples *host_batch,
+                                   void *staging, size_t staging_bytes,
+                                   const double *prior_scale, float *loglik_out,
+                                   sdmm_stream stream);
 /* Enable per-run event timing of the E-step kernel of each step inside the
    graph, for up to `capacity` runs before sdmm_fit_plan_timing is read. */
 sdmm_status sdmm_fit_plan_enable_timing(sdmm_fit_plan *plan, int32_t capacity);

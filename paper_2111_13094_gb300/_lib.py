@@ -22,6 +22,7 @@ SYMBOLS = ["sdmm_config_default", "sdmm_last_error", "sdmm_version", "sdmm_fit_w
            "sdmm_init_regions", "sdmm_fit_regions", "sdmm_prepare", "sdmm_condition",
            "sdmm_sample", "sdmm_pdf", "sdmm_objective", "sdmm_objective_backward",
            "sdmm_fit_plan_create", "sdmm_fit_plan_run", "sdmm_fit_plan_enable_timing",
+           "sdmm_fit_plan_staging_size", "sdmm_fit_plan_run_host",
            "sdmm_fit_plan_timing", "sdmm_fit_plan_destroy", "sdmm_autotune",
            "sdmm_fit_regions_noalloc", "sdmm_tc_selftest", "sdmm_kdtree_grid", "sdmm_kdtree_lookup",
            "sdmm_kdtree_workspace_size", "sdmm_kdtree_bin", "sdmm_kdtree_refine", "sdmm_gather_regions",
@@ -101,6 +102,8 @@ def _declare(L):
         "sdmm_fit_plan_create": [_PC, _I64, _I64, _I32, _PS, _P, ctypes.c_size_t, _P,
                                  ctypes.POINTER(ctypes.c_void_p)],
         "sdmm_fit_plan_run": [_P, _PSm, _P, _P, _P],
+        "sdmm_fit_plan_staging_size": [_P, ctypes.POINTER(ctypes.c_size_t)],
+        "sdmm_fit_plan_run_host": [_P, _PSm, _P, ctypes.c_size_t, _P, _P, _P],
         "sdmm_fit_plan_enable_timing": [_P, _I32],
         "sdmm_fit_plan_timing": [_P, _P, _I32, ctypes.POINTER(_I32)],
         "sdmm_fit_plan_destroy": [_P],

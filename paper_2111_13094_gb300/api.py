@@ -374,6 +374,21 @@ class FitPlan:
         check(self._lib.sdmm_fit_plan_run(self.h, ctypes.byref(sm), _ptr(prior_scale), _ptr(loglik),
                                           _stream(stream)), "sdmm_fit_plan_run")
 
+    def staging_bytes(self) -> int:
+        n = ctypes.c_size_t()
+        check(self._lib.sdmm_fit_plan_staging_size(self.h, ctypes.byref(n)), "sdmm_fit_plan_staging_size")
+        return n.value
+
+    def run_host(self, batch: SampleBatch, staging, prior_scale=None, loglik=None, stream=None):
+        """Run on a batch in (pinned) host memory: its copy into a slot of the
+        device `staging` buffer overlaps the previous run's replay."""
+        if batch.samples.is_cuda or batch.offsets.is_cuda:
+            raise ValueError("run_host takes a batch in host memory")
+        sm = batch.c()
+        check(self._lib.sdmm_fit_plan_run_host(self.h, ctypes.byref(sm), _ptr(staging), staging.numel(),
+                                               _ptr(prior_scale), _ptr(loglik), _stream(stream)),
+              "sdmm_fit_plan_run_host")
+
     def enable_timing(self, capacity: int):
         check(self._lib.sdmm_fit_plan_enable_timing(self.h, int(capacity)), "sdmm_fit_plan_enable_timing")
 

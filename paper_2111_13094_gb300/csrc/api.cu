@@ -535,7 +535,17 @@ struct sdmm_fit_plan {
     std::vector<cudaEvent_t> pool;             // timing: 2*iters events per run
     int32_t capacity = 0;
     int32_t runs = 0;
+    // batches from host memory: two staging slots, copies on their own stream
+    cudaStream_t copy = nullptr;
+    cudaEvent_t ready[2] = {nullptr, nullptr};  // slot's copy done (copy stream)
+    cudaEvent_t freed[2] = {nullptr, nullptr};  // slot's replay done (caller's stream)
+    int64_t host_runs = 0;
 };
+
+static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+static size_t staging_slot_bytes(const sdmm_fit_plan* p) {
+    return 7 * align256((size_t)p->N_max * sizeof(float)) + align256((size_t)(p->f.R + 1) * sizeof(int64_t));
+}
 
 sdmm_status sdmm_fit_plan_create(const sdmm_config* cfg, int64_t R, int64_t N_max, int32_t iters,
                                  sdmm_state* st, void* workspace, size_t ws_bytes, sdmm_stream stream,
@@ -623,6 +633,68 @@ sdmm_status sdmm_fit_plan_run(sdmm_fit_plan* p, const sdmm_samples* s, const dou
     return SDMM_OK;
 }
 
+sdmm_status sdmm_fit_plan_staging_size(const sdmm_fit_plan* p, size_t* bytes_out) {
+    if (!p || !bytes_out) return fail(SDMM_ERR_INVALID_ARG, "plan or bytes_out is NULL");
+    *bytes_out = 2 * staging_slot_bytes(p);
+    return SDMM_OK;
+}
+
+static bool on_device(const void* ptr) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice;
+}
+
+sdmm_status sdmm_fit_plan_run_host(sdmm_fit_plan* p, const sdmm_samples* hs, void* staging, size_t staging_bytes,
+                                   const double* prior_scale, float* loglik_out, sdmm_stream stream) {
+    sdmm_status e;
+    if (!p) return fail(SDMM_ERR_INVALID_ARG, "plan is NULL");
+    if ((e = check_samples(hs))) return e;
+    if (hs->R != p->f.R) return fail(SDMM_ERR_INVALID_ARG, "batch R %lld != plan R %lld", (long long)hs->R, (long long)p->f.R);
+    if (hs->N > p->N_max) return fail(SDMM_ERR_INVALID_ARG, "batch N %lld > plan N_max %lld", (long long)hs->N, (long long)p->N_max);
+    const size_t slot_bytes = staging_slot_bytes(p);
+    if (!staging || (reinterpret_cast<uintptr_t>(staging) & 255u) || staging_bytes < 2 * slot_bytes)
+        return fail(SDMM_ERR_WORKSPACE, "staging must be 256-byte aligned device memory of %zu bytes", 2 * slot_bytes);
+    if (on_device(hs->offsets) || (hs->N > 0 && on_device(hs->px)))
+        return fail(SDMM_ERR_INVALID_ARG, "sdmm_fit_plan_run_host takes a batch in host memory");
+    if (!p->copy) {
+        SDMM_CUDA(cudaStreamCreateWithFlags(&p->copy, cudaStreamNonBlocking), "copy stream");
+        for (int i = 0; i < 2; ++i) {
+            SDMM_CUDA(cudaEventCreateWithFlags(&p->ready[i], cudaEventDisableTiming), "event");
+            SDMM_CUDA(cudaEventCreateWithFlags(&p->freed[i], cudaEventDisableTiming), "event");
+        }
+    }
+    const int slot = (int)(p->host_runs & 1);
+    char* base = static_cast<char*>(staging) + (size_t)slot * slot_bytes;
+    const size_t col = align256((size_t)p->N_max * sizeof(float));
+    // the slot is rewritten once the replay that last read it is done; a fresh
+    // slot waits for the work already queued on the caller's stream
+    if (p->host_runs < 2) SDMM_CUDA(cudaEventRecord(p->freed[slot], stream), "event record");
+    SDMM_CUDA(cudaStreamWaitEvent(p->copy, p->freed[slot], 0), "wait");
+    const float* src[7] = {hs->px, hs->py, hs->pz, hs->ox, hs->oy, hs->oz, hs->w};
+    float* dst[7];
+    for (int i = 0; i < 7; ++i) {
+        dst[i] = reinterpret_cast<float*>(base + (size_t)i * col);
+        if (hs->N > 0)
+            SDMM_CUDA(cudaMemcpyAsync(dst[i], src[i], (size_t)hs->N * sizeof(float), cudaMemcpyHostToDevice, p->copy),
+                      "H2D samples");
+    }
+    int64_t* doff = reinterpret_cast<int64_t*>(base + 7 * col);
+    SDMM_CUDA(cudaMemcpyAsync(doff, hs->offsets, (size_t)(hs->R + 1) * sizeof(int64_t), cudaMemcpyHostToDevice,
+                              p->copy),
+              "H2D offsets");
+    SDMM_CUDA(cudaEventRecord(p->ready[slot], p->copy), "event record");
+    SDMM_CUDA(cudaStreamWaitEvent(stream, p->ready[slot], 0), "wait");
+    const sdmm_samples ds = {dst[0], dst[1], dst[2], dst[3], dst[4], dst[5], dst[6], doff, hs->R, hs->N};
+    if ((e = sdmm_fit_plan_run(p, &ds, prior_scale, loglik_out, stream))) return e;
+    SDMM_CUDA(cudaEventRecord(p->freed[slot], stream), "event record");
+    ++p->host_runs;
+    return SDMM_OK;
+}
+
 sdmm_status sdmm_fit_plan_enable_timing(sdmm_fit_plan* p, int32_t capacity) {
     if (!p || capacity < 1) return fail(SDMM_ERR_INVALID_ARG, "plan NULL or capacity < 1");
     for (auto ev : p->pool) cudaEventDestroy(ev);
@@ -659,6 +731,11 @@ sdmm_status sdmm_fit_plan_destroy(sdmm_fit_plan* p) {
         if (ev) cudaEventDestroy(ev);
     for (auto ev : p->pool)
         if (ev) cudaEventDestroy(ev);
+    for (int i = 0; i < 2; ++i) {
+        if (p->ready[i]) cudaEventDestroy(p->ready[i]);
+        if (p->freed[i]) cudaEventDestroy(p->freed[i]);
+    }
+    if (p->copy) cudaStreamDestroy(p->copy);
     delete p;
     return SDMM_OK;
 }

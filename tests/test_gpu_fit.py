@@ -253,3 +253,39 @@ def test_autotune_returns_a_valid_candidate():
     ws = api.workspace(gcfg, R, b.N)
     chunk, ctas, ms = api.autotune(gcfg, dev_batch(b), st, ws)
     assert chunk in (256, 512, 1024, 2048, 4096, 8192) and 1 <= ctas <= 4 and ms > 0
+
+
+def test_plan_on_host_batches_equals_device_batches():
+    """Batches streamed from pinned host memory through the plan's two
+    staging slots (copy of batch t + 1 overlapping the replay of batch t)
+    give the same states as the same batches resident on the device, with
+    batches of different sizes; device pointers and a short staging buffer
+    are rejected."""
+    K, R = 16, 24
+    truth = syn.batched_truth(7, R, K=K)
+    rounds = []
+    for r in range(5):
+        counts = syn.region_counts(70 + r, R, 256, 20000)
+        rounds.append(syn.batched_round(7, R, counts, r, truth))
+    ost = oracle_init(7, rounds[0], K)
+    gcfg = api.config(K)
+    a = gpu_state(ost, gcfg)
+    b = gpu_state(ost, gcfg)
+    N = max(int(x.offsets[-1]) for x in rounds)
+    wa, wb = api.workspace(gcfg, R, N), api.workspace(gcfg, R, N)
+    pa, pb = api.FitPlan(gcfg, R, N, 1, a, wa), api.FitPlan(gcfg, R, N, 1, b, wb)
+    staging = torch.empty(pb.staging_bytes(), dtype=torch.uint8, device="cuda")
+    hosts = [api.SampleBatch(torch.from_numpy(np.ascontiguousarray(x.samples)).pin_memory(),
+                             torch.from_numpy(np.ascontiguousarray(x.offsets)).pin_memory()) for x in rounds]
+    for x, h in zip(rounds, hosts):
+        pa.run(dev_batch(x))
+        pb.run_host(h, staging)
+    torch.cuda.synchronize()
+    for f in api.MixtureState.FIELDS:
+        assert torch.equal(getattr(a, f), getattr(b, f)), f
+    with pytest.raises(ValueError):
+        pb.run_host(dev_batch(rounds[0]), staging)
+    with pytest.raises(api.SdmmError):
+        pb.run_host(hosts[0], staging[: staging.numel() // 2])
+    pa.close()
+    pb.close()
