@@ -83,6 +83,12 @@ enum { SDMM_PRIOR_SCALE_SEEN = 0, SDMM_PRIOR_SCALE_ARRAY = 1 };
 enum { SDMM_PREC_FP32 = 0, SDMM_PREC_TC_3XBF16 = 1, SDMM_PREC_TC_TF32 = 2,
        SDMM_PREC_TC_3XTF32 = 3, SDMM_PREC_TC_6XBF16 = 4 };
 enum { SDMM_COV_FIRST_ORDER = 0, SDMM_COV_TWO_PASS = 1 };
+/* Directional coordinates of the fit: the tangent chart of each component
+   (the paper, Sec. 3.1), or, as an ablation without any change of
+   variables, the first two world coordinates of the direction,
+   nu = (w_x - mu_x, w_y - mu_y), with the new mean mu + (m_x, m_y, 0) and no
+   chart transport. */
+enum { SDMM_DIR_TANGENT = 0, SDMM_DIR_EUCLIDEAN = 1 };
 
 #define SDMM_MAX_K 32
 /* Floats per component in the derived FP32 tables (see sdmm_state). */
@@ -126,7 +132,10 @@ typedef struct sdmm_config {
                                   accurate update is defined for plain EM
                                   (eta_mode = SDMM_ETA_ONE; the batch is the
                                   statistic) and runs on the FP32 SIMT path   */
-    int32_t reserved_;         /* zero                                        */
+    int32_t dir_coords;        /* SDMM_DIR_*: tangent charts (default) or the
+                                  Euclidean ablation (fit and objective only;
+                                  queries, product sampling and the two-pass
+                                  update reject it: SDMM_ERR_UNSUPPORTED)     */
     double eta_alpha;          /* 0.5 (Sec. 4.3)                              */
     double eta_beta;           /* 0.1 (Sec. 4.3)                              */
     double prior_q;            /* Dirichlet prior q = prior_q / K; paper 1    */

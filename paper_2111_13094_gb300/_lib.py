@@ -36,7 +36,7 @@ class Config(ctypes.Structure):
                 ("eta_mode", ctypes.c_int32), ("estep_density", ctypes.c_int32),
                 ("prior_scale_mode", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("chunk", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
-                ("cov_update", ctypes.c_int32), ("reserved_", ctypes.c_int32),
+                ("cov_update", ctypes.c_int32), ("dir_coords", ctypes.c_int32),
                 ("eta_alpha", ctypes.c_double), ("eta_beta", ctypes.c_double),
                 ("prior_q", ctypes.c_double), ("prior_a", ctypes.c_double),
                 ("prior_B_pos", ctypes.c_double), ("prior_B_dir", ctypes.c_double)]

@@ -24,6 +24,7 @@ DENSITY_TANGENT, DENSITY_SOLID_ANGLE = 0, 1
 PRIOR_SCALE_SEEN, PRIOR_SCALE_ARRAY = 0, 1
 PREC_FP32, PREC_TC_3XBF16, PREC_TC_TF32, PREC_TC_3XTF32, PREC_TC_6XBF16 = 0, 1, 2, 3, 4
 COV_FIRST_ORDER, COV_TWO_PASS = 0, 1
+DIR_TANGENT, DIR_EUCLIDEAN = 0, 1
 
 
 def _ptr(t):

@@ -77,6 +77,10 @@ sdmm_status check_config(const sdmm_config* cfg) {
         return fail(SDMM_ERR_UNSUPPORTED, "the two-pass covariance update runs on the FP32 SIMT path");
     if (cfg->cov_update == SDMM_COV_TWO_PASS && cfg->eta_mode != SDMM_ETA_ONE)
         return fail(SDMM_ERR_UNSUPPORTED, "the two-pass covariance update is defined for eta_mode = ETA_ONE");
+    if (cfg->dir_coords != SDMM_DIR_TANGENT && cfg->dir_coords != SDMM_DIR_EUCLIDEAN)
+        return fail(SDMM_ERR_INVALID_ARG, "dir_coords %d", cfg->dir_coords);
+    if (cfg->dir_coords == SDMM_DIR_EUCLIDEAN && cfg->cov_update == SDMM_COV_TWO_PASS)
+        return fail(SDMM_ERR_UNSUPPORTED, "the two-pass covariance update needs tangent charts");
     const double v[6] = {cfg->eta_alpha, cfg->eta_beta, cfg->prior_q, cfg->prior_a,
                          cfg->prior_B_pos, cfg->prior_B_dir};
     for (double x : v)
@@ -221,22 +225,24 @@ struct FitLaunch {
 sdmm_status enqueue_fit(const FitLaunch& f, cudaStream_t s, std::vector<cudaEvent_t>* evs) {
     const int KP = pow2_ceil(f.cfg.K);
     const bool tcore = tensor_core(&f.cfg);
+    const int euclid = f.cfg.dir_coords == SDMM_DIR_EUCLIDEAN;
     SDMM_CUDA(launch_build_chunks(s, f.w.hdr, f.w.cb, f.w.cr, f.w.units, f.L.chunk, f.cfg.min_samples,
                                   f.L.max_chunks),
               "build_chunks");
     for (int it = 0; it < f.iters; ++it) {
         const int wll = f.want_ll && it == f.iters - 1;
         if (tcore)
-            SDMM_CUDA(launch_tc_prepare(s, f.cfg.K, f.R, f.st, f.w.ctab, f.w.xref), "tc_prepare");
+            SDMM_CUDA(launch_tc_prepare(s, f.cfg.K, f.R, f.st, f.w.ctab, f.w.xref, euclid), "tc_prepare");
         if (evs) SDMM_CUDA(cudaEventRecordWithFlags((*evs)[2 * it], s, cudaEventRecordExternal), "event");
         if (tcore) {
             const int grid = std::max(1, sm_count()) * tc_ctas_per_sm(f.cfg.K, f.cfg.precision);   // persistent
             SDMM_CUDA(launch_tc_estep(s, f.cfg.K, f.cfg.precision, grid, f.w.hdr, f.w.cr, f.w.units, f.w.ctab,
-                                      f.w.xref, f.w.partial, f.L.ps, wll),
+                                      f.w.xref, f.w.partial, f.L.ps, wll, euclid),
                       "tc_estep");
         } else {
             SDMM_CUDA(launch_accumulate(s, MODE_FIT, KP, f.grid, f.w.hdr, f.w.cb, f.w.cr, f.st.etab, f.cfg.K,
-                                        f.L.chunk, f.cfg.estep_density, f.w.partial, f.L.ps, wll),
+                                        f.L.chunk, f.cfg.estep_density, f.w.partial, f.L.ps, wll, nullptr,
+                                        euclid),
                       "accumulate");
         }
         if (evs) SDMM_CUDA(cudaEventRecordWithFlags((*evs)[2 * it + 1], s, cudaEventRecordExternal), "event");
@@ -357,7 +363,8 @@ sdmm_status sdmm_prepare(const sdmm_config* cfg, int64_t R, sdmm_state* st, cons
     sdmm_status e;
     if ((e = check_config(cfg)) || (e = check_state(st, false))) return e;
     if (R < 1) return fail(SDMM_ERR_INVALID_ARG, "R = %lld", (long long)R);
-    SDMM_CUDA(launch_prepare(stream, cfg->K, R, *st, logits, delta), "prepare");
+    SDMM_CUDA(launch_prepare(stream, cfg->K, R, *st, logits, delta, cfg->dir_coords == SDMM_DIR_EUCLIDEAN),
+              "prepare");
     return SDMM_OK;
 }
 
@@ -367,6 +374,8 @@ static sdmm_status query_common(const sdmm_config* cfg, const sdmm_state* st, in
                                 GridF* g) {
     sdmm_status e;
     if ((e = check_config(cfg)) || (e = check_state(st, false))) return e;
+    if (cfg->dir_coords != SDMM_DIR_TANGENT)
+        return fail(SDMM_ERR_UNSUPPORTED, "queries need tangent charts (dir_coords = SDMM_DIR_TANGENT)");
     if (R < 1 || Q < 0) return fail(SDMM_ERR_INVALID_ARG, "R = %lld, Q = %lld", (long long)R, (long long)Q);
     if (Q > 0 && !qx) return fail(SDMM_ERR_INVALID_ARG, "qx is NULL");
     std::memset(g, 0, sizeof(*g));
@@ -499,7 +508,7 @@ static sdmm_status objective_common(const sdmm_config* cfg, const sdmm_samples* 
     SDMM_CUDA(launch_build_chunks(stream, w.hdr, w.cb, w.cr, nullptr, L.chunk, 1, L.max_chunks), "build_chunks");
     SDMM_CUDA(launch_accumulate(stream, dF ? MODE_GRAD : MODE_FIT, KP, nsm * default_ctas(cfg), w.hdr,
                                 w.cb, w.cr, st->etab, cfg->K, L.chunk, cfg->estep_density, w.partial,
-                                L.ps, 0),
+                                L.ps, 0, nullptr, cfg->dir_coords == SDMM_DIR_EUCLIDEAN),
               "accumulate");
     SDMM_CUDA(launch_reduce_objective(stream, s->R, w.hdr, w.cb, w.partial, L.ps, *cfg, *st, F_out, dF,
                                       gd, gL, ga),
@@ -809,7 +818,8 @@ sdmm_status sdmm_autotune(const sdmm_config* cfg, const sdmm_samples* s, const s
                     return fail(SDMM_ERR_CUDA, "autotune launch");
                 cudaEventRecord(a, stream);
                 if (launch_accumulate(stream, MODE_FIT, KP, nsm * g, w.hdr, w.cb, w.cr, st->etab, cfg->K, c,
-                                      cfg->estep_density, w.partial, L.ps, 0) != cudaSuccess)
+                                      cfg->estep_density, w.partial, L.ps, 0, nullptr,
+                                      cfg->dir_coords == SDMM_DIR_EUCLIDEAN) != cudaSuccess)
                     return fail(SDMM_ERR_CUDA, "autotune launch");
                 cudaEventRecord(b, stream);
                 SDMM_CUDA(cudaEventSynchronize(b), "autotune sync");

@@ -155,9 +155,15 @@ __device__ inline void lower_inverse5_f64(const double L[15], double Li[15]) {
 // Writes the E-step and query records of one component.
 __device__ inline void write_records(double pi, const double mux[3], const double muw[3],
                                      const double L[15], float* __restrict__ er,
-                                     float* __restrict__ qr, const double* delta = nullptr) {
+                                     float* __restrict__ qr, const double* delta = nullptr,
+                                     bool euclid = false) {
     double t[3], b[3], Li[15];
-    basis_f64(muw, t, b);
+    if (euclid) {   // nu = (w_x, w_y) - (mu_x, mu_y): unit rows, the mean as the offset
+        t[0] = 1.0, t[1] = 0.0, t[2] = 0.0;
+        b[0] = 0.0, b[1] = 1.0, b[2] = 0.0;
+    } else {
+        basis_f64(muw, t, b);
+    }
     lower_inverse5_f64(L, Li);
     const double lpi = pi > 0.0 ? log(pi) : -INFINITY;
     const double ldA = log(L[pk(0, 0)]) + log(L[pk(1, 1)]) + log(L[pk(2, 2)]);
@@ -176,6 +182,10 @@ __device__ inline void write_records(double pi, const double mux[3], const doubl
         for (int c = 0; c < 3; ++c) me[c] += delta[c];
         er[28] = (float)delta[3];
         er[29] = (float)delta[4];
+    }
+    if (euclid) {
+        er[28] = (float)(muw[0] + (delta != nullptr ? delta[3] : 0.0));
+        er[29] = (float)(muw[1] + (delta != nullptr ? delta[4] : 0.0));
     }
     for (int c = 0; c < 3; ++c) {
         er[c] = (float)me[c];

@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(kWarps * 32, MODE == MODE_TWO ? 1 : 2)
     k_accumulate(WsHeader* __restrict__ ws, const int64_t* __restrict__ chunk_base,
                  const int32_t* __restrict__ chunk_region, const float* __restrict__ etab, int K,
                  int chunk, int density, float* __restrict__ partial, int ps, int write_ll,
-                 const float* __restrict__ chart2) {
+                 const float* __restrict__ chart2, int euclid) {
     constexpr int SPI = 32 / KP;
     constexpr int NS = MODE == MODE_TWO ? 15 : kStat;   // statistics per component
     constexpr int RED = KP * kStat + 4;
@@ -213,15 +213,21 @@ __global__ void __launch_bounds__(kWarps * 32, MODE == MODE_TWO ? 1 : 2)
                 const int j = t + h;
                 const float4 sa = *reinterpret_cast<const float4*>(&sbuf[warp][j][0]);
                 const float4 sb = *reinterpret_cast<const float4*>(&sbuf[warp][j][4]);
-                // log map at this lane's component (Sec. 3.1 Eq. log)
+                // log map at this lane's component (Sec. 3.1 Eq. log); the
+                // Euclidean ablation has unit rows and no change of variables
                 const float u = prm[3] * sb.x + prm[4] * sb.y + prm[5] * sb.z;
                 const float v = prm[6] * sb.x + prm[7] * sb.y + prm[8] * sb.z;
-                const float cz = prm[9] * sb.x + prm[10] * sb.y + prm[11] * sb.z;
-                const float s2 = u * u + v * v;
-                const float rs = rsqrtf(s2);
-                const float th = atan2_pos(s2 * rs, cz);
-                const bool off_centre = s2 > 0.f;
-                const float gg = off_centre ? th * rs : 1.f;
+                float gg = 1.f;
+                bool cut = false;
+                if (!euclid) {
+                    const float cz = prm[9] * sb.x + prm[10] * sb.y + prm[11] * sb.z;
+                    const float s2 = u * u + v * v;
+                    const float rs = rsqrtf(s2);
+                    const float th = atan2_pos(s2 * rs, cz);
+                    const bool off_centre = s2 > 0.f;
+                    gg = off_centre ? th * rs : 1.f;
+                    cut = !off_centre && cz < 0.f;   // cut locus: undefined chart
+                }
                 float d[5];
                 d[0] = (sa.x - prm[0]) - prm[32];
                 d[1] = (sa.y - prm[1]) - prm[33];
@@ -238,7 +244,7 @@ __global__ void __launch_bounds__(kWarps * 32, MODE == MODE_TWO ? 1 : 2)
                 const float q = y[0] * y[0] + y[1] * y[1] + y[2] * y[2] + y[3] * y[3] + y[4] * y[4];
                 float l = prm[27] - 0.5f * q;
                 if (density) l += __logf(gg);
-                if (!off_centre && cz < 0.f) l = -INFINITY;   // cut locus: undefined chart
+                if (cut) l = -INFINITY;
                 // log-sum-exp over the KP component lanes of this sample, shifted
                 // by the region bound; the exact per-sample maximum is used only
                 // when that underflows (or when the bound does not hold)
@@ -364,10 +370,20 @@ __device__ inline double prior_beta(const sdmm_config& cfg, const double* prior_
 // chart statistics [s0, s1 (5), s2 (15)].  Rows a, b, c hold sums of
 // w r phi, w r g phi and w r g^2 phi over the features
 // phi = [1, x', vech(x'x'), w, w (x) x', vech(ww)] with x' = x - xref.
+//
+// Euclidean ablation: g = 1 (the three rows agree), unit rows A = (e_x, e_y)
+// and the direction measured from the mean, nu = A w - (mu_x, mu_y): the
+// statistics of nu pick up the offset terms below.
 __device__ inline void features_to_stats(const double* Fa, const double* Fb, const double* Fc,
-                                         const double mp[3], const double muw[3], double* out) {
+                                         const double mp[3], const double muw[3], double* out,
+                                         bool euclid = false) {
     double t[3], b[3];
-    basis_f64(muw, t, b);
+    if (euclid) {
+        t[0] = 1.0, t[1] = 0.0, t[2] = 0.0;
+        b[0] = 0.0, b[1] = 1.0, b[2] = 0.0;
+    } else {
+        basis_f64(muw, t, b);
+    }
     const double A[2][3] = {{t[0], t[1], t[2]}, {b[0], b[1], b[2]}};
     static constexpr int V[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};   // vech index of (p, q)
     const double s0 = Fa[0];
@@ -395,6 +411,18 @@ __device__ inline void features_to_stats(const double* Fa, const double* Fb, con
                 for (int q = 0; q < 3; ++q) v += A[i][p] * Fc[22 + V[p][q]] * A[j][q];
             s2[pk(3 + i, 3 + j)] = v;
         }
+    if (euclid) {
+        // sums of A w are in s1[3..4] and s2[(3+i), *]; shift them by o = (mu_x, mu_y)
+        const double o[2] = {muw[0], muw[1]};
+        const double aw[2] = {s1[3], s1[4]};
+        for (int i = 0; i < 2; ++i)
+            for (int j = 0; j <= i; ++j)
+                s2[pk(3 + i, 3 + j)] += -o[i] * aw[j] - aw[i] * o[j] + s0 * o[i] * o[j];
+        for (int i = 0; i < 2; ++i) {
+            for (int a = 0; a < 3; ++a) s2[pk(3 + i, a)] -= o[i] * s1[a];
+            s1[3 + i] = aw[i] - o[i] * s0;
+        }
+    }
 }
 
 // Second-pass charts of the accurate covariance update: per component the
@@ -487,7 +515,8 @@ __global__ void __launch_bounds__(128) k_reduce_mstep(WsHeader* __restrict__ ws,
                 muw[c] = st.mu_w[rk * 3 + c];
             }
             features_to_stats(s_feat + tid * kFeat, s_feat + (K + tid) * kFeat,
-                              s_feat + (2 * K + tid) * kFeat, mp, muw, s_st + tid * kStat);
+                              s_feat + (2 * K + tid) * kFeat, mp, muw, s_st + tid * kStat,
+                              cfg.dir_coords == SDMM_DIR_EUCLIDEAN);
         }
         if (tid == 0) {   // W and sum w l arrive as four per-quadrant parts each
             const double* wq = s_feat + 3 * K * kFeat;
@@ -517,6 +546,7 @@ __global__ void __launch_bounds__(128) k_reduce_mstep(WsHeader* __restrict__ ws,
                            ? 1.0
                            : pow(cfg.eta_beta * (double)st.step_j[r] + 1.0, -cfg.eta_alpha);
     const double q = cfg.prior_q / K, a = cfg.prior_a / K;
+    const bool euclid = cfg.dir_coords == SDMM_DIR_EUCLIDEAN;
 
     double nmx[3], nmw[3], nL[15], nS2[15], hS0 = 0.0;
     int code = 0;
@@ -547,7 +577,13 @@ __global__ void __launch_bounds__(128) k_reduce_mstep(WsHeader* __restrict__ ws,
                 omw[c] = st.mu_w[rk * 3 + c];
                 nmx[c] = omx[c] + m[c];
             }
-            exp_map_f64(omw, m + 3, nmw);                 // Eq. tangent-space-mu-update
+            if (euclid) {                                 // ablation: translate (x, y)
+                nmw[0] = omw[0] + m[3];
+                nmw[1] = omw[1] + m[4];
+                nmw[2] = omw[2];
+            } else {
+                exp_map_f64(omw, m + 3, nmw);             // Eq. tangent-space-mu-update
+            }
             if (partial2 != nullptr) {
                 // accurate update (Eq. tangent-space-sigma-update): the second
                 // pass measured the batch in the new chart, centred at the new mean
@@ -558,8 +594,8 @@ __global__ void __launch_bounds__(128) k_reduce_mstep(WsHeader* __restrict__ ws,
                 for (int i = 0; i < 5; ++i)
                     for (int j = 0; j <= i; ++j) C[pk(i, j)] = hS2[pk(i, j)] - hS0 * m[i] * m[j];
                 // ... moved to the new chart: T C T^T, T = blockdiag(I3, J) (Sec. 3.4)
-                double J[4];
-                chart_jacobian_f64(omw, m + 3, nmw, J);
+                double J[4] = {1.0, 0.0, 0.0, 1.0};
+                if (!euclid) chart_jacobian_f64(omw, m + 3, nmw, J);
                 for (int i = 0; i < 3; ++i)
                     for (int j = 0; j <= i; ++j) nS2[pk(i, j)] = C[pk(i, j)];
                 for (int ia = 0; ia < 2; ++ia)
@@ -628,7 +664,7 @@ __global__ void __launch_bounds__(128) k_reduce_mstep(WsHeader* __restrict__ ws,
             st.S2[rk * 15 + p] = nS2[p];
         }
         st.S0[rk] = hS0;
-        write_records(npi, nmx, nmw, nL, st.etab + rk * kE, st.qtab + rk * kQ);
+        write_records(npi, nmx, nmw, nL, st.etab + rk * kE, st.qtab + rk * kQ, nullptr, euclid);
     }
     if (tid == 0) {
         st.Wbar[r] = (1.0 - eta) * st.Wbar[r] + eta * (W / (double)M);
@@ -805,7 +841,8 @@ __global__ void k_init_regions(sdmm_config cfg, BatchDesc d, const double* __res
                 st.mu_w[rk * 3 + c] = dv[c];
             }
             for (int p = 0; p < 15; ++p) st.L[rk * 15 + p] = L[p];
-            write_records(1.0 / K, mx, dv, L, st.etab + rk * kE, st.qtab + rk * kQ);
+            write_records(1.0 / K, mx, dv, L, st.etab + rk * kE, st.qtab + rk * kQ, nullptr,
+                          cfg.dir_coords == SDMM_DIR_EUCLIDEAN);
         }
     }
     st.status[r] = SDMM_REGION_OK;
@@ -813,7 +850,7 @@ __global__ void k_init_regions(sdmm_config cfg, BatchDesc d, const double* __res
 
 // ---------------------------------------------------------------------------
 __global__ void k_prepare(int K, int64_t R, sdmm_state st, const double* __restrict__ logits,
-                          const double* __restrict__ delta) {
+                          const double* __restrict__ delta, int euclid) {
     const int64_t rk = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (rk >= R * K) return;
     if (logits != nullptr) {
@@ -832,7 +869,7 @@ __global__ void k_prepare(int K, int64_t R, sdmm_state st, const double* __restr
     }
     for (int p = 0; p < 15; ++p) L[p] = st.L[rk * 15 + p];
     write_records(st.pi[rk], mx, mw, L, st.etab + rk * kE, st.qtab + rk * kQ,
-                  delta != nullptr ? delta + rk * 5 : nullptr);
+                  delta != nullptr ? delta + rk * 5 : nullptr, euclid != 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -841,11 +878,11 @@ template <int MODE>
 static cudaError_t launch_acc_mode(int KP, dim3 grid, cudaStream_t s, WsHeader* ws,
                                    const int64_t* cb, const int32_t* cr, const float* etab, int K,
                                    int chunk, int density, float* partial, int ps, int write_ll,
-                                   const float* chart2) {
+                                   const float* chart2, int euclid) {
 #define SDMM_ACC_CASE(P)                                                                       \
     case P:                                                                                    \
         k_accumulate<P, MODE><<<grid, kWarps * 32, 0, s>>>(ws, cb, cr, etab, K, chunk, density, \
-                                                          partial, ps, write_ll, chart2);      \
+                                                          partial, ps, write_ll, chart2, euclid); \
         break;
     switch (KP) {
         SDMM_ACC_CASE(1)
@@ -874,15 +911,15 @@ cudaError_t launch_build_chunks(cudaStream_t s, WsHeader* ws, int64_t* cb, int32
 cudaError_t launch_accumulate(cudaStream_t s, int mode, int KP, int grid, WsHeader* ws,
                               const int64_t* cb, const int32_t* cr, const float* etab, int K,
                               int chunk, int density, float* partial, int ps, int write_ll,
-                              const float* chart2) {
+                              const float* chart2, int euclid) {
     if (mode == MODE_FIT)
         return launch_acc_mode<MODE_FIT>(KP, dim3(grid), s, ws, cb, cr, etab, K, chunk, density,
-                                         partial, ps, write_ll, nullptr);
+                                         partial, ps, write_ll, nullptr, euclid);
     if (mode == MODE_TWO)
         return launch_acc_mode<MODE_TWO>(KP, dim3(grid), s, ws, cb, cr, etab, K, chunk, density,
-                                         partial, ps, 0, chart2);
+                                         partial, ps, 0, chart2, 0);
     return launch_acc_mode<MODE_GRAD>(KP, dim3(grid), s, ws, cb, cr, etab, K, chunk, density,
-                                      partial, ps, write_ll, nullptr);
+                                      partial, ps, write_ll, nullptr, euclid);
 }
 
 cudaError_t launch_new_charts(cudaStream_t s, int64_t R, WsHeader* ws, const int64_t* cb,
@@ -921,10 +958,10 @@ cudaError_t launch_init(cudaStream_t s, int64_t R, const sdmm_config& cfg, const
 }
 
 cudaError_t launch_prepare(cudaStream_t s, int K, int64_t R, const sdmm_state& st,
-                           const double* logits, const double* delta) {
+                           const double* logits, const double* delta, int euclid) {
     const int64_t n = R * K;
     const unsigned blocks = (unsigned)((n + 127) / 128);
-    k_prepare<<<blocks, 128, 0, s>>>(K, R, st, logits, delta);
+    k_prepare<<<blocks, 128, 0, s>>>(K, R, st, logits, delta, euclid);
     return cudaGetLastError();
 }
 

@@ -25,7 +25,7 @@ cudaError_t launch_build_chunks(cudaStream_t s, WsHeader* ws, int64_t* cb, int32
 cudaError_t launch_accumulate(cudaStream_t s, int mode, int KP, int grid, WsHeader* ws,
                               const int64_t* cb, const int32_t* cr, const float* etab, int K,
                               int chunk, int density, float* partial, int ps, int write_ll,
-                              const float* chart2 = nullptr);
+                              const float* chart2 = nullptr, int euclid = 0);
 cudaError_t launch_new_charts(cudaStream_t s, int64_t R, WsHeader* ws, const int64_t* cb,
                               const float* partial, int ps, const sdmm_config& cfg,
                               const sdmm_state& st, float* chart2);
@@ -37,11 +37,11 @@ cudaError_t launch_reduce_mstep(cudaStream_t s, int64_t R, WsHeader* ws, const i
 size_t tc_smem_bytes(int K, int prec);
 
 cudaError_t launch_tc_prepare(cudaStream_t s, int K, int64_t R, const sdmm_state& st, float* ctab,
-                              float* xref);
+                              float* xref, int euclid = 0);
 int tc_ctas_per_sm(int K, int prec);
 cudaError_t launch_tc_estep(cudaStream_t s, int K, int prec, int grid, WsHeader* ws, const int32_t* cr,
                             const int64_t* units, const float* ctab, const float* xref, float* partial,
-                            int ps, int write_ll);
+                            int ps, int write_ll, int euclid = 0);
 cudaError_t launch_reduce_objective(cudaStream_t s, int64_t R, const WsHeader* ws,
                                     const int64_t* cb, const float* partial, int ps,
                                     const sdmm_config& cfg, const sdmm_state& st, double* F,
@@ -49,7 +49,7 @@ cudaError_t launch_reduce_objective(cudaStream_t s, int64_t R, const WsHeader* w
 cudaError_t launch_init(cudaStream_t s, int64_t R, const sdmm_config& cfg, const BatchDesc& d,
                         const double* extent, const double* uniforms, const sdmm_state& st);
 cudaError_t launch_prepare(cudaStream_t s, int K, int64_t R, const sdmm_state& st,
-                           const double* logits, const double* delta);
+                           const double* logits, const double* delta, int euclid = 0);
 
 cudaError_t launch_query(cudaStream_t s, int op, int KP, int grid, const float* qtab, int K,
                          int64_t R, int64_t Q, const float* qx, const int32_t* region,

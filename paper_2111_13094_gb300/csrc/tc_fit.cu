@@ -146,7 +146,7 @@ constexpr float kLn2 = 0.693147180559945309f;
 // coefficient rows of component rk: ctab[rk][6][32] (u, v, c, T0, T1, T2),
 // the last three scaled by log2(e)
 __global__ void k_tc_prepare(int K, int64_t R, sdmm_state st, float* __restrict__ ctab,
-                             float* __restrict__ xref) {
+                             float* __restrict__ xref, int euclid) {
     const int64_t rk = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (rk >= R * K) return;
     const int64_t r = rk / K;
@@ -177,7 +177,12 @@ __global__ void k_tc_prepare(int K, int64_t R, sdmm_state st, float* __restrict_
             Q[i][j] = s;
         }
     double t[3], b[3];
-    basis_f64(muw, t, b);
+    if (euclid) {   // Euclidean ablation: unit rows, nu = A w - (mu_x, mu_y), g = 1
+        t[0] = 1.0, t[1] = 0.0, t[2] = 0.0;
+        b[0] = 0.0, b[1] = 1.0, b[2] = 0.0;
+    } else {
+        basis_f64(muw, t, b);
+    }
     const double A[2][3] = {{t[0], t[1], t[2]}, {b[0], b[1], b[2]}};
     double M[3][3], N[3][3];
     for (int a = 0; a < 3; ++a)
@@ -221,6 +226,19 @@ __global__ void k_tc_prepare(int K, int64_t R, sdmm_state st, float* __restrict_
     for (int p = 0; p < 3; ++p) {
         row[4][10 + p] = mp[0] * M[0][p] + mp[1] * M[1][p] + mp[2] * M[2][p];
         for (int q = 0; q < 3; ++q) row[4][13 + 3 * p + q] = -M[q][p];
+    }
+    if (euclid) {
+        // the offset o of nu = A w - o adds (x'-mu')^T Q_xn o - o^T Q_nn o / 2 to T0 and
+        // w^T A^T Q_nn o to T1 (the kernel sums T0 + T1 + T2 with g = 1)
+        const double o[2] = {muw[0], muw[1]};
+        double wo[3], ono = 0.0;
+        for (int a = 0; a < 3; ++a) wo[a] = Q[a][3] * o[0] + Q[a][4] * o[1];
+        for (int i = 0; i < 2; ++i)
+            for (int j = 0; j < 2; ++j) ono += o[i] * Q[3 + i][3 + j] * o[j];
+        row[3][0] += -(mp[0] * wo[0] + mp[1] * wo[1] + mp[2] * wo[2]) - 0.5 * ono;
+        for (int a = 0; a < 3; ++a) row[3][1 + a] += wo[a];
+        for (int p = 0; p < 3; ++p)
+            for (int i = 0; i < 2; ++i) row[4][10 + p] += A[i][p] * (Q[3 + i][3] * o[0] + Q[3 + i][4] * o[1]);
     }
     // T0, T1, T2 are stored times log2(e): the kernel's log-sum-exp runs in base 2
     for (int i = 3; i < 6; ++i)
@@ -375,7 +393,8 @@ template <int K, int PREC>
 __global__ void __launch_bounds__(kTcThreads, TcPlan<K, PREC>::kCtas)
     k_tc_estep(WsHeader* __restrict__ ws, const int32_t* __restrict__ chunk_region,
                const int64_t* __restrict__ units, const float* __restrict__ ctab,
-               const float* __restrict__ xref, float* __restrict__ partial, int ps, int write_ll) {
+               const float* __restrict__ xref, float* __restrict__ partial, int ps, int write_ll,
+               int euclid) {
     using P = TcPlan<K, PREC>;
     constexpr int KG = P::kKG;
     constexpr int RPQ = P::kM2 / 4;                // GEMM 2 rows per TMEM lane quadrant
@@ -732,6 +751,11 @@ __global__ void __launch_bounds__(kTcThreads, TcPlan<K, PREC>::kCtas)
         float lk[KG], gk[KG];
         {
             auto eval1 = [&](const float* q, int j) {
+                if (euclid) {                   // ablation: no change of variables, g = 1
+                    lk[j] = q[3] + q[4] + q[5];
+                    gk[j] = 1.f;
+                    return;
+                }
                 const float u = q[0], vv = q[1], cz = q[2];
                 const float s2 = u * u + vv * vv;
                 const float rs = tc::rsqrt_approx(s2);
@@ -866,28 +890,29 @@ int tc_ctas_per_sm(int K, int prec) {
 }
 
 cudaError_t launch_tc_prepare(cudaStream_t s, int K, int64_t R, const sdmm_state& st, float* ctab,
-                              float* xref) {
+                              float* xref, int euclid) {
     const int64_t n = R * K;
-    k_tc_prepare<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(K, R, st, ctab, xref);
+    k_tc_prepare<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(K, R, st, ctab, xref, euclid);
     return cudaGetLastError();
 }
 
 template <int K, int PREC>
 static cudaError_t launch_tc_estep_t(cudaStream_t s, int grid, WsHeader* ws, const int32_t* cr,
                                      const int64_t* units, const float* ctab, const float* xref,
-                                     float* partial, int ps, int write_ll) {
+                                     float* partial, int ps, int write_ll, int euclid) {
     const int bytes = TcPlan<K, PREC>::kBytes;
     cudaError_t e = cudaFuncSetAttribute(k_tc_estep<K, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
-    k_tc_estep<K, PREC><<<grid, kTcThreads, bytes, s>>>(ws, cr, units, ctab, xref, partial, ps, write_ll);
+    k_tc_estep<K, PREC><<<grid, kTcThreads, bytes, s>>>(ws, cr, units, ctab, xref, partial, ps, write_ll,
+                                                        euclid);
     return cudaGetLastError();
 }
 
 cudaError_t launch_tc_estep(cudaStream_t s, int K, int prec, int grid, WsHeader* ws, const int32_t* cr,
                             const int64_t* units, const float* ctab, const float* xref, float* partial,
-                            int ps, int write_ll) {
+                            int ps, int write_ll, int euclid) {
 #define SDMM_TC_CASE(KK, PP) \
-    if (K == KK && prec == PP) return launch_tc_estep_t<KK, PP>(s, grid, ws, cr, units, ctab, xref, partial, ps, write_ll);
+    if (K == KK && prec == PP) return launch_tc_estep_t<KK, PP>(s, grid, ws, cr, units, ctab, xref, partial, ps, write_ll, euclid);
     SDMM_TC_CASE(16, SDMM_PREC_TC_3XBF16) SDMM_TC_CASE(16, SDMM_PREC_TC_TF32)
     SDMM_TC_CASE(16, SDMM_PREC_TC_3XTF32) SDMM_TC_CASE(32, SDMM_PREC_TC_3XBF16)
     SDMM_TC_CASE(32, SDMM_PREC_TC_TF32) SDMM_TC_CASE(32, SDMM_PREC_TC_3XTF32)

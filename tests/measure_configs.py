@@ -215,6 +215,40 @@ def estep_density(seed=50, R=1024, M=16384, K=16, reps=10):
     return out
 
 
+def euclid_ablation(seed=80, R=1024, M=65536, K=16, reps=10):
+    """E-step cost of the change of variables: the tangent-chart fit (paper)
+    against the Euclidean ablation (no log map), for the FP32 SIMT form and
+    the 6xBF16 contraction form, one EM step per run (GPU time of the E-step
+    kernel from the plan's events)."""
+    truth = syn.batched_truth(seed, R, K=K)
+    counts = np.full(R, M, dtype=np.int64)
+    N = R * M
+    dev = torch.device("cuda")
+    samples = syn.draw_torch(seed, truth, counts, device=dev)
+    batch = api.SampleBatch(samples, torch.from_numpy(syn.offsets_from_counts(counts)).to(dev))
+    _, h, _ = syn.region_grid(R)
+    out = {"config": f"E-step, tangent vs Euclidean directions, {R} regions x {M} samples, K = {K}"}
+    for pname, prec in (("fp32", api.PREC_FP32), ("6xbf16", api.PREC_TC_6XBF16)):
+        for dname, dc in (("tangent", api.DIR_TANGENT), ("euclidean", api.DIR_EUCLIDEAN)):
+            cfg = api.config(K, precision=prec, dir_coords=dc)
+            st = api.MixtureState(R, K, device=dev)
+            api.init_regions(cfg, batch, torch.from_numpy(h.astype(np.float64)).to(dev),
+                             torch.from_numpy(syn.init_uniforms(seed, R, K // 8)).to(dev), st)
+            ws = api.workspace(cfg, R, N, device=dev)
+            plan = api.FitPlan(cfg, R, N, 1, st, ws)
+            for _ in range(3):
+                plan.run(batch)
+            plan.enable_timing(reps)
+            for _ in range(reps):
+                plan.run(batch)
+            torch.cuda.synchronize()
+            out[f"{pname}_{dname}_estep_ms"] = float(np.mean(plan.timing()))
+            plan.close()
+            del plan, ws, st
+        out[f"{pname}_ratio"] = out[f"{pname}_tangent_estep_ms"] / out[f"{pname}_euclidean_estep_ms"]
+    return out
+
+
 def product_queries(seed=60, Q=1 << 24, K=16, J=3, dims=(64, 32, 32), reps=10):
     """Guided queries with and without the BSDF product on the same positions
     (grid lookup, one Philox draw per query): GPU time per batch."""
@@ -252,6 +286,9 @@ def main():
     args = ap.parse_args()
     if args.which == ["product"]:
         print(json.dumps(product_queries(Q=args.queries)))
+        return
+    if args.which == ["euclid"]:
+        print(json.dumps(euclid_ablation()))
         return
     a = single_region()
     b = objective_adjoint()
