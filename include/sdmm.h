@@ -135,7 +135,9 @@ typedef struct sdmm_config {
     int32_t dir_coords;        /* SDMM_DIR_*: tangent charts (default) or the
                                   Euclidean ablation (fit and objective only;
                                   queries, product sampling and the two-pass
-                                  update reject it: SDMM_ERR_UNSUPPORTED)     */
+                                  update reject it, and of the tensor-core
+                                  forms it runs on 6xBF16 and 3xTF32:
+                                  SDMM_ERR_UNSUPPORTED)                       */
     double eta_alpha;          /* 0.5 (Sec. 4.3)                              */
     double eta_beta;           /* 0.1 (Sec. 4.3)                              */
     double prior_q;            /* Dirichlet prior q = prior_q / K; paper 1    */

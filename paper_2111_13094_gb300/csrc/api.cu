@@ -81,6 +81,9 @@ sdmm_status check_config(const sdmm_config* cfg) {
         return fail(SDMM_ERR_INVALID_ARG, "dir_coords %d", cfg->dir_coords);
     if (cfg->dir_coords == SDMM_DIR_EUCLIDEAN && cfg->cov_update == SDMM_COV_TWO_PASS)
         return fail(SDMM_ERR_UNSUPPORTED, "the two-pass covariance update needs tangent charts");
+    if (cfg->dir_coords == SDMM_DIR_EUCLIDEAN && cfg->precision != SDMM_PREC_FP32 &&
+        cfg->precision != SDMM_PREC_TC_6XBF16 && cfg->precision != SDMM_PREC_TC_3XTF32)
+        return fail(SDMM_ERR_UNSUPPORTED, "the Euclidean ablation runs on FP32 SIMT, 6xBF16 or 3xTF32");
     const double v[6] = {cfg->eta_alpha, cfg->eta_beta, cfg->prior_q, cfg->prior_a,
                          cfg->prior_B_pos, cfg->prior_B_dir};
     for (double x : v)

@@ -389,12 +389,11 @@ struct TcTile {
     bool first, live;   // first tile of its unit; tile exists
 };
 
-template <int K, int PREC>
+template <int K, int PREC, bool EU>
 __global__ void __launch_bounds__(kTcThreads, TcPlan<K, PREC>::kCtas)
     k_tc_estep(WsHeader* __restrict__ ws, const int32_t* __restrict__ chunk_region,
                const int64_t* __restrict__ units, const float* __restrict__ ctab,
-               const float* __restrict__ xref, float* __restrict__ partial, int ps, int write_ll,
-               int euclid) {
+               const float* __restrict__ xref, float* __restrict__ partial, int ps, int write_ll) {
     using P = TcPlan<K, PREC>;
     constexpr int KG = P::kKG;
     constexpr int RPQ = P::kM2 / 4;                // GEMM 2 rows per TMEM lane quadrant
@@ -406,6 +405,7 @@ __global__ void __launch_bounds__(kTcThreads, TcPlan<K, PREC>::kCtas)
     __shared__ int s_abort;
     __shared__ float2 s_ml[kTcGroups][kTile];      // per group, per sample: (m, sum 2^(l_k log2 e - m))
     __shared__ float s_xr[3][4][4];                // per staging slot and quadrant: region reference point
+    __shared__ const float* s_stream[7];           // the batch's sample streams (fixed for the launch)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int quad = warp & 3, grp = warp >> 2;
     const int smp = quad * 32 + lane;              // sample (TMEM lane) of this thread
@@ -425,6 +425,7 @@ __global__ void __launch_bounds__(kTcThreads, TcPlan<K, PREC>::kCtas)
         tc::tmem_alloc(&tmem_base, P::kCols);
         tc::tmem_relinquish();
     }
+    if (tid < 7) s_stream[tid] = ws->desc.p[tid];
     if (tid == 0) {
         tc::mbar_init(&bar1, 1);
         tc::mbar_init(&bar2, 1);
@@ -443,21 +444,24 @@ __global__ void __launch_bounds__(kTcThreads, TcPlan<K, PREC>::kCtas)
     // ---- work units of this CTA: a static round robin over the CTAs, walked
     // in the same order by every warp; the next unit's range is loaded one
     // unit ahead
-    const int n_chunks = ws->n_chunks;
-    int uc = blockIdx.x, pr = -1;
+    const int64_t n_chunks = ws->n_chunks;
+    const int64_t R = ws->desc.R;
+    int64_t uc = blockIdx.x;
+    const int64_t u_end = n_chunks;
+    int pr = -1;
     int64_t ps0 = 0, pe = 0, uend = 0;   // next unit's start / end; end of the unit being walked
     auto fetch = [&]() {
-        if (uc < n_chunks) {
+        if (uc < u_end) {
             pr = __ldg(chunk_region + uc);
             ps0 = __ldg(units + 2 * uc);
             pe = __ldg(units + 2 * uc + 1);
         }
     };
     auto enter = [&](TcTile& tl) {
-        tl.live = uc < n_chunks;
+        tl.live = uc < u_end;
         if (!tl.live) return;
-        tl.c = uc;
-        tl.r = (pr >= 0 && pr < ws->desc.R) ? pr : -1;
+        tl.c = (int)uc;
+        tl.r = (pr >= 0 && pr < R) ? pr : -1;
         tl.g0 = ps0;
         uend = tl.r >= 0 ? pe : ps0;
         tl.n = (int)min((int64_t)kTile, uend - ps0);
@@ -614,7 +618,7 @@ __global__ void __launch_bounds__(kTcThreads, TcPlan<K, PREC>::kCtas)
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int q = 4 * grp + j;
-            if (q < 7) tc::cp_async4s(dst + q * kStream, ws->desc.p[q] + i, valid);
+            if (q < 7) tc::cp_async4s(dst + q * kStream, s_stream[q] + i, valid);
         }
         if (grp == 0 && lane < 3) {
             const bool rv = tl.live && tl.r >= 0;
@@ -751,7 +755,7 @@ __global__ void __launch_bounds__(kTcThreads, TcPlan<K, PREC>::kCtas)
         float lk[KG], gk[KG];
         {
             auto eval1 = [&](const float* q, int j) {
-                if (euclid) {                   // ablation: no change of variables, g = 1
+                if constexpr (EU) {             // ablation: no change of variables, g = 1
                     lk[j] = q[3] + q[4] + q[5];
                     gk[j] = 1.f;
                     return;
@@ -896,15 +900,15 @@ cudaError_t launch_tc_prepare(cudaStream_t s, int K, int64_t R, const sdmm_state
     return cudaGetLastError();
 }
 
-template <int K, int PREC>
+template <int K, int PREC, bool EU>
 static cudaError_t launch_tc_estep_t(cudaStream_t s, int grid, WsHeader* ws, const int32_t* cr,
                                      const int64_t* units, const float* ctab, const float* xref,
-                                     float* partial, int ps, int write_ll, int euclid) {
+                                     float* partial, int ps, int write_ll) {
     const int bytes = TcPlan<K, PREC>::kBytes;
-    cudaError_t e = cudaFuncSetAttribute(k_tc_estep<K, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_tc_estep<K, PREC, EU>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
-    k_tc_estep<K, PREC><<<grid, kTcThreads, bytes, s>>>(ws, cr, units, ctab, xref, partial, ps, write_ll,
-                                                        euclid);
+    k_tc_estep<K, PREC, EU><<<grid, kTcThreads, bytes, s>>>(ws, cr, units, ctab, xref, partial, ps, write_ll);
     return cudaGetLastError();
 }
 
@@ -912,12 +916,20 @@ cudaError_t launch_tc_estep(cudaStream_t s, int K, int prec, int grid, WsHeader*
                             const int64_t* units, const float* ctab, const float* xref, float* partial,
                             int ps, int write_ll, int euclid) {
 #define SDMM_TC_CASE(KK, PP) \
-    if (K == KK && prec == PP) return launch_tc_estep_t<KK, PP>(s, grid, ws, cr, units, ctab, xref, partial, ps, write_ll, euclid);
+    if (!euclid && K == KK && prec == PP) \
+        return launch_tc_estep_t<KK, PP, false>(s, grid, ws, cr, units, ctab, xref, partial, ps, write_ll);
+#define SDMM_TC_CASE_EU(KK, PP) \
+    if (euclid && K == KK && prec == PP) \
+        return launch_tc_estep_t<KK, PP, true>(s, grid, ws, cr, units, ctab, xref, partial, ps, write_ll);
     SDMM_TC_CASE(16, SDMM_PREC_TC_3XBF16) SDMM_TC_CASE(16, SDMM_PREC_TC_TF32)
     SDMM_TC_CASE(16, SDMM_PREC_TC_3XTF32) SDMM_TC_CASE(32, SDMM_PREC_TC_3XBF16)
     SDMM_TC_CASE(32, SDMM_PREC_TC_TF32) SDMM_TC_CASE(32, SDMM_PREC_TC_3XTF32)
     SDMM_TC_CASE(16, SDMM_PREC_TC_6XBF16) SDMM_TC_CASE(32, SDMM_PREC_TC_6XBF16)
+    // the Euclidean ablation: the two forms that meet the parity contract
+    SDMM_TC_CASE_EU(16, SDMM_PREC_TC_6XBF16) SDMM_TC_CASE_EU(32, SDMM_PREC_TC_6XBF16)
+    SDMM_TC_CASE_EU(16, SDMM_PREC_TC_3XTF32) SDMM_TC_CASE_EU(32, SDMM_PREC_TC_3XTF32)
 #undef SDMM_TC_CASE
+#undef SDMM_TC_CASE_EU
     return cudaErrorInvalidValue;
 }
 

@@ -77,3 +77,12 @@ def test_host_validation_errors(lib):
                                        1, 10, ctypes.byref(n)) == 4
     assert lib.sdmm_fit_workspace_size(ctypes.byref(api.config(16, cov_update=1, eta_mode=1)), 1, 10,
                                        ctypes.byref(n)) == 0
+    # the Euclidean ablation: fit only, FP32 SIMT, 6xBF16 or 3xTF32, first-order update
+    for prec, want in ((0, 0), (4, 0), (3, 0), (1, 4), (2, 4)):
+        assert lib.sdmm_fit_workspace_size(ctypes.byref(api.config(16, dir_coords=1, precision=prec)), 1, 10,
+                                           ctypes.byref(n)) == want, prec
+    assert lib.sdmm_fit_workspace_size(ctypes.byref(api.config(16, dir_coords=1, cov_update=1, eta_mode=1)), 1, 10,
+                                       ctypes.byref(n)) == 4
+    assert lib.sdmm_fit_workspace_size(ctypes.byref(api.config(16, dir_coords=2)), 1, 10, ctypes.byref(n)) == 1
+    assert lib.sdmm_condition(ctypes.byref(api.config(16, dir_coords=1)), None, 1, 1, None, None, ctypes.byref(g),
+                              None, None, None, None) in (1, 4)
