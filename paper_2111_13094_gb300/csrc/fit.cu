@@ -222,11 +222,8 @@ __global__ void __launch_bounds__(kWarps * 32, MODE == MODE_TWO ? 1 : 2)
                 if (!euclid) {
                     const float cz = prm[9] * sb.x + prm[10] * sb.y + prm[11] * sb.z;
                     const float s2 = u * u + v * v;
-                    const float rs = rsqrtf(s2);
-                    const float th = atan2_pos(s2 * rs, cz);
-                    const bool off_centre = s2 > 0.f;
-                    gg = off_centre ? th * rs : 1.f;
-                    cut = !off_centre && cz < 0.f;   // cut locus: undefined chart
+                    cut = s2 == 0.f && cz < 0.f;     // cut locus: undefined chart
+                    gg = cut ? 1.f : g_of_cos(cz, rsqrtf(s2));
                 }
                 float d[5];
                 d[0] = (sa.x - prm[0]) - prm[32];

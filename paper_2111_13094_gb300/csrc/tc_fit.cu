@@ -762,12 +762,10 @@ __global__ void __launch_bounds__(kTcThreads, TcPlan<K, PREC>::kCtas)
                 }
                 const float u = q[0], vv = q[1], cz = q[2];
                 const float s2 = u * u + vv * vv;
-                const float rs = tc::rsqrt_approx(s2);
-                const float th = atan2_pos(s2 * rs, cz);
-                const bool off_centre = s2 > 0.f;
-                const float g = off_centre ? th * rs : 1.f;
+                const bool cut = s2 == 0.f && cz < 0.f;    // cut locus: undefined chart
+                const float g = cut ? 1.f : g_of_cos(cz, tc::rsqrt_approx(s2));
                 float l = q[3] + g * (q[4] + g * q[5]);
-                if (!off_centre && cz < 0.f) l = -INFINITY;
+                if (cut) l = -INFINITY;
                 lk[j] = l;
                 gk[j] = g;
             };
