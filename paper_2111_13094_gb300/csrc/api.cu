@@ -854,8 +854,8 @@ sdmm_status sdmm_autotune(const sdmm_config* cfg, const sdmm_samples* s, const s
 namespace {
 
 struct KdLayout {
-    size_t perm[2], seg_off[2], seg_node[2], seg_parent[2], seg_axis, seg_split, seg_flag, seg_new, seg_sum,
-        seg_left, tile_seg, tile_start, tile_left, tile_prefix, first_tile, counters, total;
+    size_t rec[2], seg_off[2], seg_node[2], seg_parent[2], seg_axis, seg_split, seg_flag, seg_new, seg_sum,
+        seg_left, tile_seg, tile_start, tile_left, tile_prefix, seg_tile0, counters, total;
     int64_t max_tiles;
 };
 
@@ -871,7 +871,7 @@ KdLayout kd_layout(const sdmm_kdtree* t, int64_t N) {
         return at;
     };
     for (int b = 0; b < 2; ++b) {
-        L.perm[b] = take(sizeof(int32_t) * (size_t)N);
+        L.rec[b] = take(sizeof(float4) * (size_t)N);
         L.seg_off[b] = take(sizeof(int64_t) * (S + 1));
         L.seg_node[b] = take(sizeof(int32_t) * S);
         L.seg_parent[b] = take(sizeof(int64_t) * S);
@@ -886,7 +886,7 @@ KdLayout kd_layout(const sdmm_kdtree* t, int64_t N) {
     L.tile_start = take(sizeof(int64_t) * T);
     L.tile_left = take(sizeof(int32_t) * T);
     L.tile_prefix = take(sizeof(int64_t) * T);
-    L.first_tile = take(sizeof(int32_t) * S);
+    L.seg_tile0 = take(sizeof(int32_t) * (S + 1));
     L.counters = take(sizeof(int32_t) * 4);
     L.total = o;
     return L;
@@ -896,7 +896,7 @@ KdWork kd_work(void* ws, const KdLayout& L) {
     char* b = static_cast<char*>(ws);
     KdWork w{};
     for (int i = 0; i < 2; ++i) {
-        w.perm[i] = reinterpret_cast<int32_t*>(b + L.perm[i]);
+        w.rec[i] = reinterpret_cast<float4*>(b + L.rec[i]);
         w.seg_off[i] = reinterpret_cast<int64_t*>(b + L.seg_off[i]);
         w.seg_node[i] = reinterpret_cast<int32_t*>(b + L.seg_node[i]);
         w.seg_parent[i] = reinterpret_cast<int64_t*>(b + L.seg_parent[i]);
@@ -911,7 +911,7 @@ KdWork kd_work(void* ws, const KdLayout& L) {
     w.tile_start = reinterpret_cast<int64_t*>(b + L.tile_start);
     w.tile_left = reinterpret_cast<int32_t*>(b + L.tile_left);
     w.tile_prefix = reinterpret_cast<int64_t*>(b + L.tile_prefix);
-    w.first_tile = reinterpret_cast<int32_t*>(b + L.first_tile);
+    w.seg_tile0 = reinterpret_cast<int32_t*>(b + L.seg_tile0);
     w.counters = reinterpret_cast<int32_t*>(b + L.counters);
     w.max_tiles = L.max_tiles;
     return w;
@@ -993,13 +993,16 @@ static sdmm_status kd_run(sdmm_kdtree* t, int binning, int64_t c, const sdmm_sam
     const KdWork w = kd_work(ws, L);
     const int64_t N = in->N;
     const int32_t S0 = binning ? 1 : t->n_leaves;
-    SDMM_CUDA(launch_kd_prepare(stream, w, binning, t->axis, t->leaf, t->n_nodes, S0, in->offsets, N), "kd_prepare");
-    int32_t *perm = nullptr, S = 0;
+    SDMM_CUDA(launch_kd_prepare(stream, w, binning, t->axis, t->leaf, t->n_nodes, S0, in->offsets, N, in->px, in->py,
+                                in->pz),
+              "kd_prepare");
+    const float4* rec = nullptr;
+    int32_t S = 0;
     int64_t *seg_off = nullptr, *seg_parent = nullptr;
     int overflow = 0;
     int32_t n_nodes = t->n_nodes, n_leaves = t->n_leaves;
     SDMM_CUDA(kd_rounds(stream, w, binning, c, t->axis, t->split, t->left, t->leaf, &n_nodes, &n_leaves,
-                        t->cap_nodes, t->cap_leaves, S0, N, in->px, in->py, in->pz, &perm, &seg_off, &seg_parent,
+                        t->cap_nodes, t->cap_leaves, S0, N, &rec, &seg_off, &seg_parent,
                         &S, &overflow),
               "kd_rounds");
     t->n_nodes = n_nodes;
@@ -1010,7 +1013,7 @@ static sdmm_status kd_run(sdmm_kdtree* t, int binning, int64_t c, const sdmm_sam
     if (binning && S != t->n_leaves)
         return fail(SDMM_ERR_INVALID_ARG, "binning reached %d of %d leaves (tree deeper than 64 levels?)", S,
                     t->n_leaves);
-    SDMM_CUDA(launch_kd_gather(stream, N, perm, desc_of(in), desc_of(out)), "kd_gather");
+    SDMM_CUDA(launch_kd_gather(stream, N, rec, desc_of(in), desc_of(out)), "kd_gather");
     SDMM_CUDA(cudaMemcpyAsync(out->offsets, seg_off, sizeof(int64_t) * ((size_t)S + 1), cudaMemcpyDeviceToDevice,
                               stream),
               "kd_offsets");

@@ -25,7 +25,9 @@
 
 namespace sdmm {
 
-constexpr int kKdTile = 1024;
+constexpr int kKdTile = 1024;                 // samples per tile
+constexpr int kKdThreads = 256;               // threads per tile CTA: 4 samples each
+constexpr int kKdPer = kKdTile / kKdThreads;
 constexpr double kTwo32 = 4294967296.0;
 
 // ---------------------------------------------------------------------------
@@ -79,7 +81,7 @@ __global__ void k_kd_lookup(const int32_t* __restrict__ axis, const double* __re
 // ---------------------------------------------------------------------------
 // Rounds of segment partitions.  State of a round (workspace, see api.cu):
 //   seg_off[S+1] (int64), seg_node[S], seg_parent[S]    the current segments
-//   perm[N]                                             sample order (int32)
+//   rec[N]                                              (x, y, z, sample index): sample order
 // Per segment: flag (split or not), axis, plane, left count; per tile: its
 // segment, first sample, left count and its exclusive prefix in the segment.
 struct KdRound {
@@ -93,6 +95,7 @@ struct KdRound {
     int32_t* seg_new;            // new index of the segment (its left part)
     unsigned long long* seg_sum; // [S][6] fixed-point sums (refinement only)
     unsigned long long* seg_left;
+    int32_t* seg_tile0;          // [S+1] first tile of each segment (exclusive prefix of tile counts)
     int32_t* tile_seg;
     int64_t* tile_start;
     int32_t* tile_left;
@@ -101,7 +104,8 @@ struct KdRound {
 };
 
 // Tiles: ceil(M_s / 1024) per segment (empty segments get none), in segment
-// order.  One CTA of 1024 threads, int64 block scan over the segments.
+// order.  One CTA of 1024 threads: the exclusive prefix of the segments' tile
+// counts (k_kd_tile_fill then maps tiles to segments in parallel).
 __global__ void __launch_bounds__(1024) k_kd_tiles(KdRound k, int64_t max_tiles) {
     __shared__ int64_t s_warp[32];
     __shared__ int64_t s_carry;
@@ -129,16 +133,30 @@ __global__ void __launch_bounds__(1024) k_kd_tiles(KdRound k, int64_t max_tiles)
         }
         __syncthreads();
         const int64_t first = s_carry + v - nt + (warp > 0 ? s_warp[warp - 1] : 0);
-        if (s < k.S)
-            for (int64_t j = 0; j < nt && first + j < max_tiles; ++j) {
-                k.tile_seg[first + j] = s;
-                k.tile_start[first + j] = k.seg_off[s] + j * kKdTile;
-            }
+        if (s < k.S) k.seg_tile0[s] = (int32_t)min(first, max_tiles);
         __syncthreads();
         if (tid == 1023) s_carry = first + nt;
         __syncthreads();
     }
-    if (tid == 0) k.counters[0] = (int32_t)min(s_carry, max_tiles);
+    if (tid == 0) {
+        k.seg_tile0[k.S] = (int32_t)min(s_carry, max_tiles);
+        k.counters[0] = (int32_t)min(s_carry, max_tiles);
+    }
+}
+
+// segment and first sample of every tile: the last segment whose first tile
+// is <= t (empty segments share their successor's first tile)
+__global__ void k_kd_tile_fill(KdRound k) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= k.counters[0]) return;
+    int lo = 0, hi = k.S;                        // seg_tile0[lo] <= t < seg_tile0[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (k.seg_tile0[mid] <= t) lo = mid;
+        else hi = mid;
+    }
+    k.tile_seg[t] = lo;
+    k.tile_start[t] = k.seg_off[lo] + (int64_t)(t - k.seg_tile0[lo]) * kKdTile;
 }
 
 __device__ __forceinline__ void fixed_point(float x, unsigned long long& q, unsigned long long& q2) {
@@ -148,22 +166,29 @@ __device__ __forceinline__ void fixed_point(float x, unsigned long long& q, unsi
 }
 
 // fixed-point sums of the samples of segments holding more than c of them
-__global__ void __launch_bounds__(kKdTile) k_kd_stats(KdRound k, const int32_t* __restrict__ perm,
-                                                     const float* __restrict__ px, const float* __restrict__ py,
-                                                     const float* __restrict__ pz, int64_t c) {
-    __shared__ unsigned long long s_red[32][6];
+__global__ void __launch_bounds__(kKdThreads) k_kd_stats(KdRound k, const float4* __restrict__ rec, int64_t c) {
+    __shared__ unsigned long long s_red[kKdThreads / 32][6];
     const int t = blockIdx.x;
     if (t >= k.counters[0]) return;
     const int s = k.tile_seg[t];
-    const int64_t M = k.seg_off[s + 1] - k.seg_off[s];
+    const int64_t end = k.seg_off[s + 1];
+    const int64_t M = end - k.seg_off[s];
     if (M <= c) return;                                        // (uniform per CTA)
-    const int64_t i = k.tile_start[t] + threadIdx.x;
+    const int64_t i0 = k.tile_start[t] + threadIdx.x;
     unsigned long long v[6] = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull};
-    if (i < k.seg_off[s + 1]) {
-        const int32_t j = perm[i];
-        fixed_point(px[j], v[0], v[3]);
-        fixed_point(py[j], v[1], v[4]);
-        fixed_point(pz[j], v[2], v[5]);
+#pragma unroll
+    for (int q = 0; q < kKdPer; ++q) {
+        const int64_t i = i0 + q * kKdThreads;
+        if (i < end) {
+            const float4 p = rec[i];
+            unsigned long long a, b;
+            fixed_point(p.x, a, b);
+            v[0] += a, v[3] += b;
+            fixed_point(p.y, a, b);
+            v[1] += a, v[4] += b;
+            fixed_point(p.z, a, b);
+            v[2] += a, v[5] += b;
+        }
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -175,7 +200,7 @@ __global__ void __launch_bounds__(kKdTile) k_kd_stats(KdRound k, const int32_t* 
     __syncthreads();
     if (threadIdx.x < 6) {
         unsigned long long a = 0ull;
-        for (int w = 0; w < kKdTile / 32; ++w) a += s_red[w][threadIdx.x];
+        for (int w = 0; w < kKdThreads / 32; ++w) a += s_red[w][threadIdx.x];
         atomicAdd(k.seg_sum + (int64_t)s * 6 + threadIdx.x, a);
     }
 }
@@ -213,28 +238,34 @@ __global__ void k_kd_plan(KdRound k, const int32_t* __restrict__ tree_axis, cons
 }
 
 // per tile: samples strictly left of the plane (x[axis] < split)
-__global__ void __launch_bounds__(kKdTile) k_kd_count(KdRound k, const int32_t* __restrict__ perm,
-                                                     const float* __restrict__ px, const float* __restrict__ py,
-                                                     const float* __restrict__ pz) {
-    __shared__ int s_red[32];
+__global__ void __launch_bounds__(kKdThreads) k_kd_count(KdRound k, const float4* __restrict__ rec) {
+    __shared__ int s_red[kKdThreads / 32];
     const int t = blockIdx.x;
     if (t >= k.counters[0]) return;
     const int s = k.tile_seg[t];
     const int a = k.seg_axis[s];
-    const int64_t i = k.tile_start[t] + threadIdx.x;
+    const int64_t end = k.seg_off[s + 1];
+    const double pl = k.seg_split[s];
+    const int64_t i0 = k.tile_start[t] + threadIdx.x;
     int f = 0;
-    if (a >= 0 && i < k.seg_off[s + 1]) {
-        const int32_t j = perm[i];
-        const float x = a == 0 ? px[j] : (a == 1 ? py[j] : pz[j]);
-        f = (double)x < k.seg_split[s] ? 1 : 0;
+#pragma unroll
+    for (int q = 0; q < kKdPer; ++q) {
+        const int64_t i = i0 + q * kKdThreads;
+        if (a >= 0 && i < end) {
+            const float4 p = rec[i];
+            const float x = a == 0 ? p.x : (a == 1 ? p.y : p.z);
+            f += (double)x < pl ? 1 : 0;
+        }
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int n = __popc(__ballot_sync(0xffffffffu, f));
+    int n = f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
     if (lane == 0) s_red[warp] = n;
     __syncthreads();
     if (threadIdx.x == 0) {
         int tot = 0;
-        for (int w = 0; w < kKdTile / 32; ++w) tot += s_red[w];
+        for (int w = 0; w < kKdThreads / 32; ++w) tot += s_red[w];
         k.tile_left[t] = tot;
         if (a >= 0) atomicAdd(k.seg_left + s, (unsigned long long)tot);
     }
@@ -318,54 +349,59 @@ __global__ void __launch_bounds__(1024) k_kd_scan(KdRound k, int binning) {
 }
 
 // Stable partition: within a split segment, left samples first (in order),
-// then the right ones (in order); other segments are copied.
-__global__ void __launch_bounds__(kKdTile) k_kd_scatter(KdRound k, const int32_t* __restrict__ perm_in,
-                                                       int32_t* __restrict__ perm_out,
-                                                       const float* __restrict__ px, const float* __restrict__ py,
-                                                       const float* __restrict__ pz, const int32_t* __restrict__ first_tile) {
-    __shared__ int s_warp[32];
+// then the right ones (in order); other segments are copied.  Thread j of the
+// CTA holds samples j, j + 256, j + 512, j + 768 of the tile.
+__global__ void __launch_bounds__(kKdThreads) k_kd_scatter(KdRound k, const float4* __restrict__ rec_in,
+                                                         float4* __restrict__ rec_out) {
+    constexpr int W = kKdThreads / 32;
+    __shared__ int s_cnt[kKdPer][W];
     const int t = blockIdx.x;
     if (t >= k.counters[0]) return;
     const int s = k.tile_seg[t];
     const int64_t o0 = k.seg_off[s], o1 = k.seg_off[s + 1];
-    const int64_t i = k.tile_start[t] + threadIdx.x;
-    const bool in = i < o1;
-    const int32_t j = in ? perm_in[i] : 0;
+    const int64_t i0 = k.tile_start[t] + threadIdx.x;
+    float4 p[kKdPer];
+#pragma unroll
+    for (int q = 0; q < kKdPer; ++q) {
+        const int64_t i = i0 + q * kKdThreads;
+        p[q] = i < o1 ? rec_in[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
     if (!k.seg_flag[s]) {
-        if (in) perm_out[i] = j;
+#pragma unroll
+        for (int q = 0; q < kKdPer; ++q)
+            if (i0 + q * kKdThreads < o1) rec_out[i0 + q * kKdThreads] = p[q];
         return;                                               // (uniform per CTA)
     }
     const int a = k.seg_axis[s];
-    int f = 0;
-    if (in) {
-        const float x = a == 0 ? px[j] : (a == 1 ? py[j] : pz[j]);
-        f = (double)x < k.seg_split[s] ? 1 : 0;
-    }
+    const double pl = k.seg_split[s];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const unsigned bal = __ballot_sync(0xffffffffu, f);
-    const int rank_w = __popc(bal & ((1u << lane) - 1u));
-    if (lane == 0) s_warp[warp] = __popc(bal);
-    __syncthreads();
-    int before = 0;
-    for (int w = 0; w < warp; ++w) before += s_warp[w];
-    const int lrank = before + rank_w;                        // left samples before i in the tile
-    const int64_t lpre = k.tile_prefix[t] - k.tile_prefix[first_tile[s]];   // left samples of earlier tiles
-    const int64_t L = (int64_t)k.seg_left[s];
-    const int64_t pos_in_seg = i - o0;
-    if (in) {
-        int64_t dst;
-        if (f) dst = o0 + lpre + lrank;
-        else dst = o0 + L + (pos_in_seg - (lpre + lrank));
-        perm_out[dst] = j;
+    int f[kKdPer], rank_w[kKdPer];
+#pragma unroll
+    for (int q = 0; q < kKdPer; ++q) {
+        const bool in = i0 + q * kKdThreads < o1;
+        const float x = a == 0 ? p[q].x : (a == 1 ? p[q].y : p[q].z);
+        f[q] = (in && (double)x < pl) ? 1 : 0;
+        const unsigned bal = __ballot_sync(0xffffffffu, f[q]);
+        rank_w[q] = __popc(bal & ((1u << lane) - 1u));
+        if (lane == 0) s_cnt[q][warp] = __popc(bal);
     }
-}
-
-// first tile of every segment (for the prefix offsets above); -1 if empty
-__global__ void k_kd_first_tile(KdRound k, int32_t* first_tile) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= k.counters[0]) return;
-    const int s = k.tile_seg[t];
-    if (t == 0 || k.tile_seg[t - 1] != s) first_tile[s] = t;
+    __syncthreads();
+    const int64_t lpre = k.tile_prefix[t] - k.tile_prefix[k.seg_tile0[s]];   // left samples of earlier tiles
+    const int64_t L = (int64_t)k.seg_left[s];
+    int before = 0;                                // left samples of the tile before (q, warp)
+#pragma unroll
+    for (int q = 0; q < kKdPer; ++q) {
+        int wb = 0;
+        for (int w = 0; w < W; ++w) wb += w < warp ? s_cnt[q][w] : 0;
+        const int64_t i = i0 + q * kKdThreads;
+        if (i < o1) {
+            const int lrank = before + wb + rank_w[q];
+            const int64_t pos_in_seg = i - o0;
+            const int64_t dst = f[q] ? o0 + lpre + lrank : o0 + L + (pos_in_seg - (lpre + lrank));
+            rec_out[dst] = p[q];
+        }
+        for (int w = 0; w < W; ++w) before += s_cnt[q][w];
+    }
 }
 
 // New segments; refinement also writes the tree (two new leaf nodes per
@@ -419,16 +455,19 @@ __global__ void k_kd_leaf_nodes(const int32_t* __restrict__ axis, const int32_t*
     if (n < n_nodes && axis[n] < 0) seg_node[leaf[n]] = n;
 }
 
-__global__ void k_kd_iota(int32_t* perm, int64_t N, int64_t* parent, int32_t S) {
+// records (x, y, z, i): the positions travel with the sample index, so every
+// round reads them in order
+__global__ void k_kd_init(float4* rec, int64_t N, const float* __restrict__ px, const float* __restrict__ py,
+                          const float* __restrict__ pz, int64_t* parent, int32_t S) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < N) perm[i] = (int32_t)i;
+    if (i < N) rec[i] = make_float4(px[i], py[i], pz[i], __int_as_float((int32_t)i));
     if (parent != nullptr && i < S) parent[i] = i;
 }
 
-__global__ void k_kd_gather(int64_t N, const int32_t* __restrict__ perm, BatchDesc in, BatchDesc out) {
+__global__ void k_kd_gather(int64_t N, const float4* __restrict__ rec, BatchDesc in, BatchDesc out) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    const int32_t j = perm[i];
+    const int32_t j = __float_as_int(rec[i].w);
 #pragma unroll
     for (int q = 0; q < 7; ++q) const_cast<float*>(out.p[q])[i] = in.p[q][j];
 }
@@ -492,7 +531,7 @@ cudaError_t launch_gather_state(cudaStream_t s, int K, int64_t R_out, const int6
 cudaError_t kd_rounds(cudaStream_t st, const KdWork& w, int binning, int64_t c, int32_t* tree_axis,
                       double* tree_split, int32_t* tree_left, int32_t* tree_leaf, int32_t* n_nodes,
                       int32_t* n_leaves, int32_t cap_nodes, int32_t cap_leaves, int32_t S0, int64_t N,
-                      const float* px, const float* py, const float* pz, int32_t** perm_final,
+                      const float4** rec_final,
                       int64_t** seg_off_final, int64_t** seg_parent_final, int32_t* S_final, int* overflow) {
     int32_t S = S0;
     int cur = 0;
@@ -509,6 +548,7 @@ cudaError_t kd_rounds(cudaStream_t st, const KdWork& w, int binning, int64_t c, 
         k.seg_new = w.seg_new;
         k.seg_sum = w.seg_sum;
         k.seg_left = w.seg_left;
+        k.seg_tile0 = w.seg_tile0;
         k.tile_seg = w.tile_seg;
         k.tile_start = w.tile_start;
         k.tile_left = w.tile_left;
@@ -517,15 +557,15 @@ cudaError_t kd_rounds(cudaStream_t st, const KdWork& w, int binning, int64_t c, 
         const int64_t max_tiles = w.max_tiles;
         cudaError_t e;
         k_kd_tiles<<<1, 1024, 0, st>>>(k, max_tiles);
+        k_kd_tile_fill<<<(unsigned)((max_tiles + 255) / 256), 256, 0, st>>>(k);
         if (!binning) {
             if ((e = cudaMemsetAsync(w.seg_sum, 0, sizeof(unsigned long long) * 6 * (size_t)S, st)) != cudaSuccess)
                 return e;
-            k_kd_stats<<<(unsigned)max_tiles, kKdTile, 0, st>>>(k, w.perm[cur & 1], px, py, pz, c);
+            k_kd_stats<<<(unsigned)max_tiles, kKdThreads, 0, st>>>(k, w.rec[cur & 1], c);
         }
         k_kd_plan<<<(S + 255) / 256, 256, 0, st>>>(k, tree_axis, tree_split, binning ? -1 : c);
-        k_kd_count<<<(unsigned)max_tiles, kKdTile, 0, st>>>(k, w.perm[cur & 1], px, py, pz);
+        k_kd_count<<<(unsigned)max_tiles, kKdThreads, 0, st>>>(k, w.rec[cur & 1]);
         k_kd_scan<<<1, 1024, 0, st>>>(k, binning);
-        k_kd_first_tile<<<(unsigned)((max_tiles + 255) / 256), 256, 0, st>>>(k, w.first_tile);
         int32_t splits = 0;
         if ((e = cudaMemcpyAsync(&splits, w.counters + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
             return e;
@@ -536,8 +576,7 @@ cudaError_t kd_rounds(cudaStream_t st, const KdWork& w, int binning, int64_t c, 
             *overflow = 1;
             return cudaSuccess;
         }
-        k_kd_scatter<<<(unsigned)max_tiles, kKdTile, 0, st>>>(k, w.perm[cur & 1], w.perm[(cur + 1) & 1], px, py, pz,
-                                                             w.first_tile);
+        k_kd_scatter<<<(unsigned)max_tiles, kKdThreads, 0, st>>>(k, w.rec[cur & 1], w.rec[(cur + 1) & 1]);
         k_kd_segments<<<(S + 255) / 256, 256, 0, st>>>(k, binning, tree_axis, tree_split, tree_left, tree_leaf,
                                                       *n_nodes, w.seg_off[cur ^ 1], w.seg_node[cur ^ 1],
                                                       w.seg_parent[cur ^ 1], N);
@@ -549,7 +588,7 @@ cudaError_t kd_rounds(cudaStream_t st, const KdWork& w, int binning, int64_t c, 
         S += splits;
         cur ^= 1;
     }
-    *perm_final = w.perm[cur & 1];
+    *rec_final = w.rec[cur & 1];
     *seg_off_final = w.seg_off[cur];
     *seg_parent_final = w.seg_parent[cur];
     *S_final = S;
@@ -558,8 +597,9 @@ cudaError_t kd_rounds(cudaStream_t st, const KdWork& w, int binning, int64_t c, 
 
 cudaError_t launch_kd_prepare(cudaStream_t st, const KdWork& w, int binning, const int32_t* tree_axis,
                               const int32_t* tree_leaf, int32_t n_nodes, int32_t S0, const int64_t* offsets_in,
-                              int64_t N) {
-    k_kd_iota<<<(unsigned)((std::max<int64_t>(N, S0) + 255) / 256), 256, 0, st>>>(w.perm[0], N, w.seg_parent[0], S0);
+                              int64_t N, const float* px, const float* py, const float* pz) {
+    k_kd_init<<<(unsigned)((std::max<int64_t>(N, S0) + 255) / 256), 256, 0, st>>>(w.rec[0], N, px, py, pz,
+                                                                                 w.seg_parent[0], S0);
     if (binning) {
         // one segment: the root with every sample
         const int64_t off[2] = {0, N};
@@ -576,10 +616,10 @@ cudaError_t launch_kd_prepare(cudaStream_t st, const KdWork& w, int binning, con
     return cudaGetLastError();
 }
 
-cudaError_t launch_kd_gather(cudaStream_t st, int64_t N, const int32_t* perm, const BatchDesc& in,
+cudaError_t launch_kd_gather(cudaStream_t st, int64_t N, const float4* rec, const BatchDesc& in,
                              const BatchDesc& out) {
     if (N == 0) return cudaSuccess;
-    k_kd_gather<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(N, perm, in, out);
+    k_kd_gather<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(N, rec, in, out);
     return cudaGetLastError();
 }
 

@@ -62,7 +62,7 @@ cudaError_t launch_tc_selftest(cudaStream_t s, int kind, int N, int Kd, const fl
 
 // ---- spatial kD-tree (kdtree.cu)
 struct KdWork {
-    int32_t* perm[2];            // sample order, ping-pong [N]
+    float4* rec[2];              // (x, y, z, sample index as int bits), ping-pong [N]
     int64_t* seg_off[2];         // segment offsets [cap_leaves + 1]
     int32_t* seg_node[2];        // tree node of each segment
     int64_t* seg_parent[2];      // leaf of the call's input each segment descends from
@@ -76,7 +76,7 @@ struct KdWork {
     int64_t* tile_start;
     int32_t* tile_left;
     int64_t* tile_prefix;
-    int32_t* first_tile;         // [cap_leaves]
+    int32_t* seg_tile0;          // [cap_leaves + 2] first tile of each segment
     int32_t* counters;           // [0] tiles, [1] splits
     int64_t max_tiles;
 };
@@ -86,13 +86,13 @@ cudaError_t launch_kd_lookup(cudaStream_t s, const int32_t* axis, const double* 
                              const float* pz, int32_t* out);
 cudaError_t launch_kd_prepare(cudaStream_t st, const KdWork& w, int binning, const int32_t* tree_axis,
                               const int32_t* tree_leaf, int32_t n_nodes, int32_t S0, const int64_t* offsets_in,
-                              int64_t N);
+                              int64_t N, const float* px, const float* py, const float* pz);
 cudaError_t kd_rounds(cudaStream_t st, const KdWork& w, int binning, int64_t c, int32_t* tree_axis,
                       double* tree_split, int32_t* tree_left, int32_t* tree_leaf, int32_t* n_nodes,
                       int32_t* n_leaves, int32_t cap_nodes, int32_t cap_leaves, int32_t S0, int64_t N,
-                      const float* px, const float* py, const float* pz, int32_t** perm_final,
+                      const float4** rec_final,
                       int64_t** seg_off_final, int64_t** seg_parent_final, int32_t* S_final, int* overflow);
-cudaError_t launch_kd_gather(cudaStream_t st, int64_t N, const int32_t* perm, const BatchDesc& in,
+cudaError_t launch_kd_gather(cudaStream_t st, int64_t N, const float4* rec, const BatchDesc& in,
                              const BatchDesc& out);
 cudaError_t launch_gather_state(cudaStream_t s, int K, int64_t R_out, const int64_t* src, const sdmm_state& in,
                                 const sdmm_state& out);
