@@ -297,7 +297,7 @@ __global__ void __launch_bounds__(256, 3)
                     vv = rn < kPiF ? 1.f : 0.f;
                     float sr, cr;
                     sincosf(rn, &sr, &cr);
-                    const float sc = rn < 1e-3f ? 1.f - rn * rn * (1.f / 6.f) : sr / rn;
+                    const float sc = rn < 1e-3f ? 1.f - rn * rn * (1.f / 6.f) : __fdividef(sr, rn);
                     const float c0 = n0 * sc, c1 = n1 * sc;
                     s0 = c0 * P[3] + c1 * P[6] + cr * P[9];
                     s1 = c0 * P[4] + c1 * P[7] + cr * P[10];
@@ -314,13 +314,11 @@ __global__ void __launch_bounds__(256, 3)
             const float v = P[6] * w0 + P[7] * wv1 + P[8] * wv2;
             const float cz = P[9] * w0 + P[10] * wv1 + P[11] * wv2;
             const float s2v = u * u + v * v;
-            const float rs = rsqrtf(s2v);
-            const float th = atan2_pos(s2v * rs, cz);
-            const bool off_centre = s2v > 0.f;
-            const float gg = off_centre ? th * rs : 1.f;
+            const bool cut = s2v == 0.f && cz < 0.f;          // antipode: outside the chart
+            const float gg = cut ? 1.f : g_of_cos(cz, rsqrtf(s2v));
             const float nu0 = gg * u, nu1 = gg * v;
             float pk = 0.f;
-            if (!(!off_centre && cz < 0.f) && th < kPiF && k < K) {
+            if (!cut && k < K) {
                 if (ea > 0.f) pk += ea * __expf(pair_logpdf(pr[0], nu0, nu1));
                 if (eb > 0.f) pk += eb * __expf(pair_logpdf(pr[1], nu0, nu1));
                 pk *= gg;

@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(256)
                     vv = rn < kPiF ? 1.f : 0.f;
                     float sr, cr;
                     sincosf(rn, &sr, &cr);
-                    const float sc = rn < 1e-3f ? 1.f - rn * rn * (1.f / 6.f) : sr / rn;
+                    const float sc = rn < 1e-3f ? 1.f - rn * rn * (1.f / 6.f) : __fdividef(sr, rn);
                     const float c0 = n0 * sc, c1 = n1 * sc;
                     s0 = c0 * P[3] + c1 * P[6] + cr * P[9];
                     s1 = c0 * P[4] + c1 * P[7] + cr * P[10];
@@ -188,15 +188,13 @@ __global__ void __launch_bounds__(256)
             const float v = P[6] * w0 + P[7] * w1 + P[8] * w2;
             const float cz = P[9] * w0 + P[10] * w1 + P[11] * w2;
             const float s2v = u * u + v * v;
-            const float rs = rsqrtf(s2v);
-            const float th = atan2_pos(s2v * rs, cz);
-            const bool off_centre = s2v > 0.f;
-            const float gg = off_centre ? th * rs : 1.f;      // theta / sin(theta) = 1/sinc
+            const bool cut = s2v == 0.f && cz < 0.f;          // antipode: outside the chart
+            const float gg = cut ? 1.f : g_of_cos(cz, rsqrtf(s2v));   // theta / sin(theta) = 1/sinc
             const float d0 = gg * u - m0, d1 = gg * v - m1;
             const float y0 = P[27] * d0;
             const float y1 = P[28] * d0 + P[29] * d1;
             float pk_ = cpi * __expf(P[31] - 0.5f * (y0 * y0 + y1 * y1)) * gg;
-            if ((!off_centre && cz < 0.f) || k >= K) pk_ = 0.f;
+            if (cut || k >= K) pk_ = 0.f;
             float p = pk_;
 #pragma unroll
             for (int o = KP / 2; o > 0; o >>= 1) p += __shfl_xor_sync(FULL, p, o);
