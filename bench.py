@@ -365,10 +365,17 @@ def run_gpu(args):
             times.append((t1 - t0, t2 - t1))
         tb = float(np.median([a for a, _ in times])) * 1e3
         tr = float(np.median([b for _, b in times])) * 1e3
+        # binning moves at least every sample's 7 streams once: 28 B read + 28 B written
+        bin_gbs = 56.0 * N / (tb * 1e-3) / 1e9
         kdres = {"samples": N, "bin_ms": tb, "refine_ms": tr, "leaves_after": tree.n_leaves,
                  "nodes_after": tree.n_nodes, "c": 16000,
                  "bin_samples_per_s": N / (tb * 1e-3), "refine_samples_per_s": N / (tr * 1e-3),
-                 "note": "host wall time of the synchronous calls (one 4-byte read-back per tree level)"}
+                 "bin_roofline": {"bound": "hbm", "achieved": bin_gbs, "peak": peaks.get("hbm_gbs", 6800.0),
+                                  "unit": "GB/s", "frac": bin_gbs / peaks.get("hbm_gbs", 6800.0),
+                                  "bytes_per_sample": 56.0},
+                 "note": "host wall time of the synchronous calls (binning: leaf lookup, stable radix sort by "
+                         "leaf, one gather; refinement: rounds of stable partitions, one 4-byte read-back per "
+                         "tree level)"}
         del tree, kb, kr, kp
 
     # ---- end to end through the public API with host buffers

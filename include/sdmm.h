@@ -557,8 +557,8 @@ sdmm_status sdmm_kdtree_workspace_size(const sdmm_kdtree *t, int64_t N, size_t *
 /* Binning (Sec. 4.2: each leaf collects the vertices located within it): the
    N samples of `in` (any order; in->offsets and in->R are ignored) sorted by
    leaf into `out`, stably (original order within a leaf), with
-   out->offsets[n_leaves + 1].  Synchronous on `stream` (one 4-byte read-back
-   per tree level). */
+   out->offsets[n_leaves + 1]: every sample's leaf by descent, a stable radix
+   sort by leaf, one gather of the seven streams.  Synchronous on `stream`. */
 sdmm_status sdmm_kdtree_bin(const sdmm_kdtree *t, const sdmm_samples *in,
                             sdmm_sample_buffers *out, void *workspace,
                             size_t ws_bytes, sdmm_stream stream);

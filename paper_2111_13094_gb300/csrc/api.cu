@@ -855,7 +855,7 @@ namespace {
 
 struct KdLayout {
     size_t rec[2], seg_off[2], seg_node[2], seg_parent[2], seg_axis, seg_split, seg_flag, seg_new, seg_sum,
-        seg_left, tile_seg, tile_start, tile_left, tile_prefix, seg_tile0, counters, total;
+        seg_left, tile_seg, tile_start, tile_left, tile_prefix, seg_tile0, counters, rx_hist, rx_bsum, total;
     int64_t max_tiles;
 };
 
@@ -888,6 +888,8 @@ KdLayout kd_layout(const sdmm_kdtree* t, int64_t N) {
     L.tile_prefix = take(sizeof(int64_t) * T);
     L.seg_tile0 = take(sizeof(int32_t) * (S + 1));
     L.counters = take(sizeof(int32_t) * 4);
+    L.rx_hist = take(sizeof(uint32_t) * 256 * (size_t)rx_tiles(N));
+    L.rx_bsum = take(sizeof(uint32_t) * ((size_t)rx_scan_blocks(N) + 1));
     L.total = o;
     return L;
 }
@@ -913,6 +915,8 @@ KdWork kd_work(void* ws, const KdLayout& L) {
     w.tile_prefix = reinterpret_cast<int64_t*>(b + L.tile_prefix);
     w.seg_tile0 = reinterpret_cast<int32_t*>(b + L.seg_tile0);
     w.counters = reinterpret_cast<int32_t*>(b + L.counters);
+    w.rx_hist = reinterpret_cast<uint32_t*>(b + L.rx_hist);
+    w.rx_bsum = reinterpret_cast<uint32_t*>(b + L.rx_bsum);
     w.max_tiles = L.max_tiles;
     return w;
 }
@@ -992,8 +996,18 @@ static sdmm_status kd_run(sdmm_kdtree* t, int binning, int64_t c, const sdmm_sam
     if (ws_bytes < L.total) return fail(SDMM_ERR_WORKSPACE, "workspace %zu bytes < required %zu", ws_bytes, L.total);
     const KdWork w = kd_work(ws, L);
     const int64_t N = in->N;
-    const int32_t S0 = binning ? 1 : t->n_leaves;
-    SDMM_CUDA(launch_kd_prepare(stream, w, binning, t->axis, t->leaf, t->n_nodes, S0, in->offsets, N, in->px, in->py,
+    if (binning) {
+        // every sample's leaf, a stable radix sort by leaf, the gather and the offsets
+        SDMM_CUDA(launch_kd_bin(stream, w, t->axis, t->split, t->left, t->leaf, t->n_nodes, t->n_leaves, N, in->px,
+                                in->py, in->pz, desc_of(in), desc_of(out), out->offsets),
+                  "kd_bin");
+        SDMM_CUDA(cudaStreamSynchronize(stream), "kd_bin");
+        out->R = t->n_leaves;
+        out->N = N;
+        return SDMM_OK;
+    }
+    const int32_t S0 = t->n_leaves;
+    SDMM_CUDA(launch_kd_prepare(stream, w, t->axis, t->leaf, t->n_nodes, S0, in->offsets, N, in->px, in->py,
                                 in->pz),
               "kd_prepare");
     const float4* rec = nullptr;
@@ -1001,7 +1015,7 @@ static sdmm_status kd_run(sdmm_kdtree* t, int binning, int64_t c, const sdmm_sam
     int64_t *seg_off = nullptr, *seg_parent = nullptr;
     int overflow = 0;
     int32_t n_nodes = t->n_nodes, n_leaves = t->n_leaves;
-    SDMM_CUDA(kd_rounds(stream, w, binning, c, t->axis, t->split, t->left, t->leaf, &n_nodes, &n_leaves,
+    SDMM_CUDA(kd_rounds(stream, w, c, t->axis, t->split, t->left, t->leaf, &n_nodes, &n_leaves,
                         t->cap_nodes, t->cap_leaves, S0, N, &rec, &seg_off, &seg_parent,
                         &S, &overflow),
               "kd_rounds");
@@ -1010,9 +1024,6 @@ static sdmm_status kd_run(sdmm_kdtree* t, int binning, int64_t c, const sdmm_sam
     if (overflow)
         return fail(SDMM_ERR_WORKSPACE, "kD-tree capacities (%d nodes, %d leaves) too small", t->cap_nodes,
                     t->cap_leaves);
-    if (binning && S != t->n_leaves)
-        return fail(SDMM_ERR_INVALID_ARG, "binning reached %d of %d leaves (tree deeper than 64 levels?)", S,
-                    t->n_leaves);
     SDMM_CUDA(launch_kd_gather(stream, N, rec, desc_of(in), desc_of(out)), "kd_gather");
     SDMM_CUDA(cudaMemcpyAsync(out->offsets, seg_off, sizeof(int64_t) * ((size_t)S + 1), cudaMemcpyDeviceToDevice,
                               stream),

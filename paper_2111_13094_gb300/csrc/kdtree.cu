@@ -3,7 +3,9 @@
 //
 //  k_kd_grid        regular pre-subdivision, heap-numbered nodes
 //  k_kd_lookup      leaf of each point by descent
-//  binning and refinement, both as rounds of stable segment partitions:
+//  binning (k_bin_keys, k_rx_*, k_bin_offsets, k_gather_idx): every sample's
+//  leaf, a stable radix sort by leaf, offsets, one gather
+//  refinement, as rounds of stable segment partitions:
 //    k_kd_tiles     tiles of 1,024 samples, none spanning two segments
 //    k_kd_stats     fixed-point position sums of the segments to split
 //    k_kd_plan      split plane of each segment (tree node, or mean along the
@@ -12,7 +14,7 @@
 //    k_kd_scan      which segments split, their new indices, tile prefixes
 //    k_kd_scatter   stable partition of every split segment
 //    k_kd_segments  new segments, new tree nodes, parents of the new leaves
-//  k_kd_gather      the sample streams in the final order
+//  k_kd_gather      the sample streams in the refined order
 //  k_gather_state   mixture states copied from the parent regions
 //
 // Leaves are numbered in tree order (left before right), so a leaf's
@@ -205,20 +207,15 @@ __global__ void __launch_bounds__(kKdThreads) k_kd_stats(KdRound k, const float4
     }
 }
 
-// Split plane of every segment.  Binning (c < 0): the segment's tree node
-// (leaves keep their segment).  Refinement: more than c samples -> the mean
-// along the axis of largest variance (lowest axis on ties), from the sums.
-__global__ void k_kd_plan(KdRound k, const int32_t* __restrict__ tree_axis, const double* __restrict__ tree_split,
-                          int64_t c) {
+// Split plane of every segment holding more than c samples: the mean along
+// the axis of largest variance (lowest axis on ties), from the sums.
+__global__ void k_kd_plan(KdRound k, int64_t c) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= k.S) return;
     const int64_t M = k.seg_off[s + 1] - k.seg_off[s];
     int a = -1;
     double pl = 0.0;
-    if (c < 0) {
-        a = tree_axis[k.seg_node[s]];
-        pl = a >= 0 ? tree_split[k.seg_node[s]] : 0.0;
-    } else if (M > c) {
+    if (M > c) {
         double best = -1.0;
         for (int q = 0; q < 3; ++q) {
             const double S1 = (double)k.seg_sum[(int64_t)s * 6 + q];
@@ -271,10 +268,10 @@ __global__ void __launch_bounds__(kKdThreads) k_kd_count(KdRound k, const float4
     }
 }
 
-// Which segments split (binning: every internal node; refinement: both
-// sides non-empty), their new indices, and the exclusive prefix of each
-// tile's left count within its segment.  One CTA of 1024 threads.
-__global__ void __launch_bounds__(1024) k_kd_scan(KdRound k, int binning) {
+// Which segments split (both sides non-empty), their new indices, and the
+// exclusive prefix of each tile's left count within its segment.  One CTA of
+// 1024 threads.
+__global__ void __launch_bounds__(1024) k_kd_scan(KdRound k) {
     __shared__ int32_t s_warp[32];
     __shared__ int32_t s_carry;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -286,7 +283,7 @@ __global__ void __launch_bounds__(1024) k_kd_scan(KdRound k, int binning) {
         if (s < k.S && k.seg_axis[s] >= 0) {
             const int64_t M = k.seg_off[s + 1] - k.seg_off[s];
             const int64_t L = (int64_t)k.seg_left[s];
-            f = binning ? 1 : (L > 0 && L < M ? 1 : 0);
+            f = (L > 0 && L < M) ? 1 : 0;
         }
         int v = f;
         for (int d = 1; d < 32; d <<= 1) {
@@ -404,9 +401,9 @@ __global__ void __launch_bounds__(kKdThreads) k_kd_scatter(KdRound k, const floa
     }
 }
 
-// New segments; refinement also writes the tree (two new leaf nodes per
-// split, appended from node n_nodes on) and leaf indices of kept leaves.
-__global__ void k_kd_segments(KdRound k, int binning, int32_t* tree_axis, double* tree_split, int32_t* tree_left,
+// New segments and the tree: two new leaf nodes per split, appended from node
+// n_nodes on, and leaf indices of kept leaves.
+__global__ void k_kd_segments(KdRound k, int32_t* tree_axis, double* tree_split, int32_t* tree_left,
                               int32_t* tree_leaf, int32_t n_nodes, int64_t* seg_off_out, int32_t* seg_node_out,
                               int64_t* seg_parent_out, int64_t N) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -417,22 +414,17 @@ __global__ void k_kd_segments(KdRound k, int binning, int32_t* tree_axis, double
     const int64_t par = k.seg_parent[s];
     if (k.seg_flag[s]) {
         const int64_t L = (int64_t)k.seg_left[s];
-        int32_t l;
-        if (binning) {
-            l = tree_left[node];
-        } else {
-            l = n_nodes + 2 * (ns - s);
-            tree_axis[node] = k.seg_axis[s];
-            tree_split[node] = k.seg_split[s];
-            tree_left[node] = l;
-            tree_leaf[node] = -1;
-            tree_axis[l] = -1;
-            tree_axis[l + 1] = -1;
-            tree_split[l] = tree_split[l + 1] = 0.0;
-            tree_left[l] = tree_left[l + 1] = -1;
-            tree_leaf[l] = ns;
-            tree_leaf[l + 1] = ns + 1;
-        }
+        const int32_t l = n_nodes + 2 * (ns - s);
+        tree_axis[node] = k.seg_axis[s];
+        tree_split[node] = k.seg_split[s];
+        tree_left[node] = l;
+        tree_leaf[node] = -1;
+        tree_axis[l] = -1;
+        tree_axis[l + 1] = -1;
+        tree_split[l] = tree_split[l + 1] = 0.0;
+        tree_left[l] = tree_left[l + 1] = -1;
+        tree_leaf[l] = ns;
+        tree_leaf[l + 1] = ns + 1;
         seg_node_out[ns] = l;
         seg_node_out[ns + 1] = l + 1;
         seg_off_out[ns] = off;
@@ -440,7 +432,7 @@ __global__ void k_kd_segments(KdRound k, int binning, int32_t* tree_axis, double
         seg_parent_out[ns] = par;
         seg_parent_out[ns + 1] = par;
     } else {
-        if (!binning) tree_leaf[node] = ns;
+        tree_leaf[node] = ns;
         seg_node_out[ns] = node;
         seg_off_out[ns] = off;
         seg_parent_out[ns] = par;
@@ -526,9 +518,9 @@ cudaError_t launch_gather_state(cudaStream_t s, int K, int64_t R_out, const int6
     return cudaGetLastError();
 }
 
-// One binning or refinement pass over all rounds (host loop; one 4-byte
-// read-back per round).  ws layout in KdWork (api.cu).
-cudaError_t kd_rounds(cudaStream_t st, const KdWork& w, int binning, int64_t c, int32_t* tree_axis,
+// One refinement over all rounds (host loop; one 4-byte read-back per round).
+// ws layout in KdWork (api.cu).
+cudaError_t kd_rounds(cudaStream_t st, const KdWork& w, int64_t c, int32_t* tree_axis,
                       double* tree_split, int32_t* tree_left, int32_t* tree_leaf, int32_t* n_nodes,
                       int32_t* n_leaves, int32_t cap_nodes, int32_t cap_leaves, int32_t S0, int64_t N,
                       const float4** rec_final,
@@ -558,33 +550,29 @@ cudaError_t kd_rounds(cudaStream_t st, const KdWork& w, int binning, int64_t c, 
         cudaError_t e;
         k_kd_tiles<<<1, 1024, 0, st>>>(k, max_tiles);
         k_kd_tile_fill<<<(unsigned)((max_tiles + 255) / 256), 256, 0, st>>>(k);
-        if (!binning) {
-            if ((e = cudaMemsetAsync(w.seg_sum, 0, sizeof(unsigned long long) * 6 * (size_t)S, st)) != cudaSuccess)
-                return e;
-            k_kd_stats<<<(unsigned)max_tiles, kKdThreads, 0, st>>>(k, w.rec[cur & 1], c);
-        }
-        k_kd_plan<<<(S + 255) / 256, 256, 0, st>>>(k, tree_axis, tree_split, binning ? -1 : c);
+        if ((e = cudaMemsetAsync(w.seg_sum, 0, sizeof(unsigned long long) * 6 * (size_t)S, st)) != cudaSuccess)
+            return e;
+        k_kd_stats<<<(unsigned)max_tiles, kKdThreads, 0, st>>>(k, w.rec[cur & 1], c);
+        k_kd_plan<<<(S + 255) / 256, 256, 0, st>>>(k, c);
         k_kd_count<<<(unsigned)max_tiles, kKdThreads, 0, st>>>(k, w.rec[cur & 1]);
-        k_kd_scan<<<1, 1024, 0, st>>>(k, binning);
+        k_kd_scan<<<1, 1024, 0, st>>>(k);
         int32_t splits = 0;
         if ((e = cudaMemcpyAsync(&splits, w.counters + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
             return e;
         if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if (splits == 0) break;
-        if (S + splits > cap_leaves || (!binning && *n_nodes + 2 * splits > cap_nodes)) {
+        if (S + splits > cap_leaves || *n_nodes + 2 * splits > cap_nodes) {
             *overflow = 1;
             return cudaSuccess;
         }
         k_kd_scatter<<<(unsigned)max_tiles, kKdThreads, 0, st>>>(k, w.rec[cur & 1], w.rec[(cur + 1) & 1]);
-        k_kd_segments<<<(S + 255) / 256, 256, 0, st>>>(k, binning, tree_axis, tree_split, tree_left, tree_leaf,
+        k_kd_segments<<<(S + 255) / 256, 256, 0, st>>>(k, tree_axis, tree_split, tree_left, tree_leaf,
                                                       *n_nodes, w.seg_off[cur ^ 1], w.seg_node[cur ^ 1],
                                                       w.seg_parent[cur ^ 1], N);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        if (!binning) {
-            *n_nodes += 2 * splits;
-            *n_leaves += splits;
-        }
+        *n_nodes += 2 * splits;
+        *n_leaves += splits;
         S += splits;
         cur ^= 1;
     }
@@ -595,24 +583,228 @@ cudaError_t kd_rounds(cudaStream_t st, const KdWork& w, int binning, int64_t c, 
     return cudaSuccess;
 }
 
-cudaError_t launch_kd_prepare(cudaStream_t st, const KdWork& w, int binning, const int32_t* tree_axis,
+cudaError_t launch_kd_prepare(cudaStream_t st, const KdWork& w, const int32_t* tree_axis,
                               const int32_t* tree_leaf, int32_t n_nodes, int32_t S0, const int64_t* offsets_in,
                               int64_t N, const float* px, const float* py, const float* pz) {
     k_kd_init<<<(unsigned)((std::max<int64_t>(N, S0) + 255) / 256), 256, 0, st>>>(w.rec[0], N, px, py, pz,
                                                                                  w.seg_parent[0], S0);
-    if (binning) {
-        // one segment: the root with every sample
-        const int64_t off[2] = {0, N};
-        const int32_t root = 0;
-        cudaError_t e;
-        if ((e = cudaMemcpyAsync(w.seg_off[0], off, sizeof(off), cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
-        if ((e = cudaMemcpyAsync(w.seg_node[0], &root, sizeof(root), cudaMemcpyHostToDevice, st)) != cudaSuccess)
-            return e;
-        return cudaStreamSynchronize(st);
-    }
     cudaError_t e = cudaMemcpyAsync(w.seg_off[0], offsets_in, sizeof(int64_t) * (S0 + 1), cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) return e;
     k_kd_leaf_nodes<<<(n_nodes + 255) / 256, 256, 0, st>>>(tree_axis, tree_leaf, n_nodes, w.seg_node[0]);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Binning into a fixed tree (Sec. 4.2: the samples of a round go to the leaf
+// that contains them): every sample's leaf by descent, then a stable LSD
+// radix sort of (leaf, index) pairs with 8-bit digits, the leaf offsets from
+// the sorted keys, and one gather of the seven streams.  Stability keeps the
+// samples of a leaf in their input order.
+constexpr int kRxThreads = 256, kRxPer = 8, kRxTile = kRxThreads * kRxPer;   // keys per tile
+constexpr int kRxScan = 4096;                                                 // entries per scan block
+
+__global__ void k_bin_keys(const int32_t* __restrict__ axis, const double* __restrict__ split,
+                           const int32_t* __restrict__ left, const int32_t* __restrict__ leaf, int max_depth,
+                           int64_t N, const float* __restrict__ px, const float* __restrict__ py,
+                           const float* __restrict__ pz, uint32_t* __restrict__ key, uint32_t* __restrict__ idx) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const float x[3] = {px[i], py[i], pz[i]};
+    int n = 0;
+    for (int d = 0; d <= max_depth && axis[n] >= 0; ++d) {      // bounded by the tree's node count
+        const int a = axis[n];
+        n = (double)x[a] < split[n] ? left[n] : left[n] + 1;
+    }
+    key[i] = axis[n] < 0 ? (uint32_t)leaf[n] : 0u;
+    idx[i] = (uint32_t)i;
+}
+
+// per tile of 2048 keys: counts of each digit, digit-major (hist[d T + tile])
+__global__ void __launch_bounds__(kRxThreads) k_rx_hist(const uint32_t* __restrict__ key, int64_t N, int shift,
+                                                      int T, uint32_t* __restrict__ hist) {
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0u;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kRxTile;
+#pragma unroll
+    for (int q = 0; q < kRxPer; ++q) {
+        const int64_t i = base + q * kRxThreads + threadIdx.x;
+        if (i < N) atomicAdd(&h[(key[i] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * T + blockIdx.x] = h[threadIdx.x];
+}
+
+// exclusive scan of M counts in place: block sums, a one-CTA scan of the
+// sums, then each block's own scan plus its offset
+__global__ void __launch_bounds__(1024) k_rx_scan_sums(const uint32_t* __restrict__ a, int64_t M,
+                                                     uint32_t* __restrict__ bsum) {
+    __shared__ uint32_t s[32];
+    const int64_t b0 = (int64_t)blockIdx.x * kRxScan;
+    uint32_t v = 0u;
+#pragma unroll
+    for (int q = 0; q < kRxScan / 1024; ++q) {
+        const int64_t i = b0 + q * 1024 + threadIdx.x;
+        if (i < M) v += a[i];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        uint32_t w = s[threadIdx.x];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+        if (threadIdx.x == 0) bsum[blockIdx.x] = w;
+    }
+}
+
+__device__ __forceinline__ uint32_t block_exclusive_1024(uint32_t v, uint32_t* s_warp, uint32_t* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t u = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d) x += u;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = s_warp[lane];
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t u = __shfl_up_sync(0xffffffffu, w, d);
+            if (lane >= d) w += u;
+        }
+        s_warp[lane] = w;
+    }
+    __syncthreads();
+    const uint32_t ex = x - v + (warp > 0 ? s_warp[warp - 1] : 0u);
+    *total = s_warp[31];
+    __syncthreads();
+    return ex;
+}
+
+__global__ void __launch_bounds__(1024) k_rx_scan_top(uint32_t* __restrict__ bsum, int nb) {
+    __shared__ uint32_t s_warp[32];
+    uint32_t carry = 0u;
+    for (int base = 0; base < nb; base += 1024) {
+        const int i = base + threadIdx.x;
+        const uint32_t v = i < nb ? bsum[i] : 0u;
+        uint32_t tot;
+        const uint32_t ex = block_exclusive_1024(v, s_warp, &tot);
+        if (i < nb) bsum[i] = carry + ex;
+        carry += tot;
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_rx_scan_down(uint32_t* __restrict__ a, int64_t M,
+                                                     const uint32_t* __restrict__ bsum) {
+    __shared__ uint32_t s_warp[32];
+    const int64_t b0 = (int64_t)blockIdx.x * kRxScan;
+    uint32_t carry = bsum[blockIdx.x];
+    for (int q = 0; q < kRxScan / 1024; ++q) {
+        const int64_t i = b0 + q * 1024 + threadIdx.x;
+        const uint32_t v = i < M ? a[i] : 0u;
+        uint32_t tot;
+        const uint32_t ex = block_exclusive_1024(v, s_warp, &tot);
+        if (i < M) a[i] = carry + ex;
+        carry += tot;
+    }
+}
+
+// stable scatter of one digit: the tile's keys in eight ordered sub-rounds of
+// 256; within a sub-round, rank among equal digits by warp, then lane
+__global__ void __launch_bounds__(kRxThreads) k_rx_scatter(const uint32_t* __restrict__ key_in,
+                                                         const uint32_t* __restrict__ idx_in,
+                                                         uint32_t* __restrict__ key_out,
+                                                         uint32_t* __restrict__ idx_out, int64_t N, int shift,
+                                                         int T, const uint32_t* __restrict__ off) {
+    constexpr int W = kRxThreads / 32;
+    __shared__ uint32_t s_carry[256];
+    __shared__ uint32_t s_wc[W][256];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tile = blockIdx.x;
+    s_carry[tid] = off[(int64_t)tid * T + tile];
+    const int64_t base = (int64_t)tile * kRxTile;
+    for (int r = 0; r < kRxPer; ++r) {
+#pragma unroll
+        for (int w = 0; w < W; ++w) s_wc[w][tid] = 0u;
+        __syncthreads();
+        const int64_t i = base + r * kRxThreads + tid;
+        const bool valid = i < N;
+        const uint32_t k = valid ? key_in[i] : 0u;
+        const uint32_t v = valid ? idx_in[i] : 0u;
+        const uint32_t d = valid ? (k >> shift) & 255u : 256u;   // invalid lanes only match each other
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const int rank = __popc(peers & ((1u << lane) - 1u));
+        if (valid && rank == 0) s_wc[warp][d] = (uint32_t)__popc(peers);
+        __syncthreads();
+        if (valid) {
+            uint32_t pre = 0u;
+            for (int w = 0; w < warp; ++w) pre += s_wc[w][d];
+            const uint32_t dst = s_carry[d] + pre + (uint32_t)rank;
+            key_out[dst] = k;
+            idx_out[dst] = v;
+        }
+        __syncthreads();
+        uint32_t add = 0u;
+#pragma unroll
+        for (int w = 0; w < W; ++w) add += s_wc[w][tid];
+        s_carry[tid] += add;
+        __syncthreads();
+    }
+}
+
+// offsets[l] = first position of leaf l in the sorted keys (S + 1 entries)
+__global__ void k_bin_offsets(const uint32_t* __restrict__ key, int64_t N, int32_t S, int64_t* __restrict__ offsets) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > N) return;
+    const int64_t prev = i > 0 ? (int64_t)key[i - 1] : -1;
+    const int64_t cur = i < N ? (int64_t)key[i] : (int64_t)S;
+    for (int64_t l = prev + 1; l <= cur; ++l) offsets[l] = i;
+}
+
+__global__ void k_gather_idx(int64_t N, const uint32_t* __restrict__ idx, BatchDesc in, BatchDesc out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const uint32_t j = idx[i];
+#pragma unroll
+    for (int q = 0; q < 7; ++q) const_cast<float*>(out.p[q])[i] = in.p[q][j];
+}
+
+int64_t rx_tiles(int64_t N) { return (N + kRxTile - 1) / kRxTile; }
+int64_t rx_scan_blocks(int64_t N) { return (256 * rx_tiles(N) + kRxScan - 1) / kRxScan; }
+
+cudaError_t launch_kd_bin(cudaStream_t st, const KdWork& w, const int32_t* axis, const double* split,
+                          const int32_t* left, const int32_t* leaf, int32_t n_nodes, int32_t n_leaves, int64_t N,
+                          const float* px, const float* py, const float* pz, const BatchDesc& in,
+                          const BatchDesc& out, int64_t* offsets) {
+    uint32_t* key[2] = {reinterpret_cast<uint32_t*>(w.rec[0]), reinterpret_cast<uint32_t*>(w.rec[1])};
+    uint32_t* idx[2] = {key[0] + N, key[1] + N};
+    if (N > 0) {
+        k_bin_keys<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(axis, split, left, leaf, n_nodes, N, px, py, pz,
+                                                               key[0], idx[0]);
+        int bits = 0;
+        while (bits < 32 && (int64_t(1) << bits) < (int64_t)n_leaves) ++bits;
+        const int passes = std::max(1, (bits + 7) / 8);
+        const int T = (int)rx_tiles(N);
+        const int64_t M = 256 * (int64_t)T;
+        const int nb = (int)rx_scan_blocks(N);
+        for (int p = 0; p < passes; ++p) {
+            const int src = p & 1, dst = src ^ 1;
+            k_rx_hist<<<T, kRxThreads, 0, st>>>(key[src], N, 8 * p, T, w.rx_hist);
+            k_rx_scan_sums<<<nb, 1024, 0, st>>>(w.rx_hist, M, w.rx_bsum);
+            k_rx_scan_top<<<1, 1024, 0, st>>>(w.rx_bsum, nb);
+            k_rx_scan_down<<<nb, 1024, 0, st>>>(w.rx_hist, M, w.rx_bsum);
+            k_rx_scatter<<<T, kRxThreads, 0, st>>>(key[src], idx[src], key[dst], idx[dst], N, 8 * p, T, w.rx_hist);
+        }
+        const int fin = passes & 1;
+        k_gather_idx<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(N, idx[fin], in, out);
+        k_bin_offsets<<<(unsigned)((N + 1 + 255) / 256), 256, 0, st>>>(key[fin], N, n_leaves, offsets);
+    } else {
+        k_bin_offsets<<<1, 256, 0, st>>>(key[0], 0, n_leaves, offsets);
+    }
     return cudaGetLastError();
 }
 

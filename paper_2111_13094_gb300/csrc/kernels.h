@@ -78,20 +78,28 @@ struct KdWork {
     int64_t* tile_prefix;
     int32_t* seg_tile0;          // [cap_leaves + 2] first tile of each segment
     int32_t* counters;           // [0] tiles, [1] splits
+    uint32_t* rx_hist;           // binning: digit counts per radix tile, then their offsets
+    uint32_t* rx_bsum;           // binning: scan block sums
     int64_t max_tiles;
 };
 cudaError_t launch_kd_grid(cudaStream_t s, int levels, int32_t* axis, double* split, int32_t* left, int32_t* leaf);
 cudaError_t launch_kd_lookup(cudaStream_t s, const int32_t* axis, const double* split, const int32_t* left,
                              const int32_t* leaf, int max_depth, int64_t Q, const float* px, const float* py,
                              const float* pz, int32_t* out);
-cudaError_t launch_kd_prepare(cudaStream_t st, const KdWork& w, int binning, const int32_t* tree_axis,
+cudaError_t launch_kd_prepare(cudaStream_t st, const KdWork& w, const int32_t* tree_axis,
                               const int32_t* tree_leaf, int32_t n_nodes, int32_t S0, const int64_t* offsets_in,
                               int64_t N, const float* px, const float* py, const float* pz);
-cudaError_t kd_rounds(cudaStream_t st, const KdWork& w, int binning, int64_t c, int32_t* tree_axis,
+cudaError_t kd_rounds(cudaStream_t st, const KdWork& w, int64_t c, int32_t* tree_axis,
                       double* tree_split, int32_t* tree_left, int32_t* tree_leaf, int32_t* n_nodes,
                       int32_t* n_leaves, int32_t cap_nodes, int32_t cap_leaves, int32_t S0, int64_t N,
                       const float4** rec_final,
                       int64_t** seg_off_final, int64_t** seg_parent_final, int32_t* S_final, int* overflow);
+int64_t rx_tiles(int64_t N);
+int64_t rx_scan_blocks(int64_t N);
+cudaError_t launch_kd_bin(cudaStream_t st, const KdWork& w, const int32_t* axis, const double* split,
+                          const int32_t* left, const int32_t* leaf, int32_t n_nodes, int32_t n_leaves, int64_t N,
+                          const float* px, const float* py, const float* pz, const BatchDesc& in,
+                          const BatchDesc& out, int64_t* offsets);
 cudaError_t launch_kd_gather(cudaStream_t st, int64_t N, const float4* rec, const BatchDesc& in,
                              const BatchDesc& out);
 cudaError_t launch_gather_state(cudaStream_t s, int K, int64_t R_out, const int64_t* src, const sdmm_state& in,
