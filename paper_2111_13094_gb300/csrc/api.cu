@@ -854,7 +854,7 @@ sdmm_status sdmm_autotune(const sdmm_config* cfg, const sdmm_samples* s, const s
 namespace {
 
 struct KdLayout {
-    size_t rec[2], seg_off[2], seg_node[2], seg_parent[2], seg_axis, seg_split, seg_flag, seg_new, seg_sum,
+    size_t rec[2], seg_off[2], seg_node[2], seg_parent[2], seg_axis, seg_split, seg_split_f, split_f, seg_flag, seg_new, seg_sum,
         seg_left, tile_seg, tile_start, tile_left, tile_prefix, seg_tile0, counters, rx_hist, rx_bsum, total;
     int64_t max_tiles;
 };
@@ -878,6 +878,8 @@ KdLayout kd_layout(const sdmm_kdtree* t, int64_t N) {
     }
     L.seg_axis = take(sizeof(int32_t) * S);
     L.seg_split = take(sizeof(double) * S);
+    L.seg_split_f = take(sizeof(float) * S);
+    L.split_f = take(sizeof(float) * (size_t)t->cap_nodes);
     L.seg_flag = take(sizeof(int32_t) * S);
     L.seg_new = take(sizeof(int32_t) * S);
     L.seg_sum = take(sizeof(unsigned long long) * 6 * S);
@@ -905,6 +907,8 @@ KdWork kd_work(void* ws, const KdLayout& L) {
     }
     w.seg_axis = reinterpret_cast<int32_t*>(b + L.seg_axis);
     w.seg_split = reinterpret_cast<double*>(b + L.seg_split);
+    w.seg_split_f = reinterpret_cast<float*>(b + L.seg_split_f);
+    w.split_f = reinterpret_cast<float*>(b + L.split_f);
     w.seg_flag = reinterpret_cast<int32_t*>(b + L.seg_flag);
     w.seg_new = reinterpret_cast<int32_t*>(b + L.seg_new);
     w.seg_sum = reinterpret_cast<unsigned long long*>(b + L.seg_sum);

@@ -93,6 +93,7 @@ struct KdRound {
     int32_t S;
     int32_t* seg_axis;
     double* seg_split;
+    float* seg_split_f;          // the smallest float >= seg_split: x < split <=> x < split_f for float x
     int32_t* seg_flag;           // 1: the segment splits this round
     int32_t* seg_new;            // new index of the segment (its left part)
     unsigned long long* seg_sum; // [S][6] fixed-point sums (refinement only)
@@ -161,10 +162,26 @@ __global__ void k_kd_tile_fill(KdRound k) {
     k.tile_start[t] = k.seg_off[lo] + (int64_t)(t - k.seg_tile0[lo]) * kKdTile;
 }
 
+// q = floor(clamp(x, 0, 1) 2^32) and q2 = floor(clamp(x, 0, 1)^2 2^32), exactly,
+// from the float's integer mantissa and exponent (x = m 2^e), in integer
+// arithmetic (the FP64 units of this GPU are few)
 __device__ __forceinline__ void fixed_point(float x, unsigned long long& q, unsigned long long& q2) {
-    const double xc = fmin(fmax((double)x, 0.0), 1.0);
-    q = (unsigned long long)floor(xc * kTwo32);
-    q2 = (unsigned long long)floor(__dmul_rn(xc, xc) * kTwo32);
+    if (!(x > 0.f)) {                                     // also NaN
+        q = q2 = 0ull;
+        return;
+    }
+    if (x >= 1.f) {
+        q = q2 = 4294967296ull;
+        return;
+    }
+    const uint32_t b = __float_as_uint(x);
+    const int ef = (int)(b >> 23);                        // biased exponent, 0 for subnormals
+    const unsigned long long m = ef ? ((b & 0x7FFFFFu) | 0x800000u) : (b & 0x7FFFFFu);
+    const int e = (ef ? ef : 1) - 150;                   // x = m 2^e, e <= -24 here
+    const int s1 = e + 32, s2 = 2 * e + 32;
+    q = s1 >= 0 ? (m << s1) : (-s1 >= 64 ? 0ull : (m >> -s1));
+    const unsigned long long mm = m * m;                 // < 2^48
+    q2 = s2 >= 0 ? (mm << s2) : (-s2 >= 64 ? 0ull : (mm >> -s2));
 }
 
 // fixed-point sums of the samples of segments holding more than c of them
@@ -231,6 +248,7 @@ __global__ void k_kd_plan(KdRound k, int64_t c) {
     }
     k.seg_axis[s] = a;
     k.seg_split[s] = pl;
+    k.seg_split_f[s] = __double2float_ru(pl);
     k.seg_left[s] = 0ull;
 }
 
@@ -242,7 +260,7 @@ __global__ void __launch_bounds__(kKdThreads) k_kd_count(KdRound k, const float4
     const int s = k.tile_seg[t];
     const int a = k.seg_axis[s];
     const int64_t end = k.seg_off[s + 1];
-    const double pl = k.seg_split[s];
+    const float pl = k.seg_split_f[s];
     const int64_t i0 = k.tile_start[t] + threadIdx.x;
     int f = 0;
 #pragma unroll
@@ -251,7 +269,7 @@ __global__ void __launch_bounds__(kKdThreads) k_kd_count(KdRound k, const float4
         if (a >= 0 && i < end) {
             const float4 p = rec[i];
             const float x = a == 0 ? p.x : (a == 1 ? p.y : p.z);
-            f += (double)x < pl ? 1 : 0;
+            f += x < pl ? 1 : 0;
         }
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -370,14 +388,14 @@ __global__ void __launch_bounds__(kKdThreads) k_kd_scatter(KdRound k, const floa
         return;                                               // (uniform per CTA)
     }
     const int a = k.seg_axis[s];
-    const double pl = k.seg_split[s];
+    const float pl = k.seg_split_f[s];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int f[kKdPer], rank_w[kKdPer];
 #pragma unroll
     for (int q = 0; q < kKdPer; ++q) {
         const bool in = i0 + q * kKdThreads < o1;
         const float x = a == 0 ? p[q].x : (a == 1 ? p[q].y : p[q].z);
-        f[q] = (in && (double)x < pl) ? 1 : 0;
+        f[q] = (in && x < pl) ? 1 : 0;
         const unsigned bal = __ballot_sync(0xffffffffu, f[q]);
         rank_w[q] = __popc(bal & ((1u << lane) - 1u));
         if (lane == 0) s_cnt[q][warp] = __popc(bal);
@@ -536,6 +554,7 @@ cudaError_t kd_rounds(cudaStream_t st, const KdWork& w, int64_t c, int32_t* tree
         k.S = S;
         k.seg_axis = w.seg_axis;
         k.seg_split = w.seg_split;
+        k.seg_split_f = w.seg_split_f;
         k.seg_flag = w.seg_flag;
         k.seg_new = w.seg_new;
         k.seg_sum = w.seg_sum;
@@ -603,7 +622,13 @@ cudaError_t launch_kd_prepare(cudaStream_t st, const KdWork& w, const int32_t* t
 constexpr int kRxThreads = 256, kRxPer = 8, kRxTile = kRxThreads * kRxPer;   // keys per tile
 constexpr int kRxScan = 4096;                                                 // entries per scan block
 
-__global__ void k_bin_keys(const int32_t* __restrict__ axis, const double* __restrict__ split,
+// the float threshold of every node: the smallest float >= split (exact test)
+__global__ void k_kd_split_f(const double* __restrict__ split, int32_t n_nodes, float* __restrict__ split_f) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n < n_nodes) split_f[n] = __double2float_ru(split[n]);
+}
+
+__global__ void k_bin_keys(const int32_t* __restrict__ axis, const float* __restrict__ split,
                            const int32_t* __restrict__ left, const int32_t* __restrict__ leaf, int max_depth,
                            int64_t N, const float* __restrict__ px, const float* __restrict__ py,
                            const float* __restrict__ pz, uint32_t* __restrict__ key, uint32_t* __restrict__ idx) {
@@ -613,7 +638,7 @@ __global__ void k_bin_keys(const int32_t* __restrict__ axis, const double* __res
     int n = 0;
     for (int d = 0; d <= max_depth && axis[n] >= 0; ++d) {      // bounded by the tree's node count
         const int a = axis[n];
-        n = (double)x[a] < split[n] ? left[n] : left[n] + 1;
+        n = x[a] < split[n] ? left[n] : left[n] + 1;
     }
     key[i] = axis[n] < 0 ? (uint32_t)leaf[n] : 0u;
     idx[i] = (uint32_t)i;
@@ -783,8 +808,9 @@ cudaError_t launch_kd_bin(cudaStream_t st, const KdWork& w, const int32_t* axis,
     uint32_t* key[2] = {reinterpret_cast<uint32_t*>(w.rec[0]), reinterpret_cast<uint32_t*>(w.rec[1])};
     uint32_t* idx[2] = {key[0] + N, key[1] + N};
     if (N > 0) {
-        k_bin_keys<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(axis, split, left, leaf, n_nodes, N, px, py, pz,
-                                                               key[0], idx[0]);
+        k_kd_split_f<<<(n_nodes + 255) / 256, 256, 0, st>>>(split, n_nodes, w.split_f);
+        k_bin_keys<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(axis, w.split_f, left, leaf, n_nodes, N, px, py,
+                                                               pz, key[0], idx[0]);
         int bits = 0;
         while (bits < 32 && (int64_t(1) << bits) < (int64_t)n_leaves) ++bits;
         const int passes = std::max(1, (bits + 7) / 8);

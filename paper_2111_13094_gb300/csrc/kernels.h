@@ -68,6 +68,8 @@ struct KdWork {
     int64_t* seg_parent[2];      // leaf of the call's input each segment descends from
     int32_t* seg_axis;
     double* seg_split;
+    float* seg_split_f;          // [cap_leaves] float thresholds of seg_split
+    float* split_f;              // [cap_nodes] float thresholds of the tree's splits (binning)
     int32_t* seg_flag;
     int32_t* seg_new;
     unsigned long long* seg_sum; // [cap_leaves][6]
