@@ -464,8 +464,10 @@ __global__ void __launch_bounds__(128) k_new_charts(WsHeader* __restrict__ ws,
     }
 }
 
-template <bool FEAT>
-__global__ void __launch_bounds__(128) k_reduce_mstep(WsHeader* __restrict__ ws,
+constexpr int kMstepThreads = 32;
+
+template <bool FEAT, bool TWO>
+__global__ void __launch_bounds__(kMstepThreads) k_reduce_mstep(WsHeader* __restrict__ ws,
                                                       const int64_t* __restrict__ chunk_base,
                                                       const float* __restrict__ partial, int ps,
                                                       sdmm_config cfg, sdmm_state st, int iter,
@@ -477,7 +479,7 @@ __global__ void __launch_bounds__(128) k_reduce_mstep(WsHeader* __restrict__ ws,
     __shared__ double s_st[SDMM_MAX_K * kStat + 2];
     __shared__ double s_feat[FEAT ? 3 * SDMM_MAX_K * kFeat + 8 : 1];
     __shared__ double s_S0[SDMM_MAX_K];
-    __shared__ double s_two[SDMM_MAX_K * 15];    // second-pass moments (accurate update)
+    __shared__ double s_two[TWO ? SDMM_MAX_K * 15 : 1];   // second-pass moments (accurate update)
     __shared__ int s_code[SDMM_MAX_K];
     __shared__ int s_skip;
 
@@ -523,7 +525,7 @@ __global__ void __launch_bounds__(128) k_reduce_mstep(WsHeader* __restrict__ ws,
     } else {
         reduce_partials(partial, ps, c0, c1, K * kStat + 2, s_st);
     }
-    if (partial2 != nullptr) reduce_partials(partial2, ps2, c0, c1, K * 15, s_two);
+    if (TWO) reduce_partials(partial2, ps2, c0, c1, K * 15, s_two);
     __syncthreads();
     const double W = s_st[K * kStat];
     if (tid == 0) {
@@ -581,7 +583,7 @@ __global__ void __launch_bounds__(128) k_reduce_mstep(WsHeader* __restrict__ ws,
             } else {
                 exp_map_f64(omw, m + 3, nmw);             // Eq. tangent-space-mu-update
             }
-            if (partial2 != nullptr) {
+            if (TWO) {
                 // accurate update (Eq. tangent-space-sigma-update): the second
                 // pass measured the batch in the new chart, centred at the new mean
                 for (int p = 0; p < 15; ++p) nS2[p] = s_two[tid * 15 + p] * invW;
@@ -930,12 +932,18 @@ cudaError_t launch_reduce_mstep(cudaStream_t s, int64_t R, WsHeader* ws, const i
                                 const float* partial, int ps, const sdmm_config& cfg,
                                 const sdmm_state& st, int iter, const float* xref,
                                 const float* partial2, int ps2) {
+    // one warp per region: lane k < K updates component k, all lanes
+    // threads share the reduction of the unit partials; small shared arrays
+    // keep every region of a large batch resident at once
     if (xref != nullptr)
-        k_reduce_mstep<true><<<(unsigned)R, 128, 0, s>>>(ws, cb, partial, ps, cfg, st, iter, xref,
-                                                         partial2, ps2);
+        k_reduce_mstep<true, false><<<(unsigned)R, kMstepThreads, 0, s>>>(ws, cb, partial, ps, cfg, st, iter, xref,
+                                                                         nullptr, 0);
+    else if (partial2 != nullptr)
+        k_reduce_mstep<false, true><<<(unsigned)R, kMstepThreads, 0, s>>>(ws, cb, partial, ps, cfg, st, iter, xref,
+                                                                         partial2, ps2);
     else
-        k_reduce_mstep<false><<<(unsigned)R, 128, 0, s>>>(ws, cb, partial, ps, cfg, st, iter, xref,
-                                                          partial2, ps2);
+        k_reduce_mstep<false, false><<<(unsigned)R, kMstepThreads, 0, s>>>(ws, cb, partial, ps, cfg, st, iter, xref,
+                                                                          nullptr, 0);
     return cudaGetLastError();
 }
 
