@@ -229,6 +229,7 @@ sdmm_status enqueue_fit(const FitLaunch& f, cudaStream_t s, std::vector<cudaEven
     const int KP = pow2_ceil(f.cfg.K);
     const bool tcore = tensor_core(&f.cfg);
     const int euclid = f.cfg.dir_coords == SDMM_DIR_EUCLIDEAN;
+    const int mstep_threads = f.R > 3 * (int64_t)std::max(1, sm_count()) ? 32 : 128;
     SDMM_CUDA(launch_build_chunks(s, f.w.hdr, f.w.cb, f.w.cr, f.w.units, f.L.chunk, f.cfg.min_samples,
                                   f.L.max_chunks),
               "build_chunks");
@@ -258,7 +259,7 @@ sdmm_status enqueue_fit(const FitLaunch& f, cudaStream_t s, std::vector<cudaEven
                       "accumulate_two");
         }
         SDMM_CUDA(launch_reduce_mstep(s, f.R, f.w.hdr, f.w.cb, f.w.partial, f.L.ps, f.cfg, f.st, it,
-                                      tcore ? f.w.xref : nullptr, f.w.partial2, f.L.ps2),
+                                      tcore ? f.w.xref : nullptr, f.w.partial2, f.L.ps2, mstep_threads),
                   "reduce_mstep");
     }
     return SDMM_OK;

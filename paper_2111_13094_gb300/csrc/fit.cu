@@ -464,10 +464,9 @@ __global__ void __launch_bounds__(128) k_new_charts(WsHeader* __restrict__ ws,
     }
 }
 
-constexpr int kMstepThreads = 32;
 
 template <bool FEAT, bool TWO>
-__global__ void __launch_bounds__(kMstepThreads) k_reduce_mstep(WsHeader* __restrict__ ws,
+__global__ void __launch_bounds__(128) k_reduce_mstep(WsHeader* __restrict__ ws,
                                                       const int64_t* __restrict__ chunk_base,
                                                       const float* __restrict__ partial, int ps,
                                                       sdmm_config cfg, sdmm_state st, int iter,
@@ -931,19 +930,21 @@ cudaError_t launch_new_charts(cudaStream_t s, int64_t R, WsHeader* ws, const int
 cudaError_t launch_reduce_mstep(cudaStream_t s, int64_t R, WsHeader* ws, const int64_t* cb,
                                 const float* partial, int ps, const sdmm_config& cfg,
                                 const sdmm_state& st, int iter, const float* xref,
-                                const float* partial2, int ps2) {
-    // one warp per region: lane k < K updates component k, all lanes
-    // threads share the reduction of the unit partials; small shared arrays
-    // keep every region of a large batch resident at once
+                                const float* partial2, int ps2, int threads) {
+    // one CTA per region: thread k < K updates component k, all threads share
+    // the reduction of the unit partials.  The caller picks the width: one
+    // warp when the regions outnumber what 128-thread CTAs keep resident
+    // (the per-component thread needs about 156 registers), four warps (a
+    // faster reduction of many units) for a few large regions.
     if (xref != nullptr)
-        k_reduce_mstep<true, false><<<(unsigned)R, kMstepThreads, 0, s>>>(ws, cb, partial, ps, cfg, st, iter, xref,
-                                                                         nullptr, 0);
+        k_reduce_mstep<true, false><<<(unsigned)R, threads, 0, s>>>(ws, cb, partial, ps, cfg, st, iter, xref,
+                                                                   nullptr, 0);
     else if (partial2 != nullptr)
-        k_reduce_mstep<false, true><<<(unsigned)R, kMstepThreads, 0, s>>>(ws, cb, partial, ps, cfg, st, iter, xref,
-                                                                         partial2, ps2);
+        k_reduce_mstep<false, true><<<(unsigned)R, threads, 0, s>>>(ws, cb, partial, ps, cfg, st, iter, xref,
+                                                                   partial2, ps2);
     else
-        k_reduce_mstep<false, false><<<(unsigned)R, kMstepThreads, 0, s>>>(ws, cb, partial, ps, cfg, st, iter, xref,
-                                                                          nullptr, 0);
+        k_reduce_mstep<false, false><<<(unsigned)R, threads, 0, s>>>(ws, cb, partial, ps, cfg, st, iter, xref,
+                                                                    nullptr, 0);
     return cudaGetLastError();
 }
 

@@ -32,7 +32,7 @@ cudaError_t launch_new_charts(cudaStream_t s, int64_t R, WsHeader* ws, const int
 cudaError_t launch_reduce_mstep(cudaStream_t s, int64_t R, WsHeader* ws, const int64_t* cb,
                                 const float* partial, int ps, const sdmm_config& cfg,
                                 const sdmm_state& st, int iter, const float* xref,
-                                const float* partial2 = nullptr, int ps2 = 0);
+                                const float* partial2 = nullptr, int ps2 = 0, int threads = 128);
 // contraction form on the tensor cores
 size_t tc_smem_bytes(int K, int prec);
 
