@@ -863,7 +863,7 @@ struct KdLayout {
 KdLayout kd_layout(const sdmm_kdtree* t, int64_t N) {
     KdLayout L{};
     const size_t S = (size_t)t->cap_leaves + 1;
-    L.max_tiles = N / 1024 + (int64_t)t->cap_leaves + 1;
+    L.max_tiles = N / kKdTile + (int64_t)t->cap_leaves + 1;
     const size_t T = (size_t)L.max_tiles;
     size_t o = 0;
     auto take = [&](size_t bytes) {

@@ -6,7 +6,7 @@
 //  binning (k_bin_keys, k_rx_*, k_bin_offsets, k_gather_idx): every sample's
 //  leaf, a stable radix sort by leaf, offsets, one gather
 //  refinement, as rounds of stable segment partitions:
-//    k_kd_tiles     tiles of 1,024 samples, none spanning two segments
+//    k_kd_tiles     tiles of kKdTile samples, none spanning two segments
 //    k_kd_stats     fixed-point position sums of the segments to split
 //    k_kd_plan      split plane of each segment (tree node, or mean along the
 //                   axis of largest variance)
@@ -27,8 +27,7 @@
 
 namespace sdmm {
 
-constexpr int kKdTile = 1024;                 // samples per tile
-constexpr int kKdThreads = 256;               // threads per tile CTA: 4 samples each
+constexpr int kKdThreads = 256;               // threads per tile CTA: kKdTile / 256 samples each
 constexpr int kKdPer = kKdTile / kKdThreads;
 constexpr double kTwo32 = 4294967296.0;
 
@@ -106,7 +105,7 @@ struct KdRound {
     int32_t* counters;           // [0] tiles, [1] splits
 };
 
-// Tiles: ceil(M_s / 1024) per segment (empty segments get none), in segment
+// Tiles: ceil(M_s / kKdTile) per segment (empty segments get none), in segment
 // order.  One CTA of 1024 threads: the exclusive prefix of the segments' tile
 // counts (k_kd_tile_fill then maps tiles to segments in parallel).
 __global__ void __launch_bounds__(1024) k_kd_tiles(KdRound k, int64_t max_tiles) {

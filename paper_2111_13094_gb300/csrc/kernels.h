@@ -61,6 +61,8 @@ cudaError_t launch_tc_selftest(cudaStream_t s, int kind, int N, int Kd, const fl
                                float* D, int variant, int* status);
 
 // ---- spatial kD-tree (kdtree.cu)
+constexpr int kKdTile = 1024;                 // samples per tile of the refinement rounds
+
 struct KdWork {
     float4* rec[2];              // (x, y, z, sample index as int bits), ping-pong [N]
     int64_t* seg_off[2];         // segment offsets [cap_leaves + 1]
