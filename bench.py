@@ -171,10 +171,22 @@ def cpu_baseline(budget_s=15.0, seed=1, R_REGIONS=4096):
                       f"{ROUNDS} stepwise rounds each, FP64, single thread, {t_total:.1f} s"}
 
 
+def fit_config(R_REGIONS, N):
+    """The workload both arms report (the GPU arm adds its run's status counts)."""
+    return {"workload": f"batched stepwise MAP-EM fit: {R_REGIONS} regions x K=16, sample counts "
+                        "log-uniform in [256, 65536], 4 Robbins-Monro rounds per step with a "
+                        "fresh batch each, CUDA-graph replay per round",
+            "regions": R_REGIONS, "K": K_COMP, "rounds_per_step": ROUNDS,
+            "samples_per_round": N, "per_rank": True,
+            "l2": "inputs larger than L2 (about 1.35 GB per round)"}
+
+
 def run_reference(args):
     _, rank, _ = rank_env()
     if rank != 0:                            # the oracle runs once, on rank 0
         return None
+    from paper_2111_13094_gb300 import synthetic as syn
+    n_round = int(syn.region_counts(rank_seed(0), args.regions).sum())   # rank 0's workload, as the GPU arm
     per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
     for _ in range(args.warmup):
         cpu_baseline(budget_s=per_step / 4)
@@ -188,7 +200,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "batched stepwise fit, 4096 regions x K=16, 4 rounds (bounded sample)"},
+            "config": fit_config(args.regions, n_round),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": vals[0]["sample"]},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -437,14 +449,8 @@ def run_gpu(args):
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic (seeded; shapes of the paper's leaves: K=16, log-uniform leaf sizes)",
-                "config": {"workload": f"batched stepwise MAP-EM fit: {R_REGIONS} regions x K=16, sample counts "
-                                       "log-uniform in [256, 65536], 4 Robbins-Monro rounds per step with a "
-                                       "fresh batch each, CUDA-graph replay per round",
-                           "regions": R_REGIONS, "K": K_COMP, "rounds_per_step": ROUNDS,
-                           "samples_per_round": N, "per_rank": True,
-                           "l2": "inputs larger than L2 (about 1.35 GB per round)",
-                           "all_regions_ok": status_ok, "status_counts": status_counts,
-                           "precision": args.precision},
+                "config": dict(fit_config(R_REGIONS, N), all_regions_ok=status_ok, status_counts=status_counts,
+                               precision=args.precision),
                 "clocks": ck, "e2e": e2e,
                 "gpu_launches": args.steps * ROUNDS * (4 if prec == api.PREC_FP32 else 5),
                 "roofline": roof, "cpu_baseline": cpu, "queries": qres, "tensor_core": tcres,
