@@ -435,10 +435,13 @@ def run_gpu(args):
         # product sampling with a 3-lobe BSDF mixture per query (top-2 lobes kept)
         bw, bmu, bL = (torch.from_numpy(a).to(dev) for a in syn.bsdf_lobes(seed, Q_COUNT, 3))
         t_prod = timed(lambda: api.product_sample(cfg, qst, qx, bw, bmu, bL, grid=grid, seed=7))
+        bw_b, bmu_b, bL_b = bw[order].contiguous(), bmu[order].contiguous(), bL[order].contiguous()
+        t_prod_b = timed(lambda: api.product_sample(cfg, qst, qx_b, bw_b, bmu_b, bL_b, region=reg_b, seed=7))
         qres["product"] = {"value": world * Q_COUNT / (t_prod * 1e-3), "unit": "queries/s", "kernel_ms": t_prod,
+                           "binned_value": world * Q_COUNT / (t_prod_b * 1e-3), "binned_kernel_ms": t_prod_b,
                            "config": "the same 16M queries, 3 BSDF lobes each (wide, narrow, random), "
                                      "2K pairs per query: condition + pair products + sample + product pdf, FP32"}
-        del bw, bmu, bL
+        del bw, bmu, bL, bw_b, bmu_b, bL_b
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:

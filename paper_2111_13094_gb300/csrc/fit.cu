@@ -272,17 +272,15 @@ __global__ void __launch_bounds__(kWarps * 32, MODE == MODE_TWO ? 1 : 2)
                     const float v2 = c2[6] * sb.x + c2[7] * sb.y + c2[8] * sb.z;
                     const float cz2 = c2[9] * sb.x + c2[10] * sb.y + c2[11] * sb.z;
                     const float s22 = u2 * u2 + v2 * v2;
-                    const float rs2 = rsqrtf(s22);
-                    const float th2 = atan2_pos(s22 * rs2, cz2);
-                    const bool oc2 = s22 > 0.f;
-                    const float g2 = oc2 ? th2 * rs2 : 1.f;
+                    const bool cut2 = s22 == 0.f && cz2 < 0.f;   // cut locus of the new chart
+                    const float g2 = cut2 ? 1.f : g_of_cos(cz2, rsqrtf(s22));
                     float dn[5];
                     dn[0] = (sa.x - c2[0]) - c2[12];
                     dn[1] = (sa.y - c2[1]) - c2[13];
                     dn[2] = (sa.z - c2[2]) - c2[14];
                     dn[3] = g2 * u2;
                     dn[4] = g2 * v2;
-                    const float wr2 = (!oc2 && cz2 < 0.f) ? 0.f : wr;   // cut locus of the new chart
+                    const float wr2 = cut2 ? 0.f : wr;
 #pragma unroll
                     for (int a2 = 0; a2 < 5; ++a2) {
                         const float wa = wr2 * dn[a2];
