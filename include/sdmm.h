@@ -20,7 +20,12 @@
  *  - Calls are asynchronous on `stream`.  Argument errors are detected on the
  *    host before any launch and return SDMM_ERR_INVALID_ARG; nothing is
  *    launched then.  Launch failures return SDMM_ERR_CUDA.  A call never
- *    synchronises the stream, except sdmm_autotune and sdmm_fit_plan_timing.
+ *    synchronises the stream, except sdmm_autotune, sdmm_fit_plan_timing and
+ *    the kD-tree calls (said there).
+ *  - Tracing: with the environment variable SDMM_PROFILE=1 (read once per
+ *    process) the fit, objective, query, product and kD-tree entry points
+ *    time their launches with CUDA events, wait for them and print
+ *    "sdmm: <call> <ms> ms" to stderr; streams being captured are skipped.
  *  - Inputs (const pointers) are never modified.  sdmm_state is in/out.
  *  - The library allocates no device memory: all scratch is the caller's
  *    workspace, whose size sdmm_*_workspace_size reports.
@@ -419,6 +424,18 @@ sdmm_status sdmm_autotune(const sdmm_config *cfg, const sdmm_samples *s,
  * status (device int32): set to 1 if the MMA did not complete within 2 s.
  * (The paper has no counterpart: this checks the hardware path.)
  */
+/*
+ * Failure detection without a fault: the bounded mbarrier wait that every
+ * tensor-core wait of the E-step uses, on a barrier that completes only when
+ * `arrive` is non-zero.  With nobody arriving the wait gives up after
+ * limit_ns (1 .. 2e9), writes *status = 1 (device int32) and the elapsed time
+ * (*elapsed_ns, device int64) and the kernel returns normally, leaving the
+ * context usable; with an arrival *status = 0.  (The E-step reports the same
+ * event as region status SDMM_REGION_DEVICE_TIMEOUT.)  Asynchronous.
+ */
+sdmm_status sdmm_wait_selftest(int64_t limit_ns, int32_t arrive, int32_t *status,
+                               int64_t *elapsed_ns, sdmm_stream stream);
+
 sdmm_status sdmm_tc_selftest(int32_t kind, int32_t N, int32_t Kd,
                              const float *A, const float *B, float *D,
                              int32_t variant, int32_t *status,

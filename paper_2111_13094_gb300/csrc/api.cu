@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -15,6 +16,49 @@ using namespace sdmm;
 namespace {
 
 thread_local char g_err[512] = "";
+
+// SDMM_PROFILE=1 (environment): the main entry points record CUDA events
+// around their launches on their stream, wait for them and print
+// "sdmm: <call> <ms> ms" to stderr.  The calls are then synchronous; streams
+// that are being captured into a graph are left alone.
+bool profile_on() {
+    static const bool on = [] {
+        const char* v = std::getenv("SDMM_PROFILE");
+        return v != nullptr && v[0] != '\0' && v[0] != '0';
+    }();
+    return on;
+}
+
+struct ProfileScope {
+    const char* name;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr, b = nullptr;
+    ProfileScope(const char* n, sdmm_stream st) : name(n), s(static_cast<cudaStream_t>(st)) {
+        if (!profile_on()) return;
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+            cudaGetLastError();
+            return;
+        }
+        if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+            if (a) cudaEventDestroy(a);
+            a = b = nullptr;
+            cudaGetLastError();
+            return;
+        }
+        cudaEventRecord(a, s);
+    }
+    ~ProfileScope() {
+        if (!a) return;
+        cudaEventRecord(b, s);
+        float ms = 0.f;
+        if (cudaEventSynchronize(b) == cudaSuccess && cudaEventElapsedTime(&ms, a, b) == cudaSuccess)
+            std::fprintf(stderr, "sdmm: %s %.3f ms\n", name, ms);
+        cudaGetLastError();
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+    }
+};
 
 sdmm_status fail(sdmm_status code, const char* fmt, ...) {
     va_list ap;
@@ -336,6 +380,7 @@ sdmm_status sdmm_fit_workspace_size(const sdmm_config* cfg, int64_t R, int64_t N
 
 sdmm_status sdmm_init_regions(const sdmm_config* cfg, const sdmm_samples* s, const double* extent,
                               const double* uniforms, sdmm_state* st, sdmm_stream stream) {
+    ProfileScope prof_("init_regions", stream);
     sdmm_status e;
     if ((e = check_config(cfg)) || (e = check_samples(s)) || (e = check_state(st, true))) return e;
     if (!extent || !uniforms) return fail(SDMM_ERR_INVALID_ARG, "extent/uniforms are NULL");
@@ -347,6 +392,7 @@ sdmm_status sdmm_init_regions(const sdmm_config* cfg, const sdmm_samples* s, con
 sdmm_status sdmm_fit_regions(const sdmm_config* cfg, const sdmm_samples* s, int32_t iters,
                              const double* prior_scale, sdmm_state* st, float* loglik_out,
                              void* workspace, size_t ws_bytes, sdmm_stream stream) {
+    ProfileScope prof_("fit_regions", stream);
     sdmm_status e;
     if ((e = check_config(cfg)) || (e = check_samples(s)) || (e = check_state(st, true))) return e;
     if (iters < 1) return fail(SDMM_ERR_INVALID_ARG, "iters = %d must be >= 1", iters);
@@ -364,6 +410,7 @@ sdmm_status sdmm_fit_regions(const sdmm_config* cfg, const sdmm_samples* s, int3
 
 sdmm_status sdmm_prepare(const sdmm_config* cfg, int64_t R, sdmm_state* st, const double* logits,
                          const double* delta, sdmm_stream stream) {
+    ProfileScope prof_("prepare", stream);
     sdmm_status e;
     if ((e = check_config(cfg)) || (e = check_state(st, false))) return e;
     if (R < 1) return fail(SDMM_ERR_INVALID_ARG, "R = %lld", (long long)R);
@@ -410,6 +457,7 @@ static int query_grid(int64_t Q) {
 sdmm_status sdmm_condition(const sdmm_config* cfg, const sdmm_state* st, int64_t R, int64_t Q,
                            const float* qx, const int32_t* region, const sdmm_grid* grid,
                            float* cond_pi, float* cond_m, float* cond_L, sdmm_stream stream) {
+    ProfileScope prof_("condition", stream);
     GridF g;
     sdmm_status e = query_common(cfg, st, R, Q, qx, region, grid, &g);
     if (e) return e;
@@ -426,6 +474,7 @@ sdmm_status sdmm_sample(const sdmm_config* cfg, const sdmm_state* st, int64_t R,
                         const float* qx, const int32_t* region, const sdmm_grid* grid, uint64_t seed,
                         const float* uniforms, float* dir_out, float* pdf_out, uint8_t* valid_out,
                         sdmm_stream stream) {
+    ProfileScope prof_("sample", stream);
     GridF g;
     sdmm_status e = query_common(cfg, st, R, Q, qx, region, grid, &g);
     if (e) return e;
@@ -449,6 +498,7 @@ sdmm_status sdmm_product_sample(const sdmm_config* cfg, const sdmm_state* st, in
                                 const float* qx, const int32_t* region, const sdmm_grid* grid,
                                 const sdmm_bsdf_lobes* bsdf, uint64_t seed, const float* uniforms,
                                 float* dir_out, float* pdf_out, uint8_t* valid_out, sdmm_stream stream) {
+    ProfileScope prof_("product_sample", stream);
     GridF g;
     sdmm_status e = query_common(cfg, st, R, Q, qx, region, grid, &g);
     if (!e) e = bsdf_check(bsdf, Q);
@@ -465,6 +515,7 @@ sdmm_status sdmm_product_sample(const sdmm_config* cfg, const sdmm_state* st, in
 sdmm_status sdmm_product_pdf(const sdmm_config* cfg, const sdmm_state* st, int64_t R, int64_t Q, const float* qx,
                              const int32_t* region, const sdmm_grid* grid, const sdmm_bsdf_lobes* bsdf,
                              const float* dir, float* pdf_out, sdmm_stream stream) {
+    ProfileScope prof_("product_pdf", stream);
     GridF g;
     sdmm_status e = query_common(cfg, st, R, Q, qx, region, grid, &g);
     if (!e) e = bsdf_check(bsdf, Q);
@@ -480,6 +531,7 @@ sdmm_status sdmm_product_pdf(const sdmm_config* cfg, const sdmm_state* st, int64
 sdmm_status sdmm_pdf(const sdmm_config* cfg, const sdmm_state* st, int64_t R, int64_t Q,
                      const float* qx, const int32_t* region, const sdmm_grid* grid, const float* dir,
                      float* pdf_out, sdmm_stream stream) {
+    ProfileScope prof_("pdf", stream);
     GridF g;
     sdmm_status e = query_common(cfg, st, R, Q, qx, region, grid, &g);
     if (e) return e;
@@ -523,6 +575,7 @@ static sdmm_status objective_common(const sdmm_config* cfg, const sdmm_samples* 
 sdmm_status sdmm_objective(const sdmm_config* cfg, const sdmm_samples* s, const double* prior_scale,
                            const sdmm_state* st, double* F_out, void* workspace, size_t ws_bytes,
                            sdmm_stream stream) {
+    ProfileScope prof_("objective", stream);
     if (!F_out) return fail(SDMM_ERR_INVALID_ARG, "F_out is NULL");
     return objective_common(cfg, s, prior_scale, st, F_out, nullptr, nullptr, nullptr, nullptr,
                             workspace, ws_bytes, stream);
@@ -532,6 +585,7 @@ sdmm_status sdmm_objective_backward(const sdmm_config* cfg, const sdmm_samples* 
                                     const double* prior_scale, const sdmm_state* st, const double* dF,
                                     float* g_delta, float* g_L, float* g_logit, void* workspace,
                                     size_t ws_bytes, sdmm_stream stream) {
+    ProfileScope prof_("objective_backward", stream);
     if (!dF || !g_delta || !g_L || !g_logit) return fail(SDMM_ERR_INVALID_ARG, "dF/gradient outputs are NULL");
     return objective_common(cfg, s, prior_scale, st, nullptr, dF, g_delta, g_L, g_logit, workspace,
                             ws_bytes, stream);
@@ -625,6 +679,7 @@ sdmm_status sdmm_fit_plan_create(const sdmm_config* cfg, int64_t R, int64_t N_ma
 
 sdmm_status sdmm_fit_plan_run(sdmm_fit_plan* p, const sdmm_samples* s, const double* prior_scale,
                               float* loglik_out, sdmm_stream stream) {
+    ProfileScope prof_("fit_plan_run", stream);
     sdmm_status e;
     if (!p) return fail(SDMM_ERR_INVALID_ARG, "plan is NULL");
     if ((e = check_samples(s))) return e;
@@ -663,6 +718,7 @@ static bool on_device(const void* ptr) {
 
 sdmm_status sdmm_fit_plan_run_host(sdmm_fit_plan* p, const sdmm_samples* hs, void* staging, size_t staging_bytes,
                                    const double* prior_scale, float* loglik_out, sdmm_stream stream) {
+    ProfileScope prof_("fit_plan_run_host", stream);
     sdmm_status e;
     if (!p) return fail(SDMM_ERR_INVALID_ARG, "plan is NULL");
     if ((e = check_samples(hs))) return e;
@@ -764,6 +820,16 @@ sdmm_status sdmm_tc_selftest(int32_t kind, int32_t N, int32_t Kd, const float* A
     if (kind != 0 && (variant & 6)) return fail(SDMM_ERR_INVALID_ARG, "MN-major operands are tested for BF16 only");
     if (!A || !B || !D || !status) return fail(SDMM_ERR_INVALID_ARG, "NULL pointer");
     SDMM_CUDA(launch_tc_selftest(stream, kind, N, Kd, A, B, D, variant, status), "tc_selftest");
+    return SDMM_OK;
+}
+
+sdmm_status sdmm_wait_selftest(int64_t limit_ns, int32_t arrive, int32_t* status, int64_t* elapsed_ns,
+                               sdmm_stream stream) {
+    if (limit_ns < 1 || limit_ns > 2000000000ll) return fail(SDMM_ERR_INVALID_ARG, "limit_ns %lld: 1 .. 2e9", (long long)limit_ns);
+    if (!status || !elapsed_ns) return fail(SDMM_ERR_INVALID_ARG, "NULL pointer");
+    SDMM_CUDA(launch_wait_selftest(stream, (uint64_t)limit_ns, arrive != 0, status,
+                                   reinterpret_cast<unsigned long long*>(elapsed_ns)),
+              "wait_selftest");
     return SDMM_OK;
 }
 
@@ -1045,6 +1111,7 @@ static sdmm_status kd_run(sdmm_kdtree* t, int binning, int64_t c, const sdmm_sam
 
 sdmm_status sdmm_kdtree_bin(const sdmm_kdtree* t, const sdmm_samples* in, sdmm_sample_buffers* out, void* ws,
                             size_t ws_bytes, sdmm_stream stream) {
+    ProfileScope prof_("kdtree_bin", stream);
     sdmm_status e = kd_check(t);
     if (!e) e = kd_streams(in, out);
     if (e) return e;
@@ -1055,6 +1122,7 @@ sdmm_status sdmm_kdtree_bin(const sdmm_kdtree* t, const sdmm_samples* in, sdmm_s
 
 sdmm_status sdmm_kdtree_refine(sdmm_kdtree* t, int64_t c, const sdmm_samples* in, sdmm_sample_buffers* out,
                                int64_t* leaf_parent, void* ws, size_t ws_bytes, sdmm_stream stream) {
+    ProfileScope prof_("kdtree_refine", stream);
     sdmm_status e = kd_check(t);
     if (!e) e = kd_streams(in, out);
     if (e) return e;

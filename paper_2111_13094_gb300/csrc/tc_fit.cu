@@ -116,6 +116,34 @@ cudaError_t launch_tc_selftest(cudaStream_t s, int kind, int N, int Kd, const fl
     return cudaGetLastError();
 }
 
+// The bounded mbarrier wait of the E-step on a barrier that completes only if
+// `arrive` is set: with nobody arriving the wait gives up after limit_ns and
+// the kernel reports it (status 1) and returns normally.
+__global__ void __launch_bounds__(128) k_wait_selftest(uint64_t limit_ns, int arrive, int* __restrict__ status,
+                                                       unsigned long long* __restrict__ elapsed_ns) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&bar, 1);
+        tc::fence_mbar_init();
+    }
+    __syncthreads();
+    if (arrive && threadIdx.x == 0) tc::mbar_arrive(&bar);
+    const uint64_t t0 = tc::global_ns();
+    const bool ok = tc::mbar_wait_bounded(&bar, 0, limit_ns);
+    const uint64_t dt = tc::global_ns() - t0;
+    const int fail = __syncthreads_or(!ok);
+    if (threadIdx.x == 0) {
+        *status = fail ? 1 : 0;
+        *elapsed_ns = (unsigned long long)dt;
+    }
+}
+
+cudaError_t launch_wait_selftest(cudaStream_t s, uint64_t limit_ns, int arrive, int* status,
+                                 unsigned long long* elapsed_ns) {
+    k_wait_selftest<<<1, 128, 0, s>>>(limit_ns, arrive, status, elapsed_ns);
+    return cudaGetLastError();
+}
+
 // ===========================================================================
 // Contraction form of the E-step (derived from Sec. 3.1 Eq. log and the
 // 5-D Gaussian of Eq. em-ss-computation).  With A_k = [t_k; b_k] (the first

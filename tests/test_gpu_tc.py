@@ -63,3 +63,28 @@ def test_tc_swapped_offsets_are_detected():
     for variant in (1, 10):
         D, ref = _run(0, 96, 32, variant=variant)
         assert np.abs(D - ref).max() > 1.0
+
+
+def _wait(limit_ns, arrive):
+    st = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    el = torch.zeros(1, dtype=torch.int64, device="cuda")
+    lib = _lib.load()
+    s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    code = lib.sdmm_wait_selftest(limit_ns, arrive, ctypes.c_void_p(st.data_ptr()), ctypes.c_void_p(el.data_ptr()), s)
+    assert code == 0, lib.sdmm_last_error()
+    torch.cuda.synchronize()
+    return int(st.item()), int(el.item())
+
+
+def test_bounded_wait_gives_up_and_the_context_survives():
+    """The E-step's bounded mbarrier wait on a barrier nothing completes: it
+    gives up after its limit, reports it, and the GPU stays usable; with an
+    arrival it completes at once."""
+    status, elapsed = _wait(2_000_000, 0)            # 2 ms limit, nobody arrives
+    assert status == 1 and 2_000_000 <= elapsed < 1_000_000_000
+    status, elapsed = _wait(2_000_000, 1)
+    assert status == 0 and elapsed < 2_000_000
+    x = torch.arange(1024, device="cuda", dtype=torch.float32)   # the context still runs work
+    assert float(x.sum().item()) == 1024 * 1023 / 2
+    lib = _lib.load()
+    assert lib.sdmm_wait_selftest(0, 0, None, None, None) == 1   # argument errors come from the host
