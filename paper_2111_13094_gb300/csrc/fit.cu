@@ -736,112 +736,160 @@ __global__ void __launch_bounds__(128) k_reduce_objective(
 }
 
 // ---------------------------------------------------------------------------
-// Initialisation (Sec. 4.3 "Initialization", App. B, App. C), one thread per
-// region.  The weighted picks are sequential FP64 sums with explicit
-// round-to-nearest operations (no contraction), so that the chosen samples
-// are reproducible bit for bit.
-__device__ int64_t pick_index(const float* __restrict__ pw, const float* __restrict__ px,
-                              const float* __restrict__ py, const float* __restrict__ pz,
-                              int64_t o, int64_t M, const int64_t* seeds, int n_seeds, double u) {
-    auto weight = [&](int64_t i) {
-        double c = (double)pw[o + i];
-        c = c < 0.1 ? 0.1 : (c > 3.0 ? 3.0 : c);   // App. C: clamp to [W0, W1]
-        if (n_seeds == 0) return c;
-        double dmin = INFINITY;
-        for (int s = 0; s < n_seeds; ++s) {
-            const double dx = __dsub_rn((double)px[o + i], (double)px[o + seeds[s]]);
-            const double dy = __dsub_rn((double)py[o + i], (double)py[o + seeds[s]]);
-            const double dz = __dsub_rn((double)pz[o + i], (double)pz[o + seeds[s]]);
-            const double dd = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)),
-                                                   __dmul_rn(dz, dz)));
-            dmin = dd < dmin ? dd : dmin;
-        }
-        return __dmul_rn(c, dmin);
-    };
-    double tot = 0.0;
-    for (int64_t i = 0; i < M; ++i) tot = __dadd_rn(tot, weight(i));
-    if (!(tot > 0.0)) return -1;
-    const double t = __dmul_rn(u, tot);
-    double cum = 0.0;
-    int64_t last = -1;
-    for (int64_t i = 0; i < M; ++i) {
-        const double p = weight(i);
-        cum = __dadd_rn(cum, p);
-        if (p > 0.0) last = i;
-        if (t < cum) return i;
+// Initialisation (Sec. 4.3 "Initialization", App. B, App. C), one CTA per
+// region.  The weighted picks are sums in sample order with explicit
+// round-to-nearest FP64 operations (no contraction), so that the chosen
+// samples are reproducible bit for bit: the CTA computes the weights of a
+// chunk of samples in parallel and one thread adds them in order.
+constexpr int kInitThreads = 128, kInitChunk = 8 * kInitThreads;
+
+__device__ __forceinline__ double pick_weight(const float* __restrict__ pw, const float* __restrict__ px,
+                                              const float* __restrict__ py, const float* __restrict__ pz,
+                                              int64_t o, int64_t i, const int64_t* seeds, int n_seeds) {
+    double c = (double)pw[o + i];
+    c = c < 0.1 ? 0.1 : (c > 3.0 ? 3.0 : c);   // App. C: clamp to [W0, W1]
+    if (n_seeds == 0) return c;
+    double dmin = INFINITY;
+    for (int s = 0; s < n_seeds; ++s) {
+        const double dx = __dsub_rn((double)px[o + i], (double)px[o + seeds[s]]);
+        const double dy = __dsub_rn((double)py[o + i], (double)py[o + seeds[s]]);
+        const double dz = __dsub_rn((double)pz[o + i], (double)pz[o + seeds[s]]);
+        const double dd = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
+        dmin = dd < dmin ? dd : dmin;
     }
-    return last;
+    return __dmul_rn(c, dmin);
 }
 
-__global__ void k_init_regions(sdmm_config cfg, BatchDesc d, const double* __restrict__ extent,
-                               const double* __restrict__ uniforms, sdmm_state st) {
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= d.R) return;
+// the first i with u * sum(w) < w_0 + ... + w_i (the last positive weight if
+// rounding leaves none), -1 if all weights vanish; every thread returns it
+__device__ int64_t pick_index_cta(const float* __restrict__ pw, const float* __restrict__ px,
+                                  const float* __restrict__ py, const float* __restrict__ pz, int64_t o,
+                                  int64_t M, const int64_t* seeds, int n_seeds, double u, double* s_w,
+                                  double* s_acc, int64_t* s_pick) {
+    const int tid = threadIdx.x;
+    // pass 1: the total, in sample order
+    if (tid == 0) *s_acc = 0.0;
+    for (int64_t c0 = 0; c0 < M; c0 += kInitChunk) {
+        const int n = (int)min((int64_t)kInitChunk, M - c0);
+        for (int q = tid; q < n; q += kInitThreads) s_w[q] = pick_weight(pw, px, py, pz, o, c0 + q, seeds, n_seeds);
+        __syncthreads();
+        if (tid == 0) {
+            double a = *s_acc;
+            for (int q = 0; q < n; ++q) a = __dadd_rn(a, s_w[q]);
+            *s_acc = a;
+        }
+        __syncthreads();
+    }
+    const double tot = *s_acc;
+    __syncthreads();
+    if (!(tot > 0.0)) return -1;
+    // pass 2: the first cumulative sum above u * total
+    const double th = __dmul_rn(u, tot);
+    if (tid == 0) {
+        *s_acc = 0.0;
+        s_pick[0] = -1;       // the answer
+        s_pick[1] = -1;       // last index with a positive weight
+    }
+    __syncthreads();
+    for (int64_t c0 = 0; c0 < M; c0 += kInitChunk) {
+        const int n = (int)min((int64_t)kInitChunk, M - c0);
+        for (int q = tid; q < n; q += kInitThreads) s_w[q] = pick_weight(pw, px, py, pz, o, c0 + q, seeds, n_seeds);
+        __syncthreads();
+        if (tid == 0) {
+            double a = *s_acc;
+            for (int q = 0; q < n; ++q) {
+                a = __dadd_rn(a, s_w[q]);
+                if (s_w[q] > 0.0) s_pick[1] = c0 + q;
+                if (th < a) {
+                    s_pick[0] = c0 + q;
+                    break;
+                }
+            }
+            *s_acc = a;
+        }
+        __syncthreads();
+        if (s_pick[0] >= 0) break;                    // (uniform: read after the barrier)
+    }
+    const int64_t r = s_pick[0] >= 0 ? s_pick[0] : s_pick[1];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kInitThreads) k_init_regions(sdmm_config cfg, BatchDesc d,
+                                                               const double* __restrict__ extent,
+                                                               const double* __restrict__ uniforms, sdmm_state st) {
+    __shared__ double s_w[kInitChunk];
+    __shared__ double s_acc;
+    __shared__ int64_t s_pick[2];
+    __shared__ int64_t seeds[SDMM_MAX_K / 8 > 0 ? SDMM_MAX_K / 8 : 1];
+    const int64_t r = blockIdx.x;
+    const int tid = threadIdx.x;
     const int K = cfg.K;
     const int n_pos = (K % 8 == 0) ? K / 8 : 1;
     const int n_dir = K / n_pos;
     const int64_t o = d.offsets[r], M = d.offsets[r + 1] - d.offsets[r];
-    st.n_seen[r] = 0;
-    st.step_j[r] = 0;
-    st.Wbar[r] = 0.0;
-    for (int k = 0; k < K; ++k) {
-        st.S0[r * K + k] = 0.0;
-        for (int p = 0; p < 15; ++p) st.S2[(r * K + k) * 15 + p] = 0.0;
+    if (tid == 0) {
+        st.n_seen[r] = 0;
+        st.step_j[r] = 0;
+        st.Wbar[r] = 0.0;
+    }
+    for (int e = tid; e < K * 16; e += kInitThreads) {
+        const int k = e / 16, p = e % 16;
+        if (p == 15) st.S0[r * K + k] = 0.0;
+        else st.S2[(r * K + k) * 15 + p] = 0.0;
     }
     if (!(o >= 0 && M >= 0 && d.offsets[r + 1] <= d.N)) {
-        st.status[r] = SDMM_REGION_BAD_OFFSETS;
+        if (tid == 0) st.status[r] = SDMM_REGION_BAD_OFFSETS;
         return;
     }
     if (M < cfg.min_samples || M <= 0) {
-        st.status[r] = SDMM_REGION_SKIPPED;
+        if (tid == 0) st.status[r] = SDMM_REGION_SKIPPED;
         return;
     }
-    int64_t seeds[SDMM_MAX_K / 8 > 0 ? SDMM_MAX_K / 8 : 1];
     const float* px = d.p[0];
     const float* py = d.p[1];
     const float* pz = d.p[2];
     const float* pw = d.p[6];
     for (int j = 0; j < n_pos; ++j) {
-        const int64_t s = pick_index(pw, px, py, pz, o, M, seeds, j, uniforms[r * n_pos + j]);
-        seeds[j] = (s < 0) ? (j > 0 ? seeds[0] : 0) : s;
+        const int64_t s = pick_index_cta(pw, px, py, pz, o, M, seeds, j, uniforms[r * n_pos + j], s_w, &s_acc, s_pick);
+        if (tid == 0) seeds[j] = (s < 0) ? (j > 0 ? seeds[0] : 0) : s;
+        __syncthreads();
     }
     const double rst = 2.0 * extent[r] / n_pos;            // App. B: r_st = 2 d / n_pos
     const double sx = rst / sqrt(kChi2_3_q90);
     const double sw = sqrt(kTwoPi / n_dir);                  // App. B: sigma^2 = 2 pi / n_dir
-    for (int j = 0; j < n_pos; ++j) {
-        for (int t = 0; t < n_dir; ++t) {
-            const int64_t rk = r * K + j * n_dir + t;
-            double dv[3];
-            if (n_dir == 8) {
-                const double hh = 1.0 / sqrt(3.0);
-                dv[0] = (t & 1) ? -hh : hh;
-                dv[1] = (t & 2) ? -hh : hh;
-                dv[2] = (t & 4) ? -hh : hh;
-            } else {
-                const double ga = 3.141592653589793238462643383279502884 * (3.0 - sqrt(5.0));
-                const double z = 1.0 - (2.0 * t + 1.0) / n_dir;
-                const double rad = sqrt(1.0 - z * z);
-                dv[0] = rad * cos(ga * t);
-                dv[1] = rad * sin(ga * t);
-                dv[2] = z;
-            }
-            double mx[3] = {(double)px[o + seeds[j]], (double)py[o + seeds[j]],
-                            (double)pz[o + seeds[j]]};
-            double L[15];
-            for (int p = 0; p < 15; ++p) L[p] = 0.0;
-            for (int c = 0; c < 3; ++c) L[pk(c, c)] = sx;
-            for (int c = 3; c < 5; ++c) L[pk(c, c)] = sw;
-            st.pi[rk] = 1.0 / K;
-            for (int c = 0; c < 3; ++c) {
-                st.mu_x[rk * 3 + c] = mx[c];
-                st.mu_w[rk * 3 + c] = dv[c];
-            }
-            for (int p = 0; p < 15; ++p) st.L[rk * 15 + p] = L[p];
-            write_records(1.0 / K, mx, dv, L, st.etab + rk * kE, st.qtab + rk * kQ, nullptr,
-                          cfg.dir_coords == SDMM_DIR_EUCLIDEAN);
+    for (int kk = tid; kk < K; kk += kInitThreads) {
+        const int j = kk / n_dir, t = kk % n_dir;
+        const int64_t rk = r * K + kk;
+        double dv[3];
+        if (n_dir == 8) {
+            const double hh = 1.0 / sqrt(3.0);
+            dv[0] = (t & 1) ? -hh : hh;
+            dv[1] = (t & 2) ? -hh : hh;
+            dv[2] = (t & 4) ? -hh : hh;
+        } else {
+            const double ga = 3.141592653589793238462643383279502884 * (3.0 - sqrt(5.0));
+            const double z = 1.0 - (2.0 * t + 1.0) / n_dir;
+            const double rad = sqrt(1.0 - z * z);
+            dv[0] = rad * cos(ga * t);
+            dv[1] = rad * sin(ga * t);
+            dv[2] = z;
         }
+        double mx[3] = {(double)px[o + seeds[j]], (double)py[o + seeds[j]], (double)pz[o + seeds[j]]};
+        double L[15];
+        for (int p = 0; p < 15; ++p) L[p] = 0.0;
+        for (int c = 0; c < 3; ++c) L[pk(c, c)] = sx;
+        for (int c = 3; c < 5; ++c) L[pk(c, c)] = sw;
+        st.pi[rk] = 1.0 / K;
+        for (int c = 0; c < 3; ++c) {
+            st.mu_x[rk * 3 + c] = mx[c];
+            st.mu_w[rk * 3 + c] = dv[c];
+        }
+        for (int p = 0; p < 15; ++p) st.L[rk * 15 + p] = L[p];
+        write_records(1.0 / K, mx, dv, L, st.etab + rk * kE, st.qtab + rk * kQ, nullptr,
+                      cfg.dir_coords == SDMM_DIR_EUCLIDEAN);
     }
-    st.status[r] = SDMM_REGION_OK;
+    if (tid == 0) st.status[r] = SDMM_REGION_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -956,8 +1004,7 @@ cudaError_t launch_reduce_objective(cudaStream_t s, int64_t R, const WsHeader* w
 
 cudaError_t launch_init(cudaStream_t s, int64_t R, const sdmm_config& cfg, const BatchDesc& d,
                         const double* extent, const double* uniforms, const sdmm_state& st) {
-    const unsigned blocks = (unsigned)((R + 127) / 128);
-    k_init_regions<<<blocks, 128, 0, s>>>(cfg, d, extent, uniforms, st);
+    k_init_regions<<<(unsigned)R, kInitThreads, 0, s>>>(cfg, d, extent, uniforms, st);
     return cudaGetLastError();
 }
 
