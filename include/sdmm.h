@@ -425,6 +425,16 @@ sdmm_status sdmm_autotune(const sdmm_config *cfg, const sdmm_samples *s,
  * (The paper has no counterpart: this checks the hardware path.)
  */
 /*
+ * Input validation (the fit itself does not check samples): counts[0] =
+ * samples whose direction is not unit length within unit_tol (|w|^2 - 1
+ * beyond 2 unit_tol), counts[1] = weights negative or not finite, counts[2] =
+ * positions not finite; counts is device int64[3], overwritten.  offsets and
+ * R are not used.  Asynchronous.
+ */
+sdmm_status sdmm_validate_samples(const sdmm_samples *s, float unit_tol, int64_t *counts,
+                                  sdmm_stream stream);
+
+/*
  * Failure detection without a fault: the bounded mbarrier wait that every
  * tensor-core wait of the E-step uses, on a barrier that completes only when
  * `arrive` is non-zero.  With nobody arriving the wait gives up after

@@ -24,7 +24,7 @@ SYMBOLS = ["sdmm_config_default", "sdmm_last_error", "sdmm_version", "sdmm_fit_w
            "sdmm_fit_plan_create", "sdmm_fit_plan_run", "sdmm_fit_plan_enable_timing",
            "sdmm_fit_plan_staging_size", "sdmm_fit_plan_run_host",
            "sdmm_fit_plan_timing", "sdmm_fit_plan_destroy", "sdmm_autotune",
-           "sdmm_fit_regions_noalloc", "sdmm_tc_selftest", "sdmm_wait_selftest", "sdmm_kdtree_grid", "sdmm_kdtree_lookup",
+           "sdmm_fit_regions_noalloc", "sdmm_tc_selftest", "sdmm_wait_selftest", "sdmm_validate_samples", "sdmm_kdtree_grid", "sdmm_kdtree_lookup",
            "sdmm_kdtree_workspace_size", "sdmm_kdtree_bin", "sdmm_kdtree_refine", "sdmm_gather_regions",
            "sdmm_product_sample", "sdmm_product_pdf"]
 
@@ -112,6 +112,7 @@ def _declare(L):
         "sdmm_fit_regions_noalloc": [_PC, _PSm, _I32, _P, _PS, _P, _P],
         "sdmm_tc_selftest": [_I32, _I32, _I32, _P, _P, _P, _I32, _P, _P],
         "sdmm_wait_selftest": [ctypes.c_int64, _I32, _P, _P, _P],
+        "sdmm_validate_samples": [_PSm, ctypes.c_float, _P, _P],
         "sdmm_kdtree_grid": [ctypes.POINTER(KdTree), _I32, _P],
         "sdmm_kdtree_lookup": [ctypes.POINTER(KdTree), _I64, _P, _P, _P, _P, _P],
         "sdmm_kdtree_workspace_size": [ctypes.POINTER(KdTree), _I64, ctypes.POINTER(ctypes.c_size_t)],

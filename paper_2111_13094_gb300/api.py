@@ -213,6 +213,16 @@ def workspace(cfg, R: int, N: int, device="cuda") -> torch.Tensor:
     return torch.empty(workspace_bytes(cfg, R, N), dtype=torch.uint8, device=device)
 
 
+def validate_samples(batch: SampleBatch, unit_tol=1e-5, stream=None):
+    """Counts of bad samples: (directions not unit length within unit_tol,
+    weights negative or not finite, positions not finite), int64 on the device."""
+    counts = torch.empty(3, dtype=torch.int64, device=batch.samples.device)
+    sm = batch.c()
+    check(_lib.load().sdmm_validate_samples(ctypes.byref(sm), float(unit_tol), _ptr(counts), _stream(stream)),
+          "sdmm_validate_samples")
+    return counts
+
+
 def init_regions(cfg, batch: SampleBatch, extent, uniforms, state: MixtureState, stream=None):
     sm = batch.c()
     st = state.c()

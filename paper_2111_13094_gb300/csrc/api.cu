@@ -823,6 +823,22 @@ sdmm_status sdmm_tc_selftest(int32_t kind, int32_t N, int32_t Kd, const float* A
     return SDMM_OK;
 }
 
+sdmm_status sdmm_validate_samples(const sdmm_samples* s, float unit_tol, int64_t* counts, sdmm_stream stream) {
+    if (!s) return fail(SDMM_ERR_INVALID_ARG, "samples is NULL");
+    if (s->N < 0) return fail(SDMM_ERR_INVALID_ARG, "N = %lld", (long long)s->N);
+    if (s->N > 0 && (!s->px || !s->py || !s->pz || !s->ox || !s->oy || !s->oz || !s->w))
+        return fail(SDMM_ERR_INVALID_ARG, "sample streams are NULL");
+    if (!counts) return fail(SDMM_ERR_INVALID_ARG, "counts is NULL");
+    if (!(unit_tol > 0.f) || !(unit_tol < 1.f)) return fail(SDMM_ERR_INVALID_ARG, "unit_tol must be in (0, 1)");
+    ProfileScope prof_("validate_samples", stream);
+    BatchDesc d{};
+    d.p[0] = s->px; d.p[1] = s->py; d.p[2] = s->pz; d.p[3] = s->ox; d.p[4] = s->oy; d.p[5] = s->oz; d.p[6] = s->w;
+    SDMM_CUDA(launch_validate(static_cast<cudaStream_t>(stream), d, s->N, unit_tol,
+                              reinterpret_cast<unsigned long long*>(counts), std::max(1, sm_count()) * 4),
+              "validate_samples");
+    return SDMM_OK;
+}
+
 sdmm_status sdmm_wait_selftest(int64_t limit_ns, int32_t arrive, int32_t* status, int64_t* elapsed_ns,
                                sdmm_stream stream) {
     if (limit_ns < 1 || limit_ns > 2000000000ll) return fail(SDMM_ERR_INVALID_ARG, "limit_ns %lld: 1 .. 2e9", (long long)limit_ns);

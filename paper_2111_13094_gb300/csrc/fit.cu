@@ -917,6 +917,42 @@ __global__ void k_prepare(int K, int64_t R, sdmm_state st, const double* __restr
 }
 
 // ---------------------------------------------------------------------------
+// Input validation: counts of samples whose direction is not unit length
+// within tol, whose weight is negative or not finite, or whose position is
+// not finite (three int64 counters, accumulated per CTA, then once per CTA).
+__global__ void __launch_bounds__(256) k_validate(BatchDesc d, int64_t N, float tol,
+                                                  unsigned long long* __restrict__ counts) {
+    __shared__ unsigned int s_c[3];
+    if (threadIdx.x < 3) s_c[threadIdx.x] = 0u;
+    __syncthreads();
+    unsigned int c[3] = {0u, 0u, 0u};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const float ox = d.p[3][i], oy = d.p[4][i], oz = d.p[5][i], w = d.p[6][i];
+        const float n2 = ox * ox + oy * oy + oz * oz;
+        c[0] += !(fabsf(n2 - 1.f) <= 2.f * tol);                 // |w|^2 - 1 ~ 2 (|w| - 1)
+        c[1] += !(w >= 0.f && isfinite(w));
+        c[2] += !(isfinite(d.p[0][i]) && isfinite(d.p[1][i]) && isfinite(d.p[2][i]));
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        unsigned int v = c[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0 && v) atomicAdd(&s_c[q], v);
+    }
+    __syncthreads();
+    if (threadIdx.x < 3 && s_c[threadIdx.x]) atomicAdd(counts + threadIdx.x, (unsigned long long)s_c[threadIdx.x]);
+}
+
+cudaError_t launch_validate(cudaStream_t s, const BatchDesc& d, int64_t N, float tol, unsigned long long* counts,
+                            int grid) {
+    cudaError_t e = cudaMemsetAsync(counts, 0, 3 * sizeof(unsigned long long), s);
+    if (e != cudaSuccess || N == 0) return e;
+    k_validate<<<grid, 256, 0, s>>>(d, N, tol, counts);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // Host-side launch helpers (declared in kernels.h)
 template <int MODE>
 static cudaError_t launch_acc_mode(int KP, dim3 grid, cudaStream_t s, WsHeader* ws,

@@ -57,6 +57,8 @@ cudaError_t launch_query(cudaStream_t s, int op, int KP, int grid, const float* 
                          float* cond_pi, float* cond_m, float* cond_L, float* dir_out,
                          float* pdf_out, uint8_t* valid_out);
 
+cudaError_t launch_validate(cudaStream_t s, const BatchDesc& d, int64_t N, float tol, unsigned long long* counts,
+                            int grid);
 cudaError_t launch_wait_selftest(cudaStream_t s, uint64_t limit_ns, int arrive, int* status,
                                  unsigned long long* elapsed_ns);
 cudaError_t launch_tc_selftest(cudaStream_t s, int kind, int N, int Kd, const float* A, const float* B,
