@@ -117,6 +117,7 @@ __global__ void __launch_bounds__(kWarps * 32, MODE == MODE_TWO ? 1 : 2)
     constexpr int NS = MODE == MODE_TWO ? 15 : kStat;   // statistics per component
     constexpr int RED = KP * kStat + 4;
     __shared__ __align__(16) float sbuf[kWarps][32][8];
+    __shared__ float2 s_lse[kWarps][32];   // per sample of the batch: (sum of exp, shift)
     __shared__ float red[kWarps][RED];
     __shared__ int s_c;
 
@@ -206,6 +207,7 @@ __global__ void __launch_bounds__(kWarps * 32, MODE == MODE_TWO ? 1 : 2)
             }
             *reinterpret_cast<float4*>(&sbuf[warp][lane][0]) = a;
             *reinterpret_cast<float4*>(&sbuf[warp][lane][4]) = b;
+            const float my_w = a.w;                 // weight of sample g + lane (0 past the unit)
             __syncwarp();
             const int n = (int)min((int64_t)32, end - g);
 #pragma unroll 2
@@ -262,10 +264,8 @@ __global__ void __launch_bounds__(kWarps * 32, MODE == MODE_TWO ? 1 : 2)
                 const float rr = (se > 0.f) ? __fdividef(e, se) : 0.f;
                 const float wt = sa.w;
                 const float wr = wt * rr;
-                const float li = (se > 0.f) ? ref + __logf(se) : -INFINITY;
-                wsum += wt;
-                wll += (wt > 0.f) ? wt * li : 0.f;
-                if (loglik != nullptr && k == 0 && j < n) loglik[g + j] = li;
+                // the sample's log-likelihood is formed once per batch, below
+                if (MODE != MODE_TWO && k == 0) s_lse[warp][j] = make_float2(se, ref);
                 if (MODE == MODE_TWO) {
                     // the sample in the chart of the new mean: same log map, new centre
                     const float u2 = c2[3] * sb.x + c2[4] * sb.y + c2[5] * sb.z;
@@ -312,12 +312,26 @@ __global__ void __launch_bounds__(kWarps * 32, MODE == MODE_TWO ? 1 : 2)
                 }
             }
             __syncwarp();
+            if (MODE != MODE_TWO) {
+                // lane i: log-likelihood, weight and weighted log-likelihood of sample g + i
+                const float2 q = s_lse[warp][lane];
+                if (lane < n) {
+                    const float li = (q.x > 0.f) ? q.y + __logf(q.x) : -INFINITY;
+                    wsum += my_w;
+                    wll += (my_w > 0.f) ? my_w * li : 0.f;
+                    if (loglik != nullptr) loglik[g + lane] = li;
+                }
+                __syncwarp();
+            }
         }
-        // combine the SPI sample slots of each component
+        // combine the SPI sample slots of each component; W and sum w l over all lanes
 #pragma unroll
         for (int o = KP; o < 32; o <<= 1) {
 #pragma unroll
             for (int s = 0; s < NS; ++s) acc[s] += __shfl_xor_sync(0xffffffffu, acc[s], o);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
             wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
             wll += __shfl_xor_sync(0xffffffffu, wll, o);
         }
