@@ -106,6 +106,11 @@ __global__ void __launch_bounds__(1024) k_build_chunks(WsHeader* ws, int64_t* ch
 //           the chart of each component's new mean mu' (chart2 records) and
 //           accumulates only w r d' d'^T.
 constexpr int kWarps = 8;
+// A sum of exp(l - region bound) below kLseMin means every component lies more
+// than ~69 below the bound, near the bottom of the FP32 range where the
+// exponentials are flushed or held at the smallest normal: the sum then says
+// nothing about the sample, and the exact per-sample maximum is used instead.
+constexpr float kLseMin = 1e-30f;
 
 template <int KP, int MODE>
 __global__ void __launch_bounds__(kWarps * 32, MODE == MODE_TWO ? 1 : 2)
@@ -210,9 +215,13 @@ __global__ void __launch_bounds__(kWarps * 32, MODE == MODE_TWO ? 1 : 2)
             const float my_w = a.w;                 // weight of sample g + lane (0 past the unit)
             __syncwarp();
             const int n = (int)min((int64_t)32, end - g);
-#pragma unroll 2
-            for (int t = 0; t < n; t += SPI) {
-                const int j = t + h;
+            // one (sample j, this lane's component) pair: log-likelihood, the
+            // sample's log-sum-exp over the component lanes, statistics.
+            // lse: 0 = shift by the region bound, the exact maximum when that
+            // underflows (a warp vote); 1 = the bound only (an underflowing
+            // sample gets no statistics and is redone after the batch);
+            // 2 = the exact maximum.  act = false: weight 0 (idle slot).
+            auto pair = [&](const int j, const bool act, const int lse) {
                 const float4 sa = *reinterpret_cast<const float4*>(&sbuf[warp][j][0]);
                 const float4 sb = *reinterpret_cast<const float4*>(&sbuf[warp][j][4]);
                 // log map at this lane's component (Sec. 3.1 Eq. log); the
@@ -244,15 +253,15 @@ __global__ void __launch_bounds__(kWarps * 32, MODE == MODE_TWO ? 1 : 2)
                 float l = prm[27] - 0.5f * q;
                 if (density) l += __logf(gg);
                 if (cut) l = -INFINITY;
-                // log-sum-exp over the KP component lanes of this sample, shifted
-                // by the region bound; the exact per-sample maximum is used only
-                // when that underflows (or when the bound does not hold)
-                float ref = lmax;
-                float e = __expf(l - ref);
-                float se = e;
+                // log-sum-exp over the KP component lanes of this sample
+                float ref = lmax, e = 0.f, se = 0.f;
+                if (lse != 2) {
+                    e = __expf(l - ref);
+                    se = e;
 #pragma unroll
-                for (int o = KP / 2; o > 0; o >>= 1) se += __shfl_xor_sync(0xffffffffu, se, o);
-                if (__any_sync(0xffffffffu, !(se > 0.f) || se > 1e30f || density)) {
+                    for (int o = KP / 2; o > 0; o >>= 1) se += __shfl_xor_sync(0xffffffffu, se, o);
+                }
+                if (lse == 2 || (lse == 0 && __any_sync(0xffffffffu, !(se >= kLseMin) || se > 1e30f || density))) {
                     ref = l;
 #pragma unroll
                     for (int o = KP / 2; o > 0; o >>= 1) ref = fmaxf(ref, __shfl_xor_sync(0xffffffffu, ref, o));
@@ -261,11 +270,11 @@ __global__ void __launch_bounds__(kWarps * 32, MODE == MODE_TWO ? 1 : 2)
 #pragma unroll
                     for (int o = KP / 2; o > 0; o >>= 1) se += __shfl_xor_sync(0xffffffffu, se, o);
                 }
-                const float rr = (se > 0.f) ? __fdividef(e, se) : 0.f;
-                const float wt = sa.w;
+                const float rr = (se >= kLseMin) ? __fdividef(e, se) : 0.f;
+                const float wt = act ? sa.w : 0.f;
                 const float wr = wt * rr;
                 // the sample's log-likelihood is formed once per batch, below
-                if (MODE != MODE_TWO && k == 0) s_lse[warp][j] = make_float2(se, ref);
+                if (MODE != MODE_TWO && k == 0 && act) s_lse[warp][j] = make_float2(se, ref);
                 if (MODE == MODE_TWO) {
                     // the sample in the chart of the new mean: same log map, new centre
                     const float u2 = c2[3] * sb.x + c2[4] * sb.y + c2[5] * sb.z;
@@ -287,7 +296,7 @@ __global__ void __launch_bounds__(kWarps * 32, MODE == MODE_TWO ? 1 : 2)
 #pragma unroll
                         for (int b2 = 0; b2 <= a2; ++b2) acc[pk(a2, b2)] += wa * dn[b2];
                     }
-                    continue;
+                    return;
                 }
                 float x[5];
                 if (MODE == MODE_FIT) {
@@ -309,6 +318,28 @@ __global__ void __launch_bounds__(kWarps * 32, MODE == MODE_TWO ? 1 : 2)
                     acc[1 + a2] += wa;
 #pragma unroll
                     for (int b2 = 0; b2 <= a2; ++b2) acc[6 + pk(a2, b2)] += wa * d[b2];
+                }
+            };
+            // the plain fit defers underflowing samples (rare: every component
+            // below the region bound by more than ~87 in log) instead of
+            // voting on every sample
+            const bool defer = MODE == MODE_FIT && !density;
+#pragma unroll 2
+            for (int t = 0; t < n; t += SPI) pair(t + h, true, defer ? 1 : 0);
+            if (defer) {
+                __syncwarp();
+                unsigned redo = __ballot_sync(0xffffffffu, lane < n && !(s_lse[warp][lane].x >= kLseMin));
+                while (redo) {
+                    // slot h takes the h-th lowest flagged sample
+                    unsigned m = redo;
+                    int jj = -1;
+                    for (int hh = 0; hh <= h && m; ++hh) {
+                        jj = __ffs(m) - 1;
+                        m &= m - 1u;
+                        if (hh < h && !m) jj = -1;
+                    }
+                    for (int hh = 0; hh < SPI && redo; ++hh) redo &= redo - 1u;
+                    pair(jj >= 0 ? jj : 0, jj >= 0, 2);
                 }
             }
             __syncwarp();
