@@ -44,7 +44,7 @@ BYTES_PER_SAMPLE = 28
 # capture of a 512-region launch of the same kernel (traffic grows with the
 # samples processed, so a full launch moves this times N); None for kernels
 # without a capture of their current version
-DRAM_BYTES_PER_SAMPLE = {"k_accumulate<16,FIT>": 29.1}
+DRAM_BYTES_PER_SAMPLE = {"k_accumulate<16,FIT>": 29.0}
 
 
 # ---- multi-rank helpers (one process per GPU under torchrun; every rank fits
