@@ -297,7 +297,7 @@ sdmm_status enqueue_fit(const FitLaunch& f, cudaStream_t s, std::vector<cudaEven
         if (f.w.partial2 != nullptr) {   // accurate covariance update: second pass in the new charts
             SDMM_CUDA(launch_new_charts(s, f.R, f.w.hdr, f.w.cb, f.w.partial, f.L.ps, f.cfg, f.st, f.w.chart2),
                       "new_charts");
-            SDMM_CUDA(launch_accumulate(s, MODE_TWO, KP, std::max(1, sm_count()), f.w.hdr, f.w.cb, f.w.cr,
+            SDMM_CUDA(launch_accumulate(s, MODE_TWO, KP, f.grid, f.w.hdr, f.w.cb, f.w.cr,
                                         f.st.etab, f.cfg.K, f.L.chunk, f.cfg.estep_density, f.w.partial2,
                                         f.L.ps2, 0, f.w.chart2),
                       "accumulate_two");

@@ -113,7 +113,7 @@ constexpr int kWarps = 8;
 constexpr float kLseMin = 1e-30f;
 
 template <int KP, int MODE>
-__global__ void __launch_bounds__(kWarps * 32, MODE == MODE_TWO ? 1 : 2)
+__global__ void __launch_bounds__(kWarps * 32, 2)
     k_accumulate(WsHeader* __restrict__ ws, const int64_t* __restrict__ chunk_base,
                  const int32_t* __restrict__ chunk_region, const float* __restrict__ etab, int K,
                  int chunk, int density, float* __restrict__ partial, int ps, int write_ll,
