@@ -19,7 +19,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libsdmm.so")
-SOURCES = ["fit.cu", "query.cu", "tc_fit.cu", "kdtree.cu", "product.cu", "api.cu"]
+SOURCES = ["fit.cu", "estep.cu", "query.cu", "tc_fit.cu", "kdtree.cu", "product.cu", "api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 

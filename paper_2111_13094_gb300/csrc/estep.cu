@@ -1,0 +1,317 @@
+// estep.cu -- E-step + statistics of the plain fit on the CUDA cores (sm_103a):
+// the tangent-space (chart) density of Sec. 3.2 Eq. (em-ss-computation) with
+// the log map of Sec. 3.1 Eq. (log), one lane per mixture component.
+//
+// This is the specialisation of k_accumulate<KP, MODE_FIT> for the chart
+// density and tangent charts (the default configuration and the batched fit's
+// whole E-step).  It computes the same quantities with less work per
+// (sample, component) pair:
+//   * base 2 throughout: L^-1 is scaled by sqrt(log2(e) / 2) when a region's
+//     records are loaded, so the Mahalanobis sum of squares is already the
+//     base-2 exponent, and the per-component constant c5 is stored shifted by
+//     the region bound (the largest c5 of the region, which no component's
+//     chart density can exceed), so exp(l - bound) is one ex2;
+//   * positions relative to a per-unit reference point (the region's first
+//     spatial mean, FP32): the sample's offset is formed once per sample when
+//     it is staged, each component's mean offset once per region, so the pair
+//     needs one subtraction per coordinate, with no hi/lo correction;
+//   * two samples per lane in flight (samples t + h and t + SPI + h), so the
+//     two log-sum-exp butterflies and the two MUFU chains overlap;
+//   * the next batch of 32 samples is loaded while the current one is processed.
+// Samples whose shifted sum underflows (every component more than ~69 below
+// the region bound) get no statistics in the pass and are redone after their
+// batch with the exact per-sample maximum, as in k_accumulate.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace sdmm {
+
+namespace {
+constexpr int kEW = 8;                          // warps per CTA
+constexpr float kLog2eF = 1.44269504088896341f;
+constexpr float kLn2F = 0.693147180559945309f;
+constexpr float kHalfLog2eSqrt = 0.849321800288019f;   // sqrt(log2(e) / 2)
+constexpr float kSumMin = 1e-30f;               // smallest trusted shifted sum
+
+__device__ __forceinline__ float ex2f(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+}  // namespace
+
+template <int KP>
+__global__ void __launch_bounds__(kEW * 32, 2)
+    k_estep(WsHeader* __restrict__ ws, const int64_t* __restrict__ chunk_base,
+            const int32_t* __restrict__ chunk_region, const float* __restrict__ etab, int K, int chunk,
+            float* __restrict__ partial, int ps, int write_ll) {
+    static_assert(KP >= 4 && KP <= 32, "two samples per lane need 2 * 32 / KP <= 32");
+    constexpr int SPI = 32 / KP;
+    constexpr int RED = KP * kStat + 4;
+    constexpr unsigned FULL = 0xffffffffu;
+    __shared__ __align__(16) float4 s_x[kEW][32];   // (x - xref, weight) of the batch's samples
+    __shared__ __align__(16) float4 s_w[kEW][32];   // (direction, 0)
+    __shared__ float2 s_lse[kEW][32];               // per sample: (shifted sum, shift)
+    __shared__ float red[kEW][RED];
+    __shared__ int s_c;
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int k = lane & (KP - 1), h = lane / KP;
+    const float* __restrict__ px = ws->desc.p[0];
+    const float* __restrict__ py = ws->desc.p[1];
+    const float* __restrict__ pz = ws->desc.p[2];
+    const float* __restrict__ ox = ws->desc.p[3];
+    const float* __restrict__ oy = ws->desc.p[4];
+    const float* __restrict__ oz = ws->desc.p[5];
+    const float* __restrict__ pw = ws->desc.p[6];
+    const int64_t* __restrict__ off = ws->desc.offsets;
+    float* __restrict__ loglik = write_ll ? ws->desc.loglik : nullptr;
+    const int n_chunks = ws->n_chunks;
+    const int64_t R = ws->desc.R;
+
+    // this lane's component: R_mu rows (t, b, mu), mean offset from the
+    // reference point (3) and in-chart direction offset (2), scaled L^-1,
+    // base-2 constant shifted by the region bound
+    float rt[9], mo[5], li[15];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) rt[q] = 0.f;
+#pragma unroll
+    for (int q = 0; q < 5; ++q) mo[q] = 0.f;
+#pragma unroll
+    for (int q = 0; q < 15; ++q) li[q] = 0.f;
+    float c2 = -INFINITY, lmax = 0.f;
+    float xr0 = 0.f, xr1 = 0.f, xr2 = 0.f;
+    int prev_r = -1;
+
+    // log2 of the chart density of one sample at this lane's component,
+    // relative to the region bound; d receives the tangent vector
+    auto logp2 = [&](const float4 sa, const float4 sb, float d[5]) -> float {
+        const float u = rt[0] * sb.x + rt[1] * sb.y + rt[2] * sb.z;
+        const float v = rt[3] * sb.x + rt[4] * sb.y + rt[5] * sb.z;
+        const float cz = rt[6] * sb.x + rt[7] * sb.y + rt[8] * sb.z;
+        const float s2 = u * u + v * v;
+        const bool cut = s2 == 0.f && cz < 0.f;     // antipode of the mean: no chart
+        const float gg = cut ? 1.f : g_of_cos(cz, rsqrtf(s2));
+        d[0] = sa.x - mo[0];
+        d[1] = sa.y - mo[1];
+        d[2] = sa.z - mo[2];
+        d[3] = gg * u - mo[3];
+        d[4] = gg * v - mo[4];
+        const float y0 = li[0] * d[0];
+        const float y1 = li[1] * d[0] + li[2] * d[1];
+        const float y2 = li[3] * d[0] + li[4] * d[1] + li[5] * d[2];
+        const float y3 = li[6] * d[0] + li[7] * d[1] + li[8] * d[2] + li[9] * d[3];
+        const float y4 = li[10] * d[0] + li[11] * d[1] + li[12] * d[2] + li[13] * d[3] + li[14] * d[4];
+        float l2 = fmaf(-y0, y0, c2);
+        l2 = fmaf(-y1, y1, l2);
+        l2 = fmaf(-y2, y2, l2);
+        l2 = fmaf(-y3, y3, l2);
+        l2 = fmaf(-y4, y4, l2);
+        return cut ? -INFINITY : l2;
+    };
+
+    for (;;) {
+        if (threadIdx.x == 0) s_c = atomicAdd(&ws->queue, 1);
+        __syncthreads();
+        const int c = s_c;
+        if (c >= n_chunks) break;
+        const int r = chunk_region[c];
+        if (r < 0 || r >= R) {               // never happens for units built by k_build_chunks
+            __syncthreads();                 // (uniform branch) s_c is read before it is rewritten
+            continue;
+        }
+        const int64_t o1 = off[r + 1];
+        const int64_t start = off[r] + ((int64_t)c - chunk_base[r]) * chunk;
+        const int64_t end = min(start + (int64_t)chunk, o1);
+        if (r != prev_r) {
+            prev_r = r;
+            const float* rec0 = etab + (int64_t)r * K * kE;
+            xr0 = __ldg(rec0 + 0);
+            xr1 = __ldg(rec0 + 1);
+            xr2 = __ldg(rec0 + 2);
+            float c5 = -INFINITY;
+            if (k < K) {
+                float p[kE];
+                const float4* src = reinterpret_cast<const float4*>(rec0 + (int64_t)k * kE);
+#pragma unroll
+                for (int q = 0; q < kE / 4; ++q) {
+                    const float4 v = __ldg(src + q);
+                    p[4 * q + 0] = v.x;
+                    p[4 * q + 1] = v.y;
+                    p[4 * q + 2] = v.z;
+                    p[4 * q + 3] = v.w;
+                }
+#pragma unroll
+                for (int q = 0; q < 9; ++q) rt[q] = p[3 + q];
+                mo[0] = (p[0] - xr0) + p[32];
+                mo[1] = (p[1] - xr1) + p[33];
+                mo[2] = (p[2] - xr2) + p[34];
+                mo[3] = p[28];
+                mo[4] = p[29];
+#pragma unroll
+                for (int q = 0; q < 15; ++q) li[q] = p[12 + q] * kHalfLog2eSqrt;
+                c5 = p[27];
+            } else {                         // padding lane: density 0
+#pragma unroll
+                for (int q = 0; q < 9; ++q) rt[q] = 0.f;
+                rt[8] = 1.f;
+#pragma unroll
+                for (int q = 0; q < 5; ++q) mo[q] = 0.f;
+#pragma unroll
+                for (int q = 0; q < 15; ++q) li[q] = 0.f;
+            }
+            lmax = c5;
+#pragma unroll
+            for (int o = KP / 2; o > 0; o >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(FULL, lmax, o));
+            if (!(lmax > -INFINITY)) lmax = 0.f;      // every weight zero: all densities are 0
+            c2 = (c5 - lmax) * kLog2eF;               // -inf for zero weights and padding lanes
+        }
+
+        float acc[kStat];
+#pragma unroll
+        for (int s = 0; s < kStat; ++s) acc[s] = 0.f;
+        float wsum = 0.f, wll = 0.f;
+
+        auto accumulate = [&](const float wr, const float d[5]) {
+            acc[0] += wr;
+#pragma unroll
+            for (int a = 0; a < 5; ++a) {
+                const float wa = wr * d[a];
+                acc[1 + a] += wa;
+#pragma unroll
+                for (int b = 0; b <= a; ++b) acc[6 + pk(a, b)] = fmaf(wa, d[b], acc[6 + pk(a, b)]);
+            }
+        };
+
+        // raw values of this lane's sample of the next batch
+        float f0 = 0.f, f1 = 0.f, f2 = 0.f, f3 = 0.f, f4 = 0.f, f5 = 1.f, f6 = 0.f;
+        auto fetch = [&](const int64_t i) {
+            if (i < end) {
+                f0 = __ldg(px + i);
+                f1 = __ldg(py + i);
+                f2 = __ldg(pz + i);
+                f3 = __ldg(ox + i);
+                f4 = __ldg(oy + i);
+                f5 = __ldg(oz + i);
+                f6 = __ldg(pw + i);
+            } else {
+                f0 = f1 = f2 = f3 = f4 = f6 = 0.f;
+                f5 = 1.f;
+            }
+        };
+        fetch(start + warp * 32 + lane);
+
+        for (int64_t g = start + warp * 32; g < end; g += kEW * 32) {
+            // stage this batch (past the unit: weight 0, a valid direction)
+            const float my_w = f6;
+            s_x[warp][lane] = make_float4(f0 - xr0, f1 - xr1, f2 - xr2, f6);
+            s_w[warp][lane] = make_float4(f3, f4, f5, 0.f);
+            __syncwarp();
+            fetch(g + kEW * 32 + lane);
+            const int n = (int)min((int64_t)32, end - g);
+
+            for (int t = 0; t < n; t += 2 * SPI) {
+                const int ja = t + h, jb = t + SPI + h;   // both < 32; past n they carry weight 0
+                const float4 xa = s_x[warp][ja], wa = s_w[warp][ja];
+                const float4 xb = s_x[warp][jb], wb = s_w[warp][jb];
+                float da[5], db[5];
+                const float ea = ex2f(logp2(xa, wa, da));
+                const float eb = ex2f(logp2(xb, wb, db));
+                float sa = ea, sb = eb;
+#pragma unroll
+                for (int o = KP / 2; o > 0; o >>= 1) {
+                    sa += __shfl_xor_sync(FULL, sa, o);
+                    sb += __shfl_xor_sync(FULL, sb, o);
+                }
+                if (k == 0) {
+                    s_lse[warp][ja] = make_float2(sa, lmax);
+                    s_lse[warp][jb] = make_float2(sb, lmax);
+                }
+                const float ra = sa >= kSumMin ? __fdividef(xa.w * ea, sa) : 0.f;
+                const float rb = sb >= kSumMin ? __fdividef(xb.w * eb, sb) : 0.f;
+                accumulate(ra, da);
+                accumulate(rb, db);
+            }
+            __syncwarp();
+            // samples whose shifted sum underflowed: again with the exact maximum
+            unsigned redo = __ballot_sync(FULL, lane < n && !(s_lse[warp][lane].x >= kSumMin));
+            while (redo) {
+                // slot h takes the (h+1)-th lowest flagged sample (none: 0xffffffff)
+                const unsigned jj = __fns(redo, 0u, h + 1);
+#pragma unroll
+                for (int hh = 0; hh < SPI; ++hh) redo &= redo - 1u;
+                const bool act = jj < 32u;
+                const int j = act ? (int)jj : 0;
+                const float4 xa = s_x[warp][j], wa = s_w[warp][j];
+                float da[5];
+                const float l2 = logp2(xa, wa, da);
+                float ref = l2;
+#pragma unroll
+                for (int o = KP / 2; o > 0; o >>= 1) ref = fmaxf(ref, __shfl_xor_sync(FULL, ref, o));
+                const float e = (ref == -INFINITY) ? 0.f : ex2f(l2 - ref);
+                float se = e;
+#pragma unroll
+                for (int o = KP / 2; o > 0; o >>= 1) se += __shfl_xor_sync(FULL, se, o);
+                if (k == 0 && act) s_lse[warp][j] = make_float2(se, lmax + ref * kLn2F);
+                const float rr = (act && se >= kSumMin) ? __fdividef(xa.w * e, se) : 0.f;
+                accumulate(rr, da);
+            }
+            __syncwarp();
+            // lane i: log-likelihood, weight and weighted log-likelihood of sample g + i
+            {
+                const float2 q = s_lse[warp][lane];
+                if (lane < n) {
+                    const float li_ = (q.x > 0.f) ? q.y + __logf(q.x) : -INFINITY;
+                    wsum += my_w;
+                    wll += (my_w > 0.f) ? my_w * li_ : 0.f;
+                    if (loglik != nullptr) loglik[g + lane] = li_;
+                }
+            }
+            __syncwarp();
+        }
+        // combine the SPI sample slots of each component; W and sum w l over all lanes
+#pragma unroll
+        for (int o = KP; o < 32; o <<= 1) {
+#pragma unroll
+            for (int s = 0; s < kStat; ++s) acc[s] += __shfl_xor_sync(FULL, acc[s], o);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            wsum += __shfl_xor_sync(FULL, wsum, o);
+            wll += __shfl_xor_sync(FULL, wll, o);
+        }
+        if (h == 0 && k < K) {
+#pragma unroll
+            for (int s = 0; s < kStat; ++s) red[warp][k * kStat + s] = acc[s];
+        }
+        if (lane == 0) {
+            red[warp][K * kStat] = wsum;
+            red[warp][K * kStat + 1] = wll;
+        }
+        __syncthreads();
+        const int nv = K * kStat + 2;
+        for (int v = threadIdx.x; v < nv; v += kEW * 32) {
+            float s = 0.f;
+#pragma unroll
+            for (int w = 0; w < kEW; ++w) s += red[w][v];
+            partial[(int64_t)c * ps + v] = s;
+        }
+    }
+}
+
+bool estep_fast_supported(int KP) { return KP >= 4 && KP <= 32; }
+
+cudaError_t launch_estep_fast(cudaStream_t s, int KP, int grid, WsHeader* ws, const int64_t* cb,
+                              const int32_t* cr, const float* etab, int K, int chunk, float* partial,
+                              int ps, int write_ll) {
+    switch (KP) {
+        case 4: k_estep<4><<<grid, kEW * 32, 0, s>>>(ws, cb, cr, etab, K, chunk, partial, ps, write_ll); break;
+        case 8: k_estep<8><<<grid, kEW * 32, 0, s>>>(ws, cb, cr, etab, K, chunk, partial, ps, write_ll); break;
+        case 16: k_estep<16><<<grid, kEW * 32, 0, s>>>(ws, cb, cr, etab, K, chunk, partial, ps, write_ll); break;
+        case 32: k_estep<32><<<grid, kEW * 32, 0, s>>>(ws, cb, cr, etab, K, chunk, partial, ps, write_ll); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace sdmm

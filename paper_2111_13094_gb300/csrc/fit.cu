@@ -1037,6 +1037,8 @@ cudaError_t launch_accumulate(cudaStream_t s, int mode, int KP, int grid, WsHead
                               const int64_t* cb, const int32_t* cr, const float* etab, int K,
                               int chunk, int density, float* partial, int ps, int write_ll,
                               const float* chart2, int euclid) {
+    if (mode == MODE_FIT && density == SDMM_DENSITY_TANGENT && !euclid && estep_fast_supported(KP))
+        return launch_estep_fast(s, KP, grid, ws, cb, cr, etab, K, chunk, partial, ps, write_ll);
     if (mode == MODE_FIT)
         return launch_acc_mode<MODE_FIT>(KP, dim3(grid), s, ws, cb, cr, etab, K, chunk, density,
                                          partial, ps, write_ll, nullptr, euclid);
