@@ -538,41 +538,47 @@ def query_leg(args, api, torch, dev, stream, seed, world, cfg, peaks, src, n_sm,
     """16M guided queries over 65,536 grid regions: as given (grid lookup) and
     pre-sorted by region; roofline; oracle baseline and pdf errors on the
     first queries; product sampling with 3 BSDF lobes."""
+    Q = args.queries
     Rq = int(np.prod(Q_DIMS))
     pi, mu_x, mu_w, L = syn_random_mixtures(seed)
     qst = api.MixtureState(Rq, K_COMP, device=dev)
     qst.set_params(torch.from_numpy(pi), torch.from_numpy(mu_x), torch.from_numpy(mu_w), torch.from_numpy(L))
     api.prepare(cfg, qst)
     from paper_2111_13094_gb300 import synthetic as syn
-    qx_h = syn.query_points(seed, Q_COUNT)
+    qx_h = syn.query_points(seed, Q)
     qx = torch.from_numpy(qx_h).to(dev)
     grid = api.Grid((0, 0, 0), (1, 1, 1), Q_DIMS)
-    out = (torch.empty(Q_COUNT, 3, device=dev), torch.empty(Q_COUNT, device=dev),
-           torch.empty(Q_COUNT, dtype=torch.uint8, device=dev))
+    out = (torch.empty(Q, 3, device=dev), torch.empty(Q, device=dev),
+           torch.empty(Q, dtype=torch.uint8, device=dev))
     reg_h = syn.grid_region(qx_h, Q_DIMS)
     reg = torch.from_numpy(reg_h).to(dev)
     order = torch.argsort(reg)
     qx_b, reg_b = qx[order].contiguous(), reg[order].contiguous()
+    qws = api.query_workspace(Rq, Q, device=dev)
+    t_lib = _timed(lambda: api.sample(cfg, qst, qx, grid=grid, seed=7, out=out, ws=qws), stream)
     t_grid = _timed(lambda: api.sample(cfg, qst, qx, grid=grid, seed=7, out=out), stream)
     t_bin = _timed(lambda: api.sample(cfg, qst, qx_b, region=reg_b, seed=7, out=out), stream)
     api.sample(cfg, qst, qx, grid=grid, seed=7, out=out)
     torch.cuda.synchronize()
     disc = 1.0 - out[2].float().mean().item()
     peak, basis = fp32_peak(n_sm, peaks, src)
-    flops = Q_COUNT * (K_COMP * FLOPS_PER_QUERY_COMPONENT + FLOPS_PER_QUERY)
+    flops = Q * (K_COMP * FLOPS_PER_QUERY_COMPONENT + FLOPS_PER_QUERY)
 
     def roof(ms):
         a = flops / (ms * 1e-3) / 1e12
         return {"bound": "alu", "achieved": a, "peak": peak, "unit": "TFLOP/s", "frac": a / peak,
                 "traffic": None, "kernel_ms": ms, "peak_basis": basis,
                 "flops_per_query": K_COMP * FLOPS_PER_QUERY_COMPONENT + FLOPS_PER_QUERY,
-                "hbm_gbs": Q_COUNT * BYTES_PER_QUERY / (ms * 1e-3) / 1e9}
+                "hbm_gbs": Q * BYTES_PER_QUERY / (ms * 1e-3) / 1e9}
 
-    qres = {"value": world * Q_COUNT / (t_grid * 1e-3), "unit": "queries/s",
-            "binned_value": world * Q_COUNT / (t_bin * 1e-3), "kernel_ms": t_grid,
-            "binned_kernel_ms": t_bin, "queries": Q_COUNT, "regions": Rq, "K": K_COMP,
-            "discard_rate": disc, "roofline": roof(t_grid), "binned_roofline": roof(t_bin),
-            "config": "16M positions uniform in the unit cube, 64x32x32 grid regions, "
+    qres = {"value": world * Q / (t_lib * 1e-3), "unit": "queries/s", "ms": t_lib,
+            "path": "sdmm_sample_binned: queries as given (uniform positions), grid lookup, binned by region "
+                    "in the library's workspace (counting sort), then one thread per query",
+            "unbinned_value": world * Q / (t_grid * 1e-3), "unbinned_ms": t_grid,
+            "presorted_value": world * Q / (t_bin * 1e-3), "presorted_ms": t_bin,
+            "queries": Q, "regions": Rq, "K": K_COMP,
+            "discard_rate": disc, "roofline": roof(t_lib), "presorted_roofline": roof(t_bin),
+            "config": f"{Q} positions uniform in the unit cube, 64x32x32 grid regions, "
                       "condition + Philox draw + sample + pdf, FP32"}
     if want_cpu:
         cpu, o, Qs = cpu_baseline_queries((pi, mu_x, mu_w, L), qx_h, reg_h, 7, args.cpu_budget / 3)
@@ -597,15 +603,15 @@ def query_leg(args, api, torch, dev, stream, seed, world, cfg, peaks, src, n_sm,
                             "note": "pdf: GPU value against the oracle's pdf at the GPU's FP32 direction; "
                                     "directions against the oracle's sample where its component choice "
                                     "is more than 1e-5 from a CDF boundary"}
-    bw, bmu, bL = (torch.from_numpy(a).to(dev) for a in syn.bsdf_lobes(seed, Q_COUNT, 3))
+    bw, bmu, bL = (torch.from_numpy(a).to(dev) for a in syn.bsdf_lobes(seed, Q, 3))
     t_prod = _timed(lambda: api.product_sample(cfg, qst, qx, bw, bmu, bL, grid=grid, seed=7), stream)
     bw_b, bmu_b, bL_b = bw[order].contiguous(), bmu[order].contiguous(), bL[order].contiguous()
     t_prod_b = _timed(lambda: api.product_sample(cfg, qst, qx_b, bw_b, bmu_b, bL_b, region=reg_b, seed=7), stream)
-    qres["product"] = {"value": world * Q_COUNT / (t_prod * 1e-3), "unit": "queries/s", "kernel_ms": t_prod,
-                       "binned_value": world * Q_COUNT / (t_prod_b * 1e-3), "binned_kernel_ms": t_prod_b,
+    qres["product"] = {"value": world * Q / (t_prod * 1e-3), "unit": "queries/s", "kernel_ms": t_prod,
+                       "binned_value": world * Q / (t_prod_b * 1e-3), "binned_kernel_ms": t_prod_b,
                        "config": "the same 16M queries, 3 BSDF lobes each (wide, narrow, random), "
                                  "2K pairs per query: condition + pair products + sample + product pdf, FP32"}
-    del bw, bmu, bL, bw_b, bmu_b, bL_b, qst, out
+    del bw, bmu, bL, bw_b, bmu_b, bL_b, qst, out, qws
     return qres
 
 
@@ -1084,6 +1090,7 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=list(PREC),
                     help="E-step arithmetic: FP32 SIMT or a tensor-core contraction form")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--queries", type=int, default=Q_COUNT, help="queries of the query workload")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)        # at least 3 untimed steps, reported as run
     if args.impl == "reference":

@@ -27,8 +27,10 @@
  *    time their launches with CUDA events, wait for them and print
  *    "sdmm: <call> <ms> ms" to stderr; streams being captured are skipped.
  *  - Inputs (const pointers) are never modified.  sdmm_state is in/out.
- *  - The library allocates no device memory: all scratch is the caller's
- *    workspace, whose size sdmm_*_workspace_size reports.
+ *  - The library allocates no device memory: the scratch of every call is
+ *    the caller's workspace, whose size sdmm_*_workspace_size reports --
+ *    except sdmm_fit_regions_noalloc, which uses a fixed scratch array of
+ *    SDMM_NOALLOC_SCRATCH_BYTES compiled into the library.
  *  - Sample streams are structure-of-arrays FP32, sorted by region: region r
  *    owns samples [offsets[r], offsets[r+1]) (offsets: int64, R+1 entries,
  *    device).  Stream pointers need FP32 (4-byte) alignment.
@@ -316,6 +318,35 @@ sdmm_status sdmm_pdf(const sdmm_config *cfg, const sdmm_state *st, int64_t R,
                      sdmm_stream stream);
 
 /*
+ * sdmm_sample and sdmm_pdf for queries in any order, binned by region inside
+ * the library (Sec. 3.3: every query reads its region's K components; queries
+ * of one region then share those reads).  A counting sort of the queries by
+ * region runs in the caller's workspace (device memory of at least
+ * sdmm_query_workspace_size(R, Q) bytes, 256-byte aligned, clobbered), then
+ * the queries are processed region by region; every output goes to the
+ * query's own index, and the result of a query depends only on its inputs and
+ * its index (the Philox counter), so it equals that of sdmm_sample / sdmm_pdf
+ * up to the order-independent rounding of the pdf sum.  Arguments, uniforms,
+ * outputs and errors as for sdmm_sample / sdmm_pdf; in addition Q must be
+ * below 2^31 (SDMM_ERR_INVALID_ARG) and a workspace that is NULL, misaligned
+ * or too small is SDMM_ERR_WORKSPACE.  With K > 16 the queries are processed
+ * in the given order and the workspace is not used.
+ */
+sdmm_status sdmm_query_workspace_size(int64_t R, int64_t Q, size_t *bytes);
+sdmm_status sdmm_sample_binned(const sdmm_config *cfg, const sdmm_state *st,
+                               int64_t R, int64_t Q, const float *qx,
+                               const int32_t *region, const sdmm_grid *grid,
+                               uint64_t seed, const float *uniforms,
+                               float *dir_out, float *pdf_out,
+                               uint8_t *valid_out, void *workspace,
+                               size_t ws_bytes, sdmm_stream stream);
+sdmm_status sdmm_pdf_binned(const sdmm_config *cfg, const sdmm_state *st,
+                            int64_t R, int64_t Q, const float *qx,
+                            const int32_t *region, const sdmm_grid *grid,
+                            const float *dir, float *pdf_out, void *workspace,
+                            size_t ws_bytes, sdmm_stream stream);
+
+/*
  * Weighted MAP objective per region (the function that the MAP-EM of
  * Sec. 4.3 ascends; Dirichlet and inverse-Wishart priors after Gauvain-Lee):
  *   F_r = (1/W) sum_i w_i l_i + sum_k [beta q log pi_k - (beta a/2) log|Sigma_k|
@@ -481,7 +512,9 @@ sdmm_status sdmm_tc_selftest(int32_t kind, int32_t N, int32_t Kd,
  *    before reading it, so nothing needs clearing between calls, but calls
  *    whose work overlaps on the GPU (other streams, other host threads)
  *    race on the scratch and produce wrong results: serialise them.
- * Arguments, results and per-region statuses are those of sdmm_fit_regions.
+ * Arguments, results and per-region statuses are those of sdmm_fit_regions
+ * (every precision and covariance update); with the same cfg the results are
+ * bit-identical to it, since both cut the regions into the same work units.
  */
 #define SDMM_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
 sdmm_status sdmm_fit_regions_noalloc(const sdmm_config *cfg,

@@ -26,7 +26,8 @@ SYMBOLS = ["sdmm_config_default", "sdmm_last_error", "sdmm_version", "sdmm_fit_w
            "sdmm_fit_plan_timing", "sdmm_fit_plan_destroy", "sdmm_autotune",
            "sdmm_fit_regions_noalloc", "sdmm_tc_selftest", "sdmm_wait_selftest", "sdmm_validate_samples", "sdmm_kdtree_grid", "sdmm_kdtree_lookup",
            "sdmm_kdtree_workspace_size", "sdmm_kdtree_bin", "sdmm_kdtree_refine", "sdmm_gather_regions",
-           "sdmm_product_sample", "sdmm_product_pdf"]
+           "sdmm_product_sample", "sdmm_product_pdf", "sdmm_query_workspace_size", "sdmm_sample_binned",
+           "sdmm_pdf_binned"]
 
 SDMM_NOALLOC_SCRATCH_BYTES = 16 * 1024 * 1024
 
@@ -123,6 +124,10 @@ def _declare(L):
         "sdmm_product_sample": [_PC, _PS, _I64, _I64, _P, _P, _PG, ctypes.POINTER(BsdfLobes), ctypes.c_uint64, _P,
                                 _P, _P, _P, _P],
         "sdmm_product_pdf": [_PC, _PS, _I64, _I64, _P, _P, _PG, ctypes.POINTER(BsdfLobes), _P, _P, _P],
+        "sdmm_query_workspace_size": [_I64, _I64, ctypes.POINTER(ctypes.c_size_t)],
+        "sdmm_sample_binned": [_PC, _PS, _I64, _I64, _P, _P, _PG, ctypes.c_uint64, _P, _P, _P, _P, _P,
+                               ctypes.c_size_t, _P],
+        "sdmm_pdf_binned": [_PC, _PS, _I64, _I64, _P, _P, _PG, _P, _P, _P, ctypes.c_size_t, _P],
     }
     for name, args in sig.items():
         f = getattr(L, name)

@@ -275,8 +275,17 @@ def condition(cfg, state: MixtureState, qx, region=None, grid=None, stream=None)
     return cpi, cm, cL
 
 
+def query_workspace(R: int, Q: int, device="cuda") -> torch.Tensor:
+    """Workspace of the binned query entry points (sdmm_query_workspace_size)."""
+    n = ctypes.c_size_t()
+    check(_lib.load().sdmm_query_workspace_size(int(R), int(Q), ctypes.byref(n)), "sdmm_query_workspace_size")
+    return torch.empty(max(int(n.value), 1), dtype=torch.uint8, device=device)
+
+
 def sample(cfg, state: MixtureState, qx, region=None, grid=None, seed=0, uniforms=None, out=None,
-           stream=None):
+           stream=None, ws=None):
+    """Guided directions, pdfs and validity flags; with `ws` (query_workspace)
+    the queries are binned by region inside the library (sdmm_sample_binned)."""
     Q = qx.shape[0]
     dev = qx.device
     if out is None:
@@ -285,6 +294,12 @@ def sample(cfg, state: MixtureState, qx, region=None, grid=None, seed=0, uniform
                torch.empty(Q, dtype=torch.uint8, device=dev))
     d, p, v = out
     st = state.c()
+    if ws is not None:
+        check(_lib.load().sdmm_sample_binned(ctypes.byref(cfg), ctypes.byref(st), state.R, Q, _ptr(qx),
+                                             _ptr(region), _grid_arg(grid), ctypes.c_uint64(seed), _ptr(uniforms),
+                                             _ptr(d), _ptr(p), _ptr(v), _ptr(ws), ws.numel(), _stream(stream)),
+              "sdmm_sample_binned")
+        return d, p, v
     check(_lib.load().sdmm_sample(ctypes.byref(cfg), ctypes.byref(st), state.R, Q, _ptr(qx),
                                   _ptr(region), _grid_arg(grid), ctypes.c_uint64(seed), _ptr(uniforms),
                                   _ptr(d), _ptr(p), _ptr(v), _stream(stream)), "sdmm_sample")
@@ -332,10 +347,15 @@ def product_pdf(cfg, state: MixtureState, qx, dirs, bsdf_w, bsdf_mu, bsdf_L, reg
     return p
 
 
-def pdf(cfg, state: MixtureState, qx, dirs, region=None, grid=None, out=None, stream=None):
+def pdf(cfg, state: MixtureState, qx, dirs, region=None, grid=None, out=None, stream=None, ws=None):
     Q = qx.shape[0]
     p = out if out is not None else torch.empty(Q, dtype=torch.float32, device=qx.device)
     st = state.c()
+    if ws is not None:
+        check(_lib.load().sdmm_pdf_binned(ctypes.byref(cfg), ctypes.byref(st), state.R, Q, _ptr(qx), _ptr(region),
+                                          _grid_arg(grid), _ptr(dirs), _ptr(p), _ptr(ws), ws.numel(),
+                                          _stream(stream)), "sdmm_pdf_binned")
+        return p
     check(_lib.load().sdmm_pdf(ctypes.byref(cfg), ctypes.byref(st), state.R, Q, _ptr(qx), _ptr(region),
                                _grid_arg(grid), _ptr(dirs), _ptr(p), _stream(stream)), "sdmm_pdf")
     return p

@@ -487,6 +487,68 @@ sdmm_status sdmm_sample(const sdmm_config* cfg, const sdmm_state* st, int64_t R,
     return SDMM_OK;
 }
 
+sdmm_status sdmm_query_workspace_size(int64_t R, int64_t Q, size_t* bytes) {
+    if (!bytes) return fail(SDMM_ERR_INVALID_ARG, "bytes is NULL");
+    if (R < 1 || Q < 0) return fail(SDMM_ERR_INVALID_ARG, "R = %lld, Q = %lld", (long long)R, (long long)Q);
+    *bytes = qbin_workspace_bytes(R, Q);
+    return SDMM_OK;
+}
+
+static sdmm_status binned_checks(const sdmm_config* cfg, int64_t R, int64_t Q, void* ws, size_t ws_bytes) {
+    if (Q > (int64_t)INT32_MAX) return fail(SDMM_ERR_INVALID_ARG, "Q = %lld must be below 2^31", (long long)Q);
+    if (R >= (int64_t)INT32_MAX) return fail(SDMM_ERR_INVALID_ARG, "R = %lld must be below 2^31", (long long)R);
+    if (pow2_ceil(cfg->K) > 16) return SDMM_OK;          // processed in the given order, no workspace
+    const size_t need = qbin_workspace_bytes(R, Q);
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u) || ws_bytes < need)
+        return fail(SDMM_ERR_WORKSPACE, "query workspace must be 256-byte aligned device memory of %zu bytes", need);
+    return SDMM_OK;
+}
+
+sdmm_status sdmm_sample_binned(const sdmm_config* cfg, const sdmm_state* st, int64_t R, int64_t Q,
+                               const float* qx, const int32_t* region, const sdmm_grid* grid, uint64_t seed,
+                               const float* uniforms, float* dir_out, float* pdf_out, uint8_t* valid_out,
+                               void* workspace, size_t ws_bytes, sdmm_stream stream) {
+    ProfileScope prof_("sample_binned", stream);
+    GridF g;
+    sdmm_status e = query_common(cfg, st, R, Q, qx, region, grid, &g);
+    if (e) return e;
+    if (Q > 0 && (!dir_out || !pdf_out || !valid_out)) return fail(SDMM_ERR_INVALID_ARG, "outputs are NULL");
+    if ((e = binned_checks(cfg, R, Q, workspace, ws_bytes))) return e;
+    if (Q == 0) return SDMM_OK;
+    const int KP = pow2_ceil(cfg->K);
+    if (KP > 16)
+        SDMM_CUDA(launch_query(stream, OP_SAMPLE, KP, query_grid(Q), st->qtab, cfg->K, R, Q, qx, region, g, seed,
+                               uniforms, nullptr, nullptr, nullptr, nullptr, dir_out, pdf_out, valid_out),
+                  "sample_binned");
+    else
+        SDMM_CUDA(launch_query_binned(stream, OP_SAMPLE, KP, query_grid(Q), st->qtab, cfg->K, R, Q, qx, region, g,
+                                      seed, uniforms, nullptr, dir_out, pdf_out, valid_out, workspace),
+                  "sample_binned");
+    return SDMM_OK;
+}
+
+sdmm_status sdmm_pdf_binned(const sdmm_config* cfg, const sdmm_state* st, int64_t R, int64_t Q, const float* qx,
+                            const int32_t* region, const sdmm_grid* grid, const float* dir, float* pdf_out,
+                            void* workspace, size_t ws_bytes, sdmm_stream stream) {
+    ProfileScope prof_("pdf_binned", stream);
+    GridF g;
+    sdmm_status e = query_common(cfg, st, R, Q, qx, region, grid, &g);
+    if (e) return e;
+    if (Q > 0 && (!dir || !pdf_out)) return fail(SDMM_ERR_INVALID_ARG, "dir/pdf_out are NULL");
+    if ((e = binned_checks(cfg, R, Q, workspace, ws_bytes))) return e;
+    if (Q == 0) return SDMM_OK;
+    const int KP = pow2_ceil(cfg->K);
+    if (KP > 16)
+        SDMM_CUDA(launch_query(stream, OP_PDF, KP, query_grid(Q), st->qtab, cfg->K, R, Q, qx, region, g, 0, nullptr,
+                               dir, nullptr, nullptr, nullptr, nullptr, pdf_out, nullptr),
+                  "pdf_binned");
+    else
+        SDMM_CUDA(launch_query_binned(stream, OP_PDF, KP, query_grid(Q), st->qtab, cfg->K, R, Q, qx, region, g, 0,
+                                      nullptr, dir, nullptr, pdf_out, nullptr, workspace),
+                  "pdf_binned");
+    return SDMM_OK;
+}
+
 static sdmm_status bsdf_check(const sdmm_bsdf_lobes* b, int64_t Q) {
     if (!b) return fail(SDMM_ERR_INVALID_ARG, "bsdf is NULL");
     if (b->J < 1 || b->J > 8) return fail(SDMM_ERR_INVALID_ARG, "J = %d BSDF lobes: 1..8", b->J);
@@ -853,14 +915,12 @@ sdmm_status sdmm_wait_selftest(int64_t limit_ns, int32_t arrive, int32_t* status
 sdmm_status sdmm_fit_regions_noalloc(const sdmm_config* cfg, const sdmm_samples* s, int32_t iters,
                                      const double* prior_scale, sdmm_state* st, float* loglik_out,
                                      sdmm_stream stream) {
+    ProfileScope prof_("fit_regions_noalloc", stream);
     sdmm_status e;
     if ((e = check_config(cfg)) || (e = check_samples(s)) || (e = check_state(st, true))) return e;
     if (iters < 1) return fail(SDMM_ERR_INVALID_ARG, "iters = %d must be >= 1", iters);
     if (cfg->prior_scale_mode == SDMM_PRIOR_SCALE_ARRAY && !prior_scale)
         return fail(SDMM_ERR_INVALID_ARG, "prior_scale_mode ARRAY needs prior_scale");
-    if (cfg->precision != SDMM_PREC_FP32)
-        return fail(SDMM_ERR_UNSUPPORTED, "precision %d is not available in sdmm_fit_regions_noalloc",
-                    cfg->precision);
     const Layout L = layout(cfg, s->R, s->N, choose_chunk(cfg, s->N));
     if (L.total > (size_t)SDMM_NOALLOC_SCRATCH_BYTES)
         return fail(SDMM_ERR_WORKSPACE,

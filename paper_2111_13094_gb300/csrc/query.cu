@@ -7,10 +7,411 @@
 // then processed SPI = 32/KP at a time with one lane per component (KP lanes
 // per query), the query's inputs broadcast by shuffles; the component's
 // query record stays in registers while consecutive queries share a region.
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
+#include "tc.cuh"
 
 namespace sdmm {
+
+// ---------------------------------------------------------------------------
+// Guided sampling and pdf with one thread per query (K <= KM components).
+// The thread conditions every component of its region on the position in a
+// first pass (weight and conditional mean of each component kept in shared
+// memory, one 16-byte slot per component and thread), picks the component
+// and draws the direction, then evaluates the solid-angle pdf of the
+// conditioned mixture at that direction in a second pass.  No lane waits on
+// another: the component choice, the Gaussian draw and the exp map run once
+// per query instead of in one lane of a component group.
+//
+// A warp takes 32 queries at a time.  When they all fall in one region
+// (queries sorted by region), it copies that region's K records into shared
+// memory with coalesced 16-byte loads (only when the region changes) and every
+// thread reads them from there.  A warp whose queries span several regions
+// (queries in any order, or a region boundary) processes them with one lane
+// per component instead (warp_by_components), which reads each query's
+// records once, coalesced.  With `perm`, the warp's j-th query is perm[j] and
+// its region is key[j] (the library's binning of queries given in any order);
+// outputs always go to the query's own index.
+constexpr int kQWarps = 4;
+
+template <int KP, int OP>
+__device__ __forceinline__ void warp_by_components(const float* __restrict__ qtab, int K, int n, int64_t il,
+                                                   float x0, float x1, float x2, int rr, float a0, float a1,
+                                                   float a2, float* P, int& cur_r, float* __restrict__ cond_pi,
+                                                   float* __restrict__ cond_m, float* __restrict__ cond_L,
+                                                   float* __restrict__ dir_out, float* __restrict__ pdf_out,
+                                                   uint8_t* __restrict__ valid_out);
+
+constexpr int kQCtas = 5;        // resident CTAs per SM (registers and shared memory allow five)
+
+template <int KM, int OP>
+__global__ void __launch_bounds__(kQWarps * 32, kQCtas)
+    k_query_q(const float* __restrict__ qtab, int K, int64_t R, int64_t Q,
+              const float* __restrict__ qx, const int32_t* __restrict__ region, GridF grid,
+              const int32_t* __restrict__ perm, const int32_t* __restrict__ key, uint64_t seed,
+              const float* __restrict__ uni, const float* __restrict__ dir_in, float* __restrict__ dir_out,
+              float* __restrict__ pdf_out, uint8_t* __restrict__ valid_out) {
+    static_assert(OP == OP_SAMPLE || OP == OP_PDF, "sampling and pdf only");
+    constexpr unsigned FULL = 0xffffffffu;
+    constexpr float kL2e = 1.44269504088896341f;
+    constexpr int Q4 = kQ / 4;                                 // float4 per record
+    __shared__ float4 s_rec[kQWarps][KM * Q4];                 // per warp: one region's records
+    __shared__ float4 s_cm[KM][kQWarps * 32];                  // per thread: (w'_k, m_k, -) per component
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const float4* __restrict__ q4 = reinterpret_cast<const float4*>(qtab);
+    const int n4 = K * Q4;                                     // float4 of one region's records
+    float4* const cm = &s_cm[0][threadIdx.x];                  // component k at cm[k * kQWarps * 32]
+    constexpr int CS = kQWarps * 32;
+    int staged = -1;
+    const int64_t wstride = (int64_t)gridDim.x * kQWarps * 32;
+    for (int64_t base = ((int64_t)blockIdx.x * kQWarps + warp) * 32; base < Q; base += wstride) {
+        const int64_t j = base + lane;
+        const bool in = j < Q;
+        int64_t i = j;
+        int r = -1;
+        float x0 = 0.f, x1 = 0.f, x2 = 0.f;
+        if (in) {
+            if (perm != nullptr) {
+                i = perm[j];
+                r = key[j];
+            } else if (region != nullptr) {
+                r = region[j];
+            }
+            x0 = qx[3 * i];
+            x1 = qx[3 * i + 1];
+            x2 = qx[3 * i + 2];
+            if (perm == nullptr && region == nullptr) {
+                const float xs[3] = {x0, x1, x2};
+                int id[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const int v = (int)floorf((xs[c] - grid.lo[c]) * grid.scale[c]);
+                    id[c] = min(max(v, 0), grid.dims[c] - 1);
+                }
+                r = id[0] + grid.dims[0] * (id[1] + grid.dims[1] * id[2]);
+            }
+        }
+        const bool ok = in && r >= 0 && r < R;
+        const int rr = ok ? r : 0;
+        const int r0 = __shfl_sync(FULL, rr, 0);
+        if (!__all_sync(FULL, !in || rr == r0)) {
+            // queries of several regions (given in any order): one lane per
+            // component, each query's records read once, coalesced
+            float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+            if (in) {
+                if (OP == OP_SAMPLE) {
+                    if (uni != nullptr) {
+                        a0 = uni[3 * i];
+                        a1 = uni[3 * i + 1];
+                        a2 = uni[3 * i + 2];
+                    } else {
+                        const uint4 o = philox4x32_10(
+                            make_uint4((uint32_t)i, (uint32_t)((uint64_t)i >> 32), 0u, 0u),
+                            make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+                        a0 = u24(o.x);
+                        a1 = u24(o.y);
+                        a2 = u24(o.z);
+                    }
+                } else {
+                    a0 = dir_in[3 * i];
+                    a1 = dir_in[3 * i + 1];
+                    a2 = dir_in[3 * i + 2];
+                }
+            }
+            float P[kQ];
+            int cur_r = -1;
+            warp_by_components<KM, OP>(qtab, K, (int)min((int64_t)32, Q - base), i, x0, x1, x2, ok ? r : -1,
+                                       a0, a1, a2, P, cur_r, nullptr, nullptr, nullptr, dir_out, pdf_out,
+                                       valid_out);
+            continue;
+        }
+        // one region for the warp: its records into shared memory
+        if (r0 != staged) {
+            __syncwarp();
+            const float4* src = q4 + (int64_t)r0 * n4;
+            for (int e = lane; e < n4; e += 32) s_rec[warp][e] = __ldg(src + e);
+            __syncwarp();
+            staged = r0;
+        }
+        if (!in) continue;
+        const float4* rec = &s_rec[warp][0];
+
+        // ---- pass 1: conditioning on the position (Sec. 3.2), every component:
+        // lw = log2 of pi'_k up to a common constant, m = C^T z
+        float mx = -INFINITY;
+#pragma unroll 4
+        for (int k = 0; k < K; ++k) {
+            const float4* rk = rec + k * Q4;
+            const float4 a = rk[0], f3 = rk[3], f4 = rk[4], f5 = rk[5], f7 = rk[7], f8 = rk[8];
+            const float e0 = (x0 - a.x) - f8.x, e1 = (x1 - a.y) - f8.y, e2 = (x2 - a.z) - f8.z;
+            // A^-1 packed at 12..17, C^T rows at 18..20 and 21..23, cx at 30
+            const float z0 = f3.x * e0;
+            const float z1 = f3.y * e0 + f3.z * e1;
+            const float z2 = f3.w * e0 + f4.x * e1 + f4.y * e2;
+            const float lw = fmaf(-0.5f, z0 * z0 + z1 * z1 + z2 * z2, f7.z) * kL2e;
+            cm[k * CS] = make_float4(lw, f4.z * z0 + f4.w * z1 + f5.x * z2, f5.y * z0 + f5.z * z1 + f5.w * z2, 0.f);
+            mx = fmaxf(mx, lw);
+        }
+        // normalisation: w'_k = 2^(lw - max), se = sum w'_k
+        float se = 0.f;
+#pragma unroll 4
+        for (int k = 0; k < K; ++k) {
+            const float w = mx > -INFINITY ? tc::ex2_approx(cm[k * CS].x - mx) : 0.f;
+            cm[k * CS].x = w;
+            se += w;
+        }
+
+        float w0, w1, w2;
+        int valid = 1;
+        if (OP == OP_SAMPLE) {
+            float u0, u1, u2;
+            if (uni != nullptr) {
+                u0 = uni[3 * i];
+                u1 = uni[3 * i + 1];
+                u2 = uni[3 * i + 2];
+            } else {
+                const uint4 o = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)((uint64_t)i >> 32), 0u, 0u),
+                                              make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+                u0 = u24(o.x);
+                u1 = u24(o.y);
+                u2 = u24(o.z);
+            }
+            // component by inverse CDF on u0 (Sec. 3.1 "Sampling", step i): the
+            // first k with u0 se < cumsum; rounding past the end takes the last
+            // component of positive weight
+            const float thr = u0 * se;
+            float cum = 0.f;
+            int kk = -1, last = -1;
+#pragma unroll 4
+            for (int k = 0; k < K; ++k) {
+                const float w = cm[k * CS].x;
+                cum += w;
+                last = w > 0.f ? k : last;
+                kk = (kk < 0 && thr < cum) ? k : kk;
+            }
+            if (kk < 0) kk = last >= 0 ? last : 0;
+            const float4 sel = cm[kk * CS];
+            // Gaussian draw in the chart (step ii), exp map (step iii)
+            const float4* rk = rec + kk * Q4;
+            const float4 t4 = rk[0];   // mu_x, t.x
+            const float4 t5 = rk[1];   // t.y t.z b.x b.y
+            const float4 t6 = rk[2];   // b.z mu_w
+            const float4 dd = rk[6];   // D (d00 d10 d11), D^-1 00
+            const float rad = sqrtf(-2.f * logf(1.f - u1));
+            float sn, cs;
+            sincospif(2.f * u2, &sn, &cs);
+            const float g0 = rad * cs, g1 = rad * sn;
+            const float n0 = sel.y + dd.x * g0;
+            const float n1 = sel.z + dd.y * g0 + dd.z * g1;
+            const float rn = sqrtf(n0 * n0 + n1 * n1);
+            valid = (rn < kPiF) && ok && last >= 0;
+            float sr, cr;
+            sincosf(rn, &sr, &cr);
+            const float sc = rn < 1e-3f ? 1.f - rn * rn * (1.f / 6.f) : __fdividef(sr, rn);
+            const float c0 = n0 * sc, c1 = n1 * sc;
+            w0 = c0 * t4.w + c1 * t5.z + cr * t6.y;
+            w1 = c0 * t5.x + c1 * t5.w + cr * t6.z;
+            w2 = c0 * t5.y + c1 * t6.x + cr * t6.w;
+        } else {
+            w0 = dir_in[3 * i];
+            w1 = dir_in[3 * i + 1];
+            w2 = dir_in[3 * i + 2];
+        }
+
+        // ---- pass 2: solid-angle pdf of the conditioned mixture at w
+        // (Sec. 3.1 Eq. solidangle-pdf): sum_k pi'_k N_2(log_k w; m_k, D D^T) / sinc
+        float p = 0.f;
+#pragma unroll 4
+        for (int k = 0; k < K; ++k) {
+            const float4* rk = rec + k * Q4;
+            const float4 a = rk[0], b = rk[1], c = rk[2], f6 = rk[6], f7 = rk[7];
+            const float4 wm = cm[k * CS];
+            // t = (a.w, b.x, b.y), b = (b.z, b.w, c.x), mu = (c.y, c.z, c.w)
+            const float u = a.w * w0 + b.x * w1 + b.y * w2;
+            const float v = b.z * w0 + b.w * w1 + c.x * w2;
+            const float cz = c.y * w0 + c.z * w1 + c.w * w2;
+            const float s2v = u * u + v * v;
+            // antipode of the mean (and within 1e-19 of it): outside the chart
+            const bool cut = !(s2v >= 1.17549435e-38f) && cz < 0.f;
+            const float gg = cut ? 1.f : g_of_cos(cz, tc::rsqrt_approx(s2v));
+            const float d0 = gg * u - wm.y, d1 = gg * v - wm.z;
+            // D^-1 (f6.w, f7.x, f7.y), cn at 31
+            const float y0 = f6.w * d0;
+            const float y1 = f7.x * d0 + f7.y * d1;
+            const float pk_ = wm.x * tc::ex2_approx(fmaf(-0.5f, y0 * y0 + y1 * y1, f7.w) * kL2e) * gg;
+            p += cut ? 0.f : pk_;
+        }
+        p = se > 0.f ? __fdividef(p, se) : 0.f;
+        if (OP == OP_SAMPLE) {
+            dir_out[3 * i] = w0;
+            dir_out[3 * i + 1] = w1;
+            dir_out[3 * i + 2] = w2;
+            valid_out[i] = (uint8_t)valid;
+            pdf_out[i] = valid ? p : 0.f;
+        } else {
+            pdf_out[i] = ok ? p : 0.f;
+        }
+    }
+}
+
+// The queries held by the lanes of one warp (lane l: query il with position
+// x, region rr (-1: none) and uniforms or direction a), n of them, processed
+// SPI = 32/KP at a time with one lane per component; the query's inputs are
+// broadcast by shuffles and the component's query record P stays in
+// registers while consecutive queries share a region (cur_r).
+template <int KP, int OP>
+__device__ __forceinline__ void warp_by_components(const float* __restrict__ qtab, int K, int n, int64_t il,
+                                                   float x0, float x1, float x2, int rr, float a0, float a1,
+                                                   float a2, float* P, int& cur_r, float* __restrict__ cond_pi,
+                                                   float* __restrict__ cond_m, float* __restrict__ cond_L,
+                                                   float* __restrict__ dir_out, float* __restrict__ pdf_out,
+                                                   uint8_t* __restrict__ valid_out) {
+    constexpr int SPI = 32 / KP;
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int k = lane & (KP - 1), h = lane / KP, base_lane = h * KP;
+    for (int t = 0; t < n; t += SPI) {
+        const int j = t + h;
+        const bool act = j < n;
+        const int src = act ? j : t;
+        const float qx0 = __shfl_sync(FULL, x0, src), qx1 = __shfl_sync(FULL, x1, src),
+                    qx2 = __shfl_sync(FULL, x2, src);
+        const int r = __shfl_sync(FULL, rr, src);
+        float b0 = 0.f, b1 = 0.f, b2 = 0.f;
+        if (OP != OP_CONDITION) {
+            b0 = __shfl_sync(FULL, a0, src);
+            b1 = __shfl_sync(FULL, a1, src);
+            b2 = __shfl_sync(FULL, a2, src);
+        }
+        const bool ok = act && r >= 0;
+        const int rl = r >= 0 ? r : 0;
+        // ---- this lane's component record (reused while the region repeats)
+        if (rl != cur_r) {
+            cur_r = rl;
+            if (k < K) {
+                const float4* s = reinterpret_cast<const float4*>(qtab + ((int64_t)rl * K + k) * kQ);
+#pragma unroll
+                for (int q = 0; q < kQ / 4; ++q) {
+                    const float4 v = __ldg(s + q);
+                    P[4 * q] = v.x;
+                    P[4 * q + 1] = v.y;
+                    P[4 * q + 2] = v.z;
+                    P[4 * q + 3] = v.w;
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < kQ; ++q) P[q] = 0.f;
+                P[11] = 1.f;
+                P[24] = P[26] = P[27] = P[29] = 1.f;
+                P[30] = -INFINITY;
+            }
+        }
+        // ---- conditioning on position: z = A^-1 (x - mu^x)
+        const float e0 = (qx0 - P[0]) - P[32], e1 = (qx1 - P[1]) - P[33],
+                    e2 = (qx2 - P[2]) - P[34];
+        const float z0 = P[12] * e0;
+        const float z1 = P[13] * e0 + P[14] * e1;
+        const float z2 = P[15] * e0 + P[16] * e1 + P[17] * e2;
+        const float lw = P[30] - 0.5f * (z0 * z0 + z1 * z1 + z2 * z2);
+        const float m0 = P[18] * z0 + P[19] * z1 + P[20] * z2;   // C^T z
+        const float m1 = P[21] * z0 + P[22] * z1 + P[23] * z2;
+        // normalise pi'_k over the KP component lanes (log-sum-exp)
+        float mx = lw;
+#pragma unroll
+        for (int o = KP / 2; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(FULL, mx, o));
+        const float e = (mx == -INFINITY) ? 0.f : __expf(lw - mx);
+        float se = e;
+#pragma unroll
+        for (int o = KP / 2; o > 0; o >>= 1) se += __shfl_xor_sync(FULL, se, o);
+        const float cpi = se > 0.f ? __fdividef(e, se) : 0.f;
+        const int64_t qi = __shfl_sync(FULL, (long long)il, src);
+
+        if (OP == OP_CONDITION) {
+            if (act && k < K) {
+                const int64_t o = qi * K + k;
+                cond_pi[o] = ok ? cpi : 0.f;
+                cond_m[2 * o] = m0;
+                cond_m[2 * o + 1] = m1;
+                cond_L[3 * o] = P[24];
+                cond_L[3 * o + 1] = P[25];
+                cond_L[3 * o + 2] = P[26];
+            }
+            continue;
+        }
+
+        float w0 = b0, w1 = b1, w2 = b2;   // direction to evaluate
+        int valid = 1;
+        if (OP == OP_SAMPLE) {
+            // component by inverse CDF on u0 (Sec. 3.1 "Sampling", step i)
+            float cum = e;
+#pragma unroll
+            for (int o = 1; o < KP; o <<= 1) {
+                const float v = __shfl_up_sync(FULL, cum, o);
+                if (k >= o) cum += v;
+            }
+            const float tot = __shfl_sync(FULL, cum, base_lane + KP - 1);
+            const float thr = b0 * tot;
+            const unsigned seg = (KP == 32) ? FULL : (((1u << KP) - 1u) << base_lane);
+            const unsigned hit = __ballot_sync(FULL, k < K && thr < cum) & seg;
+            const unsigned pos = __ballot_sync(FULL, k < K && e > 0.f) & seg;
+            int kk;
+            if (hit) kk = __ffs(hit) - 1 - base_lane;
+            else kk = pos ? (31 - __clz(pos)) - base_lane : 0;
+            // Gaussian draw in the chart (step ii), exp map (step iii)
+            float s0 = 0.f, s1 = 0.f, s2 = 0.f, vv = 0.f;
+            if (k == kk) {
+                const float rad = sqrtf(-2.f * logf(1.f - b1));
+                float sn, cs;
+                sincospif(2.f * b2, &sn, &cs);
+                const float g0 = rad * cs, g1 = rad * sn;
+                const float n0 = m0 + P[24] * g0;
+                const float n1 = m1 + P[25] * g0 + P[26] * g1;
+                const float rn = sqrtf(n0 * n0 + n1 * n1);
+                vv = rn < kPiF ? 1.f : 0.f;
+                float sr, cr;
+                sincosf(rn, &sr, &cr);
+                const float sc = rn < 1e-3f ? 1.f - rn * rn * (1.f / 6.f) : __fdividef(sr, rn);
+                const float c0 = n0 * sc, c1 = n1 * sc;
+                s0 = c0 * P[3] + c1 * P[6] + cr * P[9];
+                s1 = c0 * P[4] + c1 * P[7] + cr * P[10];
+                s2 = c0 * P[5] + c1 * P[8] + cr * P[11];
+            }
+            const int from = base_lane + kk;
+            w0 = __shfl_sync(FULL, s0, from);
+            w1 = __shfl_sync(FULL, s1, from);
+            w2 = __shfl_sync(FULL, s2, from);
+            valid = __shfl_sync(FULL, vv, from) > 0.5f && ok && pos != 0u;
+        }
+        // ---- solid-angle pdf of the conditioned mixture at w (Eq. solidangle-pdf)
+        const float u = P[3] * w0 + P[4] * w1 + P[5] * w2;
+        const float v = P[6] * w0 + P[7] * w1 + P[8] * w2;
+        const float cz = P[9] * w0 + P[10] * w1 + P[11] * w2;
+        const float s2v = u * u + v * v;
+        const bool cut = s2v == 0.f && cz < 0.f;          // antipode: outside the chart
+        const float gg = cut ? 1.f : g_of_cos(cz, rsqrtf(s2v));   // theta / sin(theta) = 1/sinc
+        const float d0 = gg * u - m0, d1 = gg * v - m1;
+        const float y0 = P[27] * d0;
+        const float y1 = P[28] * d0 + P[29] * d1;
+        float pk_ = cpi * __expf(P[31] - 0.5f * (y0 * y0 + y1 * y1)) * gg;
+        if (cut || k >= K) pk_ = 0.f;
+        float p = pk_;
+#pragma unroll
+        for (int o = KP / 2; o > 0; o >>= 1) p += __shfl_xor_sync(FULL, p, o);
+        if (act && k == 0) {
+            if (OP == OP_SAMPLE) {
+                dir_out[3 * qi] = w0;
+                dir_out[3 * qi + 1] = w1;
+                dir_out[3 * qi + 2] = w2;
+                valid_out[qi] = (uint8_t)valid;
+                pdf_out[qi] = valid ? p : 0.f;
+            } else {
+                pdf_out[qi] = ok ? p : 0.f;
+            }
+        }
+    }
+}
 
 template <int KP, int OP>
 __global__ void __launch_bounds__(256)
@@ -20,10 +421,7 @@ __global__ void __launch_bounds__(256)
             float* __restrict__ cond_pi, float* __restrict__ cond_m, float* __restrict__ cond_L,
             float* __restrict__ dir_out, float* __restrict__ pdf_out,
             uint8_t* __restrict__ valid_out) {
-    constexpr int SPI = 32 / KP;
-    constexpr unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    const int k = lane & (KP - 1), h = lane / KP, base_lane = h * KP;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
 
@@ -70,146 +468,8 @@ __global__ void __launch_bounds__(256)
                 a2 = dir_in[3 * i + 2];
             }
         }
-        const int n = (int)min((int64_t)32, Q - g);
-        for (int t = 0; t < n; t += SPI) {
-            const int j = t + h;
-            const bool act = j < n;
-            const int src = act ? j : t;
-            const float qx0 = __shfl_sync(FULL, x0, src), qx1 = __shfl_sync(FULL, x1, src),
-                        qx2 = __shfl_sync(FULL, x2, src);
-            const int r = __shfl_sync(FULL, rr, src);
-            float b0 = 0.f, b1 = 0.f, b2 = 0.f;
-            if (OP != OP_CONDITION) {
-                b0 = __shfl_sync(FULL, a0, src);
-                b1 = __shfl_sync(FULL, a1, src);
-                b2 = __shfl_sync(FULL, a2, src);
-            }
-            const bool ok = act && r >= 0;
-            const int rl = r >= 0 ? r : 0;
-            // ---- this lane's component record (reused while the region repeats)
-            if (rl != cur_r) {
-                cur_r = rl;
-                if (k < K) {
-                    const float4* s = reinterpret_cast<const float4*>(qtab + ((int64_t)rl * K + k) * kQ);
-#pragma unroll
-                    for (int q = 0; q < kQ / 4; ++q) {
-                        const float4 v = __ldg(s + q);
-                        P[4 * q] = v.x;
-                        P[4 * q + 1] = v.y;
-                        P[4 * q + 2] = v.z;
-                        P[4 * q + 3] = v.w;
-                    }
-                } else {
-#pragma unroll
-                    for (int q = 0; q < kQ; ++q) P[q] = 0.f;
-                    P[11] = 1.f;
-                    P[24] = P[26] = P[27] = P[29] = 1.f;
-                    P[30] = -INFINITY;
-                }
-            }
-            // ---- conditioning on position: z = A^-1 (x - mu^x)
-            const float e0 = (qx0 - P[0]) - P[32], e1 = (qx1 - P[1]) - P[33],
-                        e2 = (qx2 - P[2]) - P[34];
-            const float z0 = P[12] * e0;
-            const float z1 = P[13] * e0 + P[14] * e1;
-            const float z2 = P[15] * e0 + P[16] * e1 + P[17] * e2;
-            const float lw = P[30] - 0.5f * (z0 * z0 + z1 * z1 + z2 * z2);
-            const float m0 = P[18] * z0 + P[19] * z1 + P[20] * z2;   // C^T z
-            const float m1 = P[21] * z0 + P[22] * z1 + P[23] * z2;
-            // normalise pi'_k over the KP component lanes (log-sum-exp)
-            float mx = lw;
-#pragma unroll
-            for (int o = KP / 2; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(FULL, mx, o));
-            const float e = (mx == -INFINITY) ? 0.f : __expf(lw - mx);
-            float se = e;
-#pragma unroll
-            for (int o = KP / 2; o > 0; o >>= 1) se += __shfl_xor_sync(FULL, se, o);
-            const float cpi = se > 0.f ? __fdividef(e, se) : 0.f;
-            const int64_t qi = g + j;
-
-            if (OP == OP_CONDITION) {
-                if (act && k < K) {
-                    const int64_t o = qi * K + k;
-                    cond_pi[o] = ok ? cpi : 0.f;
-                    cond_m[2 * o] = m0;
-                    cond_m[2 * o + 1] = m1;
-                    cond_L[3 * o] = P[24];
-                    cond_L[3 * o + 1] = P[25];
-                    cond_L[3 * o + 2] = P[26];
-                }
-                continue;
-            }
-
-            float w0 = b0, w1 = b1, w2 = b2;   // direction to evaluate
-            int valid = 1;
-            if (OP == OP_SAMPLE) {
-                // component by inverse CDF on u0 (Sec. 3.1 "Sampling", step i)
-                float cum = e;
-#pragma unroll
-                for (int o = 1; o < KP; o <<= 1) {
-                    const float v = __shfl_up_sync(FULL, cum, o);
-                    if (k >= o) cum += v;
-                }
-                const float tot = __shfl_sync(FULL, cum, base_lane + KP - 1);
-                const float thr = b0 * tot;
-                const unsigned seg = (KP == 32) ? FULL : (((1u << KP) - 1u) << base_lane);
-                const unsigned hit = __ballot_sync(FULL, k < K && thr < cum) & seg;
-                const unsigned pos = __ballot_sync(FULL, k < K && e > 0.f) & seg;
-                int kk;
-                if (hit) kk = __ffs(hit) - 1 - base_lane;
-                else kk = pos ? (31 - __clz(pos)) - base_lane : 0;
-                // Gaussian draw in the chart (step ii), exp map (step iii)
-                float s0 = 0.f, s1 = 0.f, s2 = 0.f, vv = 0.f;
-                if (k == kk) {
-                    const float rad = sqrtf(-2.f * logf(1.f - b1));
-                    float sn, cs;
-                    sincospif(2.f * b2, &sn, &cs);
-                    const float g0 = rad * cs, g1 = rad * sn;
-                    const float n0 = m0 + P[24] * g0;
-                    const float n1 = m1 + P[25] * g0 + P[26] * g1;
-                    const float rn = sqrtf(n0 * n0 + n1 * n1);
-                    vv = rn < kPiF ? 1.f : 0.f;
-                    float sr, cr;
-                    sincosf(rn, &sr, &cr);
-                    const float sc = rn < 1e-3f ? 1.f - rn * rn * (1.f / 6.f) : __fdividef(sr, rn);
-                    const float c0 = n0 * sc, c1 = n1 * sc;
-                    s0 = c0 * P[3] + c1 * P[6] + cr * P[9];
-                    s1 = c0 * P[4] + c1 * P[7] + cr * P[10];
-                    s2 = c0 * P[5] + c1 * P[8] + cr * P[11];
-                }
-                const int from = base_lane + kk;
-                w0 = __shfl_sync(FULL, s0, from);
-                w1 = __shfl_sync(FULL, s1, from);
-                w2 = __shfl_sync(FULL, s2, from);
-                valid = __shfl_sync(FULL, vv, from) > 0.5f && ok && pos != 0u;
-            }
-            // ---- solid-angle pdf of the conditioned mixture at w (Eq. solidangle-pdf)
-            const float u = P[3] * w0 + P[4] * w1 + P[5] * w2;
-            const float v = P[6] * w0 + P[7] * w1 + P[8] * w2;
-            const float cz = P[9] * w0 + P[10] * w1 + P[11] * w2;
-            const float s2v = u * u + v * v;
-            const bool cut = s2v == 0.f && cz < 0.f;          // antipode: outside the chart
-            const float gg = cut ? 1.f : g_of_cos(cz, rsqrtf(s2v));   // theta / sin(theta) = 1/sinc
-            const float d0 = gg * u - m0, d1 = gg * v - m1;
-            const float y0 = P[27] * d0;
-            const float y1 = P[28] * d0 + P[29] * d1;
-            float pk_ = cpi * __expf(P[31] - 0.5f * (y0 * y0 + y1 * y1)) * gg;
-            if (cut || k >= K) pk_ = 0.f;
-            float p = pk_;
-#pragma unroll
-            for (int o = KP / 2; o > 0; o >>= 1) p += __shfl_xor_sync(FULL, p, o);
-            if (act && k == 0) {
-                if (OP == OP_SAMPLE) {
-                    dir_out[3 * qi] = w0;
-                    dir_out[3 * qi + 1] = w1;
-                    dir_out[3 * qi + 2] = w2;
-                    valid_out[qi] = (uint8_t)valid;
-                    pdf_out[qi] = valid ? p : 0.f;
-                } else {
-                    pdf_out[qi] = ok ? p : 0.f;
-                }
-            }
-        }
+        warp_by_components<KP, OP>(qtab, K, (int)min((int64_t)32, Q - g), i, x0, x1, x2, rr, a0, a1, a2, P,
+                                   cur_r, cond_pi, cond_m, cond_L, dir_out, pdf_out, valid_out);
     }
 }
 
@@ -237,11 +497,170 @@ static cudaError_t launch_query_op(int KP, cudaStream_t s, int grid, const float
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Binning of queries given in any order: a counting sort by region.
+//   k_qbin_keys     region of every query (array or grid; out of range: bin R)
+//                   and the per-bin counts (warp-aggregated atomics)
+//   k_qbin_scan     exclusive prefix sum of the R + 1 counts (one CTA)
+//   k_qbin_scatter  each query's position in its bin (warp-aggregated atomic
+//                   cursor): perm[pos] = query index, key[pos] = its region
+// The order within a bin depends on the atomics; no result does, since every
+// query's output depends only on its own inputs and index.
+__global__ void __launch_bounds__(256) k_qbin_keys(int64_t Q, int64_t R, const float* __restrict__ qx,
+                                                   const int32_t* __restrict__ region, GridF grid,
+                                                   int32_t* __restrict__ key, int32_t* __restrict__ counts) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wstride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < Q; base += wstride) {
+        const int64_t i = base + lane;
+        int r = -1;
+        if (i < Q) {
+            if (region != nullptr) {
+                r = region[i];
+            } else {
+                const float xs[3] = {qx[3 * i], qx[3 * i + 1], qx[3 * i + 2]};
+                int id[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const int v = (int)floorf((xs[c] - grid.lo[c]) * grid.scale[c]);
+                    id[c] = min(max(v, 0), grid.dims[c] - 1);
+                }
+                r = id[0] + grid.dims[0] * (id[1] + grid.dims[1] * id[2]);
+            }
+            if (r < 0 || r >= R) r = (int)R;
+            key[i] = r;
+        }
+        const unsigned m = __match_any_sync(0xffffffffu, r);
+        if (i < Q && lane == __ffs(m) - 1) atomicAdd(counts + r, __popc(m));
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_qbin_scan(int64_t n, int32_t* __restrict__ v) {
+    __shared__ int32_t s_warp[32];
+    __shared__ int32_t s_carry;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < n; base += 1024) {
+        const int64_t e = base + tid;
+        const int32_t c = e < n ? v[e] : 0;
+        int32_t x = c;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int32_t u = __shfl_up_sync(0xffffffffu, x, d);
+            if (lane >= d) x += u;
+        }
+        if (lane == 31) s_warp[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            int32_t w = s_warp[lane];
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int32_t u = __shfl_up_sync(0xffffffffu, w, d);
+                if (lane >= d) w += u;
+            }
+            s_warp[lane] = w;
+        }
+        __syncthreads();
+        const int32_t incl = x + (warp > 0 ? s_warp[warp - 1] : 0);
+        if (e < n) v[e] = s_carry + incl - c;
+        __syncthreads();
+        if (tid == 1023) s_carry += incl;
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(256) k_qbin_scatter(int64_t Q, const int32_t* __restrict__ key_in,
+                                                      int32_t* __restrict__ cursor, int32_t* __restrict__ perm,
+                                                      int32_t* __restrict__ key_out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wstride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < Q; base += wstride) {
+        const int64_t i = base + lane;
+        const int r = i < Q ? key_in[i] : -1;
+        const unsigned m = __match_any_sync(0xffffffffu, r);
+        const int leader = __ffs(m) - 1;
+        int32_t pos = 0;
+        if (i < Q && lane == leader) pos = atomicAdd(cursor + r, __popc(m));
+        pos = __shfl_sync(0xffffffffu, pos, leader) + __popc(m & ((1u << lane) - 1u));
+        if (i < Q) {
+            perm[pos] = (int32_t)i;
+            key_out[pos] = r;
+        }
+    }
+}
+
+size_t qbin_workspace_bytes(int64_t R, int64_t Q) {
+    auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    return up(sizeof(int32_t) * (size_t)(R + 1)) + 3 * up(sizeof(int32_t) * (size_t)Q);
+}
+
+cudaError_t launch_query_binned(cudaStream_t s, int op, int KP, int grid, const float* qtab, int K, int64_t R,
+                                int64_t Q, const float* qx, const int32_t* region, const GridF& g, uint64_t seed,
+                                const float* uni, const float* dir_in, float* dir_out, float* pdf_out,
+                                uint8_t* valid_out, void* ws) {
+    auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    unsigned char* p = static_cast<unsigned char*>(ws);
+    int32_t* counts = reinterpret_cast<int32_t*>(p);
+    p += up(sizeof(int32_t) * (size_t)(R + 1));
+    int32_t* key = reinterpret_cast<int32_t*>(p);
+    p += up(sizeof(int32_t) * (size_t)Q);
+    int32_t* perm = reinterpret_cast<int32_t*>(p);
+    p += up(sizeof(int32_t) * (size_t)Q);
+    int32_t* key_sorted = reinterpret_cast<int32_t*>(p);
+    cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(int32_t) * (size_t)(R + 1), s);
+    if (e != cudaSuccess) return e;
+    const int gb = (int)std::max<int64_t>(1, std::min<int64_t>((Q + 255) / 256, (int64_t)grid * 4));
+    k_qbin_keys<<<gb, 256, 0, s>>>(Q, R, qx, region, g, key, counts);
+    k_qbin_scan<<<1, 1024, 0, s>>>(R + 1, counts);
+    k_qbin_scatter<<<gb, 256, 0, s>>>(Q, key, counts, perm, key_sorted);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return launch_query_q(s, op, KP, grid, qtab, K, R, Q, qx, region, g, perm, key_sorted, seed, uni, dir_in,
+                          dir_out, pdf_out, valid_out);
+}
+
+cudaError_t launch_query_q(cudaStream_t s, int op, int KP, int grid, const float* qtab, int K, int64_t R,
+                           int64_t Q, const float* qx, const int32_t* region, const GridF& g, const int32_t* perm,
+                           const int32_t* key, uint64_t seed, const float* uni, const float* dir_in,
+                           float* dir_out, float* pdf_out, uint8_t* valid_out) {
+    // a persistent grid: every resident CTA walks the queries with a stride
+    int dev = 0, nsm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    (void)grid;
+    const int64_t blocks = (Q + kQWarps * 32 - 1) / (kQWarps * 32);
+    const int gq = (int)std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)nsm * kQCtas));
+#define SDMM_QQ(M)                                                                                           \
+    case M:                                                                                                  \
+        if (op == OP_SAMPLE)                                                                                 \
+            k_query_q<M, OP_SAMPLE><<<gq, kQWarps * 32, 0, s>>>(qtab, K, R, Q, qx, region, g, perm, key, seed, \
+                                                                uni, dir_in, dir_out, pdf_out, valid_out);   \
+        else                                                                                                 \
+            k_query_q<M, OP_PDF><<<gq, kQWarps * 32, 0, s>>>(qtab, K, R, Q, qx, region, g, perm, key, seed,    \
+                                                             uni, dir_in, dir_out, pdf_out, valid_out);      \
+        break;
+    switch (KP) {
+        SDMM_QQ(1)
+        SDMM_QQ(2)
+        SDMM_QQ(4)
+        SDMM_QQ(8)
+        SDMM_QQ(16)
+        default: return cudaErrorInvalidValue;
+    }
+#undef SDMM_QQ
+    return cudaGetLastError();
+}
+
 cudaError_t launch_query(cudaStream_t s, int op, int KP, int grid, const float* qtab, int K,
                          int64_t R, int64_t Q, const float* qx, const int32_t* region,
                          const GridF& g, uint64_t seed, const float* uni, const float* dir_in,
                          float* cond_pi, float* cond_m, float* cond_L, float* dir_out,
                          float* pdf_out, uint8_t* valid_out) {
+    // sampling and pdf with up to 16 components: one thread per query
+    if (op != OP_CONDITION && KP <= 16)
+        return launch_query_q(s, op, KP, grid, qtab, K, R, Q, qx, region, g, nullptr, nullptr, seed, uni, dir_in,
+                              dir_out, pdf_out, valid_out);
     switch (op) {
         case OP_CONDITION:
             return launch_query_op<OP_CONDITION>(KP, s, grid, qtab, K, R, Q, qx, region, g, seed,

@@ -77,3 +77,49 @@ def loglik_err(g, o, mask=None):
     if mask is not None:
         e = e[mask]
     return float(e.max()) if e.size else 0.0
+
+
+EPS32 = 2.0 ** -24
+
+
+def pdf_kappa(ost, K, x, r, om):
+    """First-order FP32 condition number of the conditioned mixture's pdf at
+    direction om (FP64 oracle quantities).  A component contributes
+    pi'_k N_2(y_k) g_k with nu_k = log_{mu_k}(om), y_k = D_k^-1 (nu_k - m_k),
+    g_k = theta/sin(theta).  Rounding the chart coordinates of om moves nu_k by
+    about eps (1 + g_k theta_k) (the log map's gain), so y_k by that over the
+    smallest singular value of D_k, and the exponent -|y|^2/2 by |y_k| times
+    that, plus its own rounding eps |y_k|^2:
+        kappa = max_k 1 + (1 + g_k theta_k) |y_k| / s_min(D_k) + |y_k|^2
+    over the components carrying at least 1e-3 of the pdf.  The pdf's relative
+    error is about eps * kappa."""
+    cpi, cm, cL = orc.condition(K, ost.pi, ost.mu_x, ost.mu_w, ost.L, x[None].astype(np.float32),
+                                np.array([r], np.int32))
+    mw = ost.mu_w.reshape(ost.R, K, 3)[r]
+    terms, kap = [], []
+    for k in range(K):
+        nu, anti, th, sn = orc.log_map(mw[k], om)
+        D = np.array([[cL[0, k, 0], 0.0], [cL[0, k, 1], cL[0, k, 2]]])
+        if anti or np.hypot(*nu) >= np.pi:
+            continue
+        g = th / sn if sn > 0 else 1.0
+        y = np.linalg.solve(D, nu - cm[0, k])
+        ny = float(np.linalg.norm(y))
+        smin = float(np.linalg.svd(D, compute_uv=False).min())
+        terms.append(cpi[0, k] * np.exp(-0.5 * ny * ny) / (2 * np.pi * abs(np.linalg.det(D))) * g)
+        kap.append(1.0 + (1.0 + g * th) * ny / smin + ny * ny)
+    if not terms:
+        return 1.0
+    p = sum(terms)
+    return max((kk for t, kk in zip(terms, kap) if t >= 1e-3 * p), default=1.0)
+
+
+def assert_pdf_close(p_gpu, p_oracle, ost, K, qx, reg, dirs, bulk=0.999):
+    """pdf parity: every value within max(PDF_RTOL, 32 eps kappa) of the FP64
+    pdf at the same direction, and the contract PDF_RTOL itself for the bulk."""
+    rel = np.abs(p_gpu - p_oracle) / p_oracle
+    assert np.mean(rel < PDF_RTOL) >= bulk, np.quantile(rel, [0.5, 0.99, 0.999, 1.0])
+    for q in np.flatnonzero(rel >= PDF_RTOL):
+        kap = pdf_kappa(ost, K, qx[q], int(reg[q]), dirs[q])
+        assert rel[q] < 32 * EPS32 * kap, (q, rel[q], kap)
+    return rel

@@ -86,3 +86,24 @@ def test_host_validation_errors(lib):
     assert lib.sdmm_fit_workspace_size(ctypes.byref(api.config(16, dir_coords=2)), 1, 10, ctypes.byref(n)) == 1
     assert lib.sdmm_condition(ctypes.byref(api.config(16, dir_coords=1)), None, 1, 1, None, None, ctypes.byref(g),
                               None, None, None, None) in (1, 4)
+
+
+def test_noalloc_scratch_constant_matches_the_header():
+    from paper_2111_13094_gb300 import _lib
+    with open(os.path.join(ROOT, "include", "sdmm.h")) as f:
+        src = f.read()
+    m = re.search(r"#define\s+SDMM_NOALLOC_SCRATCH_BYTES\s+\(([^)]*)\)", src)
+    assert m is not None
+    value = eval(m.group(1).replace("u", ""), {})          # e.g. 16u * 1024u * 1024u
+    assert value == _lib.SDMM_NOALLOC_SCRATCH_BYTES
+
+
+def test_binned_query_workspace_checks(lib):
+    from paper_2111_13094_gb300 import _lib, api
+    n = ctypes.c_size_t()
+    assert lib.sdmm_query_workspace_size(65536, 1 << 24, ctypes.byref(n)) == 0
+    assert n.value >= 4 * (65536 + 1) + 12 * (1 << 24) and n.value % 256 == 0
+    assert lib.sdmm_query_workspace_size(0, 10, ctypes.byref(n)) == 1
+    assert lib.sdmm_query_workspace_size(4, -1, ctypes.byref(n)) == 1
+    assert lib.sdmm_sample_binned(ctypes.byref(api.config(16)), None, 1, 1, None, None, None, 0, None, None, None,
+                                  None, None, 0, None) == 1

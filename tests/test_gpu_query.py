@@ -8,7 +8,7 @@ import torch
 from scipy import stats
 
 import oracle as orc
-from gpu_util import PDF_RTOL, gpu_state
+from gpu_util import PDF_RTOL, assert_pdf_close, gpu_state
 from paper_2111_13094_gb300 import api
 from paper_2111_13094_gb300 import synthetic as syn
 
@@ -69,9 +69,8 @@ def test_sample_and_pdf_match_oracle(K):
     # the reported pdf equals the FP64 pdf of the returned (FP32) direction
     po = orc.pdf(K, ost.pi, ost.mu_x, ost.mu_w, ost.L, qx, reg, d.astype(np.float64))
     vv = v == 1
-    rel = np.abs(p[vv] - po[vv]) / po[vv]
-    assert np.quantile(rel, 0.999) < PDF_RTOL, np.quantile(rel, [0.5, 0.99, 0.999, 1.0])
-    assert rel.max() < 10 * PDF_RTOL
+    rel = assert_pdf_close(p[vv], po[vv], ost, K, qx[vv], reg[vv], d[vv].astype(np.float64))
+    print(K, "pdf rel quantiles", np.quantile(rel, [0.5, 0.99, 0.999, 1.0]))
     assert np.all(p[~vv] == 0)
 
 
@@ -91,9 +90,9 @@ def test_pdf_entry_matches_oracle():
                 region=torch.from_numpy(reg).cuda()).cpu().numpy()
     po = orc.pdf(K, ost.pi, ost.mu_x, ost.mu_w, ost.L, qx, reg, dirs.astype(np.float64))
     big = po > 1e-6 * po.max()
-    rel = np.abs(p[big] - po[big]) / po[big]
-    assert np.quantile(rel, 0.999) < PDF_RTOL, np.quantile(rel, [0.5, 0.99, 0.999, 1.0])
-    assert np.abs(p - po).max() < 1e-4 * po.max()
+    rel = assert_pdf_close(p[big], po[big], ost, K, qx[big], reg[big], dirs[big].astype(np.float64))
+    print("pdf entry rel quantiles", np.quantile(rel, [0.5, 0.99, 0.999, 1.0]))
+    assert np.abs(p - po).max() < 1e-5 * po.max()
 
 
 def test_philox_and_grid_paths_are_exact():
@@ -180,7 +179,10 @@ def test_query_workload_16M_sampled_against_oracle():
     Q = 16 * 2 ** 20
     qx = syn.query_points(13, Q)
     tq = torch.from_numpy(qx).cuda()
-    d, p, v = api.sample(cfg, st, tq, grid=api.Grid((0, 0, 0), (1, 1, 1), dims), seed=99)
+    # the launch configuration the benchmark times: queries as given, binned by
+    # region in the library's workspace
+    d, p, v = api.sample(cfg, st, tq, grid=api.Grid((0, 0, 0), (1, 1, 1), dims), seed=99,
+                         ws=api.query_workspace(st.R, Q))
     torch.cuda.synchronize()
     idx = np.sort(np.random.default_rng(14).choice(Q, 20000, replace=False))
     u = orc.uniforms(99, Q)[idx]
@@ -195,7 +197,48 @@ def test_query_workload_16M_sampled_against_oracle():
     assert _angle(dg[ok], o["dir"][ok]).max() < 1e-4
     po = orc.pdf(K, ost.pi, ost.mu_x, ost.mu_w, ost.L, qx[idx], reg, dg)
     vv = vg == 1
-    rel = np.abs(pg[vv] - po[vv]) / po[vv]
-    assert np.quantile(rel, 0.999) < PDF_RTOL
+    assert_pdf_close(pg[vv], po[vv], ost, K, qx[idx][vv], reg[vv], dg[vv])
     # discard rate (|nu| >= pi) is small, as the paper reports for its lobes
     assert 1.0 - v.float().mean().item() < 0.01
+
+
+@pytest.mark.parametrize("K", [3, 16, 32])
+def test_binned_entry_points_match_the_oracle(K):
+    """sdmm_sample_binned / sdmm_pdf_binned (queries in any order, binned by
+    region inside the library) against the oracle on the same queries and
+    uniforms: validity, directions and pdfs under the sampling tolerances,
+    with region ids (including ids out of range: valid = 0, pdf = 0) and with
+    the grid lookup; a short workspace is rejected."""
+    dims = (8, 4, 4)
+    ost = _mixtures(21, dims, K)
+    cfg = api.config(K)
+    st = gpu_state(ost, cfg)
+    Q = 40000
+    qx, reg = _queries(22, Q, dims)
+    reg = reg.copy()
+    reg[::997] = -1
+    tq, tr = torch.from_numpy(qx).cuda(), torch.from_numpy(reg).cuda()
+    ws = api.query_workspace(st.R, Q)
+    grid = api.Grid((0, 0, 0), (1, 1, 1), dims)
+    u = orc.uniforms(77, Q)
+    good = reg >= 0
+    o = orc.sample(K, ost.pi, ost.mu_x, ost.mu_w, ost.L, qx[good], reg[good], u[good])
+    same = o["margin"] > 1e-5
+    for kw, sel in ((dict(region=tr), good), (dict(grid=grid), np.ones(Q, bool))):
+        dt, pt, vt = api.sample(cfg, st, tq, seed=77, ws=ws, **kw)
+        # the binned pdf entry at the sampled directions gives the sampled pdfs
+        pe = api.pdf(cfg, st, tq, dt, ws=ws, **kw).cpu().numpy()[good]
+        d, p, v = dt.cpu().numpy(), pt.cpu().numpy(), vt.cpu().numpy()
+        if "region" in kw:
+            assert not v[~good].any() and not p[~good].any()
+        d, p, v = d[good], p[good], v[good]
+        assert np.array_equal(v[same], o["valid"][same])
+        ok = same & (o["valid"] == 1)
+        assert _angle(d[ok].astype(np.float64), o["dir"][ok]).max() < 1e-4
+        vv = v == 1
+        po = orc.pdf(K, ost.pi, ost.mu_x, ost.mu_w, ost.L, qx[good][vv], reg[good][vv], d[vv].astype(np.float64))
+        assert_pdf_close(p[vv], po, ost, K, qx[good][vv], reg[good][vv], d[vv].astype(np.float64))
+        assert np.allclose(pe[vv], p[vv], rtol=1e-6, atol=0)
+    if K <= 16:                                       # the binned path needs its workspace
+        with pytest.raises(api.SdmmError):
+            api.sample(cfg, st, tq, seed=77, region=tr, ws=ws[: ws.numel() // 2])
