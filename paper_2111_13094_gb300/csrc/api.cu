@@ -626,7 +626,7 @@ static sdmm_status objective_common(const sdmm_config* cfg, const sdmm_samples* 
     SDMM_CUDA(launch_build_chunks(stream, w.hdr, w.cb, w.cr, nullptr, L.chunk, 1, L.max_chunks), "build_chunks");
     SDMM_CUDA(launch_accumulate(stream, dF ? MODE_GRAD : MODE_FIT, KP, nsm * default_ctas(cfg), w.hdr,
                                 w.cb, w.cr, st->etab, cfg->K, L.chunk, cfg->estep_density, w.partial,
-                                L.ps, 0, nullptr, cfg->dir_coords == SDMM_DIR_EUCLIDEAN),
+                                L.ps, 0, nullptr, cfg->dir_coords == SDMM_DIR_EUCLIDEAN, 1),
               "accumulate");
     SDMM_CUDA(launch_reduce_objective(stream, s->R, w.hdr, w.cb, w.partial, L.ps, *cfg, *st, F_out, dF,
                                       gd, gL, ga),

@@ -23,25 +23,30 @@
 // batch with the exact per-sample maximum, as in k_accumulate.
 #include "common.cuh"
 #include "kernels.h"
+#include "tc.cuh"
 
 namespace sdmm {
 
 namespace {
-constexpr int kEW = 8;                          // warps per CTA
+constexpr int kEW = 4;                          // warps per CTA
+constexpr int kECtas = 5;                       // resident CTAs per SM (96 registers per thread)
 constexpr float kLog2eF = 1.44269504088896341f;
 constexpr float kLn2F = 0.693147180559945309f;
 constexpr float kHalfLog2eSqrt = 0.849321800288019f;   // sqrt(log2(e) / 2)
 constexpr float kSumMin = 1e-30f;               // smallest trusted shifted sum
 
-__device__ __forceinline__ float ex2f(float x) {
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
+// *p = (a, b) in shared memory if `pred`, as one predicated store
+__device__ __forceinline__ void st_shared_pred(bool pred, float2* p, float a, float b) {
+    const uint32_t addr = static_cast<uint32_t>(__cvta_generic_to_shared(p));
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %0, 0;\n\t@q st.shared.v2.f32 [%1], {%2, %3};\n\t}" ::"r"((int)pred),
+        "r"(addr), "f"(a), "f"(b)
+        : "memory");
 }
 }  // namespace
 
-template <int KP>
-__global__ void __launch_bounds__(kEW * 32, 2)
+template <int KP, bool OFFS>
+__global__ void __launch_bounds__(kEW * 32, kECtas)
     k_estep(WsHeader* __restrict__ ws, const int64_t* __restrict__ chunk_base,
             const int32_t* __restrict__ chunk_region, const float* __restrict__ etab, int K, int chunk,
             float* __restrict__ partial, int ps, int write_ll) {
@@ -70,8 +75,9 @@ __global__ void __launch_bounds__(kEW * 32, 2)
     const int64_t R = ws->desc.R;
 
     // this lane's component: R_mu rows (t, b, mu), mean offset from the
-    // reference point (3) and in-chart direction offset (2), scaled L^-1,
-    // base-2 constant shifted by the region bound
+    // reference point (3) and, with OFFS (the objective at offset means), the
+    // in-chart direction offset (2), scaled L^-1, base-2 constant shifted by
+    // the region bound
     float rt[9], mo[5], li[15];
 #pragma unroll
     for (int q = 0; q < 9; ++q) rt[q] = 0.f;
@@ -90,13 +96,14 @@ __global__ void __launch_bounds__(kEW * 32, 2)
         const float v = rt[3] * sb.x + rt[4] * sb.y + rt[5] * sb.z;
         const float cz = rt[6] * sb.x + rt[7] * sb.y + rt[8] * sb.z;
         const float s2 = u * u + v * v;
-        const bool cut = s2 == 0.f && cz < 0.f;     // antipode of the mean: no chart
-        const float gg = cut ? 1.f : g_of_cos(cz, rsqrtf(s2));
+        // 1/sin(theta) clamped so that g stays finite (and d with it) at the
+        // antipode of the mean, which has no chart: its density is 0 below
+        const float gg = g_of_cos_fit(cz, fminf(tc::rsqrt_approx(s2), 1e18f));
         d[0] = sa.x - mo[0];
         d[1] = sa.y - mo[1];
         d[2] = sa.z - mo[2];
-        d[3] = gg * u - mo[3];
-        d[4] = gg * v - mo[4];
+        d[3] = OFFS ? gg * u - mo[3] : gg * u;
+        d[4] = OFFS ? gg * v - mo[4] : gg * v;
         const float y0 = li[0] * d[0];
         const float y1 = li[1] * d[0] + li[2] * d[1];
         const float y2 = li[3] * d[0] + li[4] * d[1] + li[5] * d[2];
@@ -107,6 +114,7 @@ __global__ void __launch_bounds__(kEW * 32, 2)
         l2 = fmaf(-y2, y2, l2);
         l2 = fmaf(-y3, y3, l2);
         l2 = fmaf(-y4, y4, l2);
+        const bool cut = !(s2 >= 1.17549435e-38f) && cz < 0.f;   // to within 1e-19 rad
         return cut ? -INFINITY : l2;
     };
 
@@ -215,20 +223,21 @@ __global__ void __launch_bounds__(kEW * 32, 2)
                 const float4 xa = s_x[warp][ja], wa = s_w[warp][ja];
                 const float4 xb = s_x[warp][jb], wb = s_w[warp][jb];
                 float da[5], db[5];
-                const float ea = ex2f(logp2(xa, wa, da));
-                const float eb = ex2f(logp2(xb, wb, db));
+                const float ea = tc::ex2_approx(logp2(xa, wa, da));
+                const float eb = tc::ex2_approx(logp2(xb, wb, db));
                 float sa = ea, sb = eb;
 #pragma unroll
                 for (int o = KP / 2; o > 0; o >>= 1) {
                     sa += __shfl_xor_sync(FULL, sa, o);
                     sb += __shfl_xor_sync(FULL, sb, o);
                 }
-                if (k == 0) {
-                    s_lse[warp][ja] = make_float2(sa, lmax);
-                    s_lse[warp][jb] = make_float2(sb, lmax);
-                }
-                const float ra = sa >= kSumMin ? __fdividef(xa.w * ea, sa) : 0.f;
-                const float rb = sb >= kSumMin ? __fdividef(xb.w * eb, sb) : 0.f;
+                // the component-0 lane of each sample slot records the sums
+                // (predicated stores: no branch in the pair loop)
+                st_shared_pred(k == 0, &s_lse[warp][ja], sa, lmax);
+                st_shared_pred(k == 0, &s_lse[warp][jb], sb, lmax);
+                const float ia = tc::rcp_approx(sa), ib = tc::rcp_approx(sb);
+                const float ra = sa >= kSumMin ? xa.w * ea * ia : 0.f;
+                const float rb = sb >= kSumMin ? xb.w * eb * ib : 0.f;
                 accumulate(ra, da);
                 accumulate(rb, db);
             }
@@ -248,7 +257,7 @@ __global__ void __launch_bounds__(kEW * 32, 2)
                 float ref = l2;
 #pragma unroll
                 for (int o = KP / 2; o > 0; o >>= 1) ref = fmaxf(ref, __shfl_xor_sync(FULL, ref, o));
-                const float e = (ref == -INFINITY) ? 0.f : ex2f(l2 - ref);
+                const float e = (ref == -INFINITY) ? 0.f : tc::ex2_approx(l2 - ref);
                 float se = e;
 #pragma unroll
                 for (int o = KP / 2; o > 0; o >>= 1) se += __shfl_xor_sync(FULL, se, o);
@@ -303,14 +312,30 @@ bool estep_fast_supported(int KP) { return KP >= 4 && KP <= 32; }
 
 cudaError_t launch_estep_fast(cudaStream_t s, int KP, int grid, WsHeader* ws, const int64_t* cb,
                               const int32_t* cr, const float* etab, int K, int chunk, float* partial,
-                              int ps, int write_ll) {
+                              int ps, int write_ll, int offsets) {
+    // persistent grid of every resident CTA (the work queue balances the
+    // units); the caller's grid, sized for the 8-warp kernels, is not used
+    (void)grid;
+    int dev = 0, nsm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    grid = nsm * kECtas;
+#define SDMM_ESTEP(P)                                                                                      \
+    case P:                                                                                                \
+        if (offsets)                                                                                       \
+            k_estep<P, true><<<grid, kEW * 32, 0, s>>>(ws, cb, cr, etab, K, chunk, partial, ps, write_ll); \
+        else                                                                                               \
+            k_estep<P, false><<<grid, kEW * 32, 0, s>>>(ws, cb, cr, etab, K, chunk, partial, ps, write_ll); \
+        break;
     switch (KP) {
-        case 4: k_estep<4><<<grid, kEW * 32, 0, s>>>(ws, cb, cr, etab, K, chunk, partial, ps, write_ll); break;
-        case 8: k_estep<8><<<grid, kEW * 32, 0, s>>>(ws, cb, cr, etab, K, chunk, partial, ps, write_ll); break;
-        case 16: k_estep<16><<<grid, kEW * 32, 0, s>>>(ws, cb, cr, etab, K, chunk, partial, ps, write_ll); break;
-        case 32: k_estep<32><<<grid, kEW * 32, 0, s>>>(ws, cb, cr, etab, K, chunk, partial, ps, write_ll); break;
+        SDMM_ESTEP(4)
+        SDMM_ESTEP(8)
+        SDMM_ESTEP(16)
+        SDMM_ESTEP(32)
         default: return cudaErrorInvalidValue;
     }
+#undef SDMM_ESTEP
     return cudaGetLastError();
 }
 

@@ -1036,9 +1036,9 @@ cudaError_t launch_build_chunks(cudaStream_t s, WsHeader* ws, int64_t* cb, int32
 cudaError_t launch_accumulate(cudaStream_t s, int mode, int KP, int grid, WsHeader* ws,
                               const int64_t* cb, const int32_t* cr, const float* etab, int K,
                               int chunk, int density, float* partial, int ps, int write_ll,
-                              const float* chart2, int euclid) {
+                              const float* chart2, int euclid, int chart_offsets) {
     if (mode == MODE_FIT && density == SDMM_DENSITY_TANGENT && !euclid && estep_fast_supported(KP))
-        return launch_estep_fast(s, KP, grid, ws, cb, cr, etab, K, chunk, partial, ps, write_ll);
+        return launch_estep_fast(s, KP, grid, ws, cb, cr, etab, K, chunk, partial, ps, write_ll, chart_offsets);
     if (mode == MODE_FIT)
         return launch_acc_mode<MODE_FIT>(KP, dim3(grid), s, ws, cb, cr, etab, K, chunk, density,
                                          partial, ps, write_ll, nullptr, euclid);

@@ -25,12 +25,12 @@ cudaError_t launch_build_chunks(cudaStream_t s, WsHeader* ws, int64_t* cb, int32
 cudaError_t launch_accumulate(cudaStream_t s, int mode, int KP, int grid, WsHeader* ws,
                               const int64_t* cb, const int32_t* cr, const float* etab, int K,
                               int chunk, int density, float* partial, int ps, int write_ll,
-                              const float* chart2 = nullptr, int euclid = 0);
+                              const float* chart2 = nullptr, int euclid = 0, int chart_offsets = 0);
 // specialised E-step of the plain fit (chart density, tangent charts), KP in 4..32
 bool estep_fast_supported(int KP);
 cudaError_t launch_estep_fast(cudaStream_t s, int KP, int grid, WsHeader* ws, const int64_t* cb,
                               const int32_t* cr, const float* etab, int K, int chunk, float* partial,
-                              int ps, int write_ll);
+                              int ps, int write_ll, int offsets);
 cudaError_t launch_new_charts(cudaStream_t s, int64_t R, WsHeader* ws, const int64_t* cb,
                               const float* partial, int ps, const sdmm_config& cfg,
                               const sdmm_state& st, float* chart2);

@@ -9,9 +9,9 @@ import numpy as np
 from conftest import ROOT
 
 
-def _coefficients():
+def _coefficients(name="g_of_cos"):
     src = open(os.path.join(ROOT, "paper_2111_13094_gb300", "csrc", "common.cuh")).read()
-    body = src[src.index("float g_of_cos"):]
+    body = src[src.index(f"float {name}("):]
     body = body[:body.index("return")]
     first = re.search(r"float p = (-?[0-9.e-]+)f;", body).group(1)
     rest = re.findall(r"p = fmaf\(p, t, (-?[0-9.e-]+)f\)", body)
@@ -46,4 +46,23 @@ def test_g_of_cos_accuracy():
     assert rel[cd >= 0].max() < 1.5e-7
     assert rel[cd < 0].max() < 4e-7
     # the chart centre is exact
+    assert _g_of_cos_f32(np.array([1.0]), np.array([np.inf]), coef)[0] == np.float32(1.0)
+
+
+def test_g_of_cos_fit_accuracy():
+    """The degree-7 form of the fit's E-step: within 6e-7 for c >= 0 and
+    within 1e-6 past pi / 2 (the pi / sin branch)."""
+    coef = _coefficients("g_of_cos_fit")
+    assert len(coef) == 8 and coef[-1] == np.float32(1.0)
+    th = np.linspace(0.0, np.pi, 2_000_001)[:-1]
+    c32 = np.cos(th).astype(np.float32)
+    s32 = np.sin(th).astype(np.float32)
+    rs = np.where(s32 > 0, 1.0 / np.maximum(s32.astype(np.float64), 1e-300), np.inf)
+    got = _g_of_cos_f32(c32, rs, coef).astype(np.float64)
+    cd, sd = c32.astype(np.float64), s32.astype(np.float64)
+    ang = np.arctan2(sd, cd)
+    ref = np.where(sd > 0, ang / np.where(sd > 0, sd, 1.0), 1.0)
+    rel = np.abs(got - ref) / ref
+    assert rel[cd >= 0].max() < 6e-7
+    assert rel[cd < 0].max() < 1e-6
     assert _g_of_cos_f32(np.array([1.0]), np.array([np.inf]), coef)[0] == np.float32(1.0)
