@@ -45,7 +45,12 @@ __device__ __forceinline__ void st_shared_pred(bool pred, float2* p, float a, fl
 }
 }  // namespace
 
-template <int KP, bool OFFS>
+// OFFS: records carry an in-chart direction offset (the objective at offset
+// means, and the Euclidean ablation's mean); EUCL: the Euclidean ablation
+// (direction coordinates without the log map, g = 1); SOLID: the solid-angle
+// density p^t / sinc of the E-step, whose log Jacobian lifts a component above
+// the region bound, so every sample takes the exact per-sample maximum.
+template <int KP, bool OFFS, bool EUCL, bool SOLID>
 __global__ void __launch_bounds__(kEW * 32, kECtas)
     k_estep(WsHeader* __restrict__ ws, const int64_t* __restrict__ chunk_base,
             const int32_t* __restrict__ chunk_region, const float* __restrict__ etab, int K, int chunk,
@@ -98,7 +103,7 @@ __global__ void __launch_bounds__(kEW * 32, kECtas)
         const float s2 = u * u + v * v;
         // 1/sin(theta) clamped so that g stays finite (and d with it) at the
         // antipode of the mean, which has no chart: its density is 0 below
-        const float gg = g_of_cos_fit(cz, fminf(tc::rsqrt_approx(s2), 1e18f));
+        const float gg = EUCL ? 1.f : g_of_cos_fit(cz, fminf(tc::rsqrt_approx(s2), 1e18f));
         d[0] = sa.x - mo[0];
         d[1] = sa.y - mo[1];
         d[2] = sa.z - mo[2];
@@ -114,6 +119,8 @@ __global__ void __launch_bounds__(kEW * 32, kECtas)
         l2 = fmaf(-y2, y2, l2);
         l2 = fmaf(-y3, y3, l2);
         l2 = fmaf(-y4, y4, l2);
+        if (SOLID) l2 += tc::lg2_approx(gg);                       // p^t / sinc: + log2(theta / sin)
+        if (EUCL) return l2;
         const bool cut = !(s2 >= 1.17549435e-38f) && cz < 0.f;   // to within 1e-19 rad
         return cut ? -INFINITY : l2;
     };
@@ -223,8 +230,20 @@ __global__ void __launch_bounds__(kEW * 32, kECtas)
                 const float4 xa = s_x[warp][ja], wa = s_w[warp][ja];
                 const float4 xb = s_x[warp][jb], wb = s_w[warp][jb];
                 float da[5], db[5];
-                const float ea = tc::ex2_approx(logp2(xa, wa, da));
-                const float eb = tc::ex2_approx(logp2(xb, wb, db));
+                const float la = logp2(xa, wa, da), lb = logp2(xb, wb, db);
+                float refa = 0.f, refb = 0.f;       // shift on top of the region bound
+                if (SOLID) {
+                    refa = la, refb = lb;
+#pragma unroll
+                    for (int o = KP / 2; o > 0; o >>= 1) {
+                        refa = fmaxf(refa, __shfl_xor_sync(FULL, refa, o));
+                        refb = fmaxf(refb, __shfl_xor_sync(FULL, refb, o));
+                    }
+                    refa = refa == -INFINITY ? 0.f : refa;
+                    refb = refb == -INFINITY ? 0.f : refb;
+                }
+                const float ea = tc::ex2_approx(la - refa);
+                const float eb = tc::ex2_approx(lb - refb);
                 float sa = ea, sb = eb;
 #pragma unroll
                 for (int o = KP / 2; o > 0; o >>= 1) {
@@ -233,8 +252,8 @@ __global__ void __launch_bounds__(kEW * 32, kECtas)
                 }
                 // the component-0 lane of each sample slot records the sums
                 // (predicated stores: no branch in the pair loop)
-                st_shared_pred(k == 0, &s_lse[warp][ja], sa, lmax);
-                st_shared_pred(k == 0, &s_lse[warp][jb], sb, lmax);
+                st_shared_pred(k == 0, &s_lse[warp][ja], sa, SOLID ? lmax + refa * kLn2F : lmax);
+                st_shared_pred(k == 0, &s_lse[warp][jb], sb, SOLID ? lmax + refb * kLn2F : lmax);
                 const float ia = tc::rcp_approx(sa), ib = tc::rcp_approx(sb);
                 const float ra = sa >= kSumMin ? xa.w * ea * ia : 0.f;
                 const float rb = sb >= kSumMin ? xb.w * eb * ib : 0.f;
@@ -312,7 +331,7 @@ bool estep_fast_supported(int KP) { return KP >= 4 && KP <= 32; }
 
 cudaError_t launch_estep_fast(cudaStream_t s, int KP, int grid, WsHeader* ws, const int64_t* cb,
                               const int32_t* cr, const float* etab, int K, int chunk, float* partial,
-                              int ps, int write_ll, int offsets) {
+                              int ps, int write_ll, int variant) {
     // persistent grid of every resident CTA (the work queue balances the
     // units); the caller's grid, sized for the 8-warp kernels, is not used
     (void)grid;
@@ -321,12 +340,23 @@ cudaError_t launch_estep_fast(cudaStream_t s, int KP, int grid, WsHeader* ws, co
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
     grid = nsm * kECtas;
-#define SDMM_ESTEP(P)                                                                                      \
-    case P:                                                                                                \
-        if (offsets)                                                                                       \
-            k_estep<P, true><<<grid, kEW * 32, 0, s>>>(ws, cb, cr, etab, K, chunk, partial, ps, write_ll); \
-        else                                                                                               \
-            k_estep<P, false><<<grid, kEW * 32, 0, s>>>(ws, cb, cr, etab, K, chunk, partial, ps, write_ll); \
+#define SDMM_ESTEP(P)                                                                                  \
+    case P:                                                                                            \
+        if (variant == ESTEP_EUCLID)                                                                   \
+            k_estep<P, true, true, false><<<grid, kEW * 32, 0, s>>>(ws, cb, cr, etab, K, chunk, partial, ps, \
+                                                                    write_ll);                         \
+        else if (variant == ESTEP_SOLID)                                                               \
+            k_estep<P, false, false, true><<<grid, kEW * 32, 0, s>>>(ws, cb, cr, etab, K, chunk, partial, ps, \
+                                                                     write_ll);                        \
+        else if (variant == ESTEP_SOLID_OFFSETS)                                                       \
+            k_estep<P, true, false, true><<<grid, kEW * 32, 0, s>>>(ws, cb, cr, etab, K, chunk, partial, ps,  \
+                                                                    write_ll);                         \
+        else if (variant == ESTEP_OFFSETS)                                                             \
+            k_estep<P, true, false, false><<<grid, kEW * 32, 0, s>>>(ws, cb, cr, etab, K, chunk, partial, ps, \
+                                                                     write_ll);                        \
+        else                                                                                           \
+            k_estep<P, false, false, false><<<grid, kEW * 32, 0, s>>>(ws, cb, cr, etab, K, chunk, partial,   \
+                                                                      ps, write_ll);                   \
         break;
     switch (KP) {
         SDMM_ESTEP(4)

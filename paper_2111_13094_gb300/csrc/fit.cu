@@ -1037,8 +1037,13 @@ cudaError_t launch_accumulate(cudaStream_t s, int mode, int KP, int grid, WsHead
                               const int64_t* cb, const int32_t* cr, const float* etab, int K,
                               int chunk, int density, float* partial, int ps, int write_ll,
                               const float* chart2, int euclid, int chart_offsets) {
-    if (mode == MODE_FIT && density == SDMM_DENSITY_TANGENT && !euclid && estep_fast_supported(KP))
-        return launch_estep_fast(s, KP, grid, ws, cb, cr, etab, K, chunk, partial, ps, write_ll, chart_offsets);
+    if (mode == MODE_FIT && estep_fast_supported(KP)) {
+        const bool solid = density == SDMM_DENSITY_SOLID_ANGLE;
+        const int variant = euclid ? ESTEP_EUCLID
+                            : solid ? (chart_offsets ? ESTEP_SOLID_OFFSETS : ESTEP_SOLID)
+                                    : (chart_offsets ? ESTEP_OFFSETS : ESTEP_CHART);
+        return launch_estep_fast(s, KP, grid, ws, cb, cr, etab, K, chunk, partial, ps, write_ll, variant);
+    }
     if (mode == MODE_FIT)
         return launch_acc_mode<MODE_FIT>(KP, dim3(grid), s, ws, cb, cr, etab, K, chunk, density,
                                          partial, ps, write_ll, nullptr, euclid);

@@ -26,11 +26,12 @@ cudaError_t launch_accumulate(cudaStream_t s, int mode, int KP, int grid, WsHead
                               const int64_t* cb, const int32_t* cr, const float* etab, int K,
                               int chunk, int density, float* partial, int ps, int write_ll,
                               const float* chart2 = nullptr, int euclid = 0, int chart_offsets = 0);
-// specialised E-step of the plain fit (chart density, tangent charts), KP in 4..32
+// specialised E-step of the fit and the objective's forward pass, KP in 4..32
+enum { ESTEP_CHART = 0, ESTEP_OFFSETS = 1, ESTEP_EUCLID = 2, ESTEP_SOLID = 3, ESTEP_SOLID_OFFSETS = 4 };
 bool estep_fast_supported(int KP);
 cudaError_t launch_estep_fast(cudaStream_t s, int KP, int grid, WsHeader* ws, const int64_t* cb,
                               const int32_t* cr, const float* etab, int K, int chunk, float* partial,
-                              int ps, int write_ll, int offsets);
+                              int ps, int write_ll, int variant);
 cudaError_t launch_new_charts(cudaStream_t s, int64_t R, WsHeader* ws, const int64_t* cb,
                               const float* partial, int ps, const sdmm_config& cfg,
                               const sdmm_state& st, float* chart2);

