@@ -128,7 +128,12 @@ typedef struct sdmm_config {
                                   0 = library heuristic; else a multiple of
                                   256 in [256, 65536]                        */
     int32_t ctas_per_sm;       /* resident CTAs per SM of the persistent fit
-                                  kernels; 0 = library default, else 1..4     */
+                                  kernels; 0 = library default, else 1..4.
+                                  The E-step of the fit and of the objective
+                                  for K >= 3 runs one grid of every resident
+                                  CTA (five 4-warp CTAs per SM) and ignores
+                                  it; it applies to the adjoint, the second
+                                  pass of the two-pass update and K <= 2     */
     int32_t cov_update;        /* SDMM_COV_*: the covariance of the new mean's
                                   chart from the first-order chart change of
                                   the averaged statistics (Sec. 3.4, default),
@@ -429,7 +434,9 @@ sdmm_status sdmm_fit_plan_destroy(sdmm_fit_plan *plan);
 /*
  * Autotuner: times the E-step kernel on this batch for candidate chunk sizes
  * and CTAs per SM (without touching the state's parameters; the statistics
- * go to the workspace) and returns the fastest pair.  Synchronises `stream`.
+ * go to the workspace) and returns the fastest pair.  Where the E-step
+ * ignores ctas_per_sm (K >= 3) only the chunk is tuned and *ctas_per_sm_out
+ * is 0 (the default).  Synchronises `stream`.
  * The workspace must be sized for the largest candidate: use
  * sdmm_fit_workspace_size with chunk = 256.
  */

@@ -952,11 +952,13 @@ sdmm_status sdmm_autotune(const sdmm_config* cfg, const sdmm_samples* s, const s
     float best = INFINITY;
     int best_c = 0, best_g = 0;
     const int chunks[] = {256, 512, 1024, 2048, 4096, 8192};
+    // the specialised E-step sizes its own grid: only the chunk is tuned
+    const int g_max = estep_fast_supported(KP) ? 1 : 4;
     for (int c : chunks) {
         const Layout L = layout(cfg, s->R, s->N, c);
         if (L.total > ws_bytes || !workspace) continue;
         const WsPtrs w = ws_ptrs(workspace, L);
-        for (int g = 1; g <= 4; ++g) {
+        for (int g = 1; g <= g_max; ++g) {
             float tmin = INFINITY;
             for (int rep = 0; rep < 4; ++rep) {
                 if (launch_set_desc(stream, w.hdr, make_desc(s, nullptr, nullptr)) != cudaSuccess ||
@@ -984,7 +986,7 @@ sdmm_status sdmm_autotune(const sdmm_config* cfg, const sdmm_samples* s, const s
     cudaEventDestroy(b);
     if (best_c == 0) return fail(SDMM_ERR_WORKSPACE, "workspace too small for any candidate");
     *chunk_out = best_c;
-    *ctas_out = best_g;
+    *ctas_out = g_max == 1 ? 0 : best_g;
     if (best_ms_out) *best_ms_out = best;
     return SDMM_OK;
 }

@@ -242,8 +242,27 @@ def test_batched_4096_regions_sampled_against_oracle():
     assert loglik_err(gll, oll) < LOGLIK_RTOL
 
 
-def test_autotune_returns_a_valid_candidate():
-    K, R = 16, 64
+def _estep_ms(cfg, batch, ost, R, N, reps=8):
+    """Mean E-step time of one-round plan replays with this configuration."""
+    st = gpu_state(ost, cfg)
+    plan = api.FitPlan(cfg, R, N, 1, st, api.workspace(cfg, R, N))
+    for _ in range(3):
+        plan.run(batch)
+    plan.enable_timing(reps)
+    for _ in range(reps):
+        plan.run(batch)
+    ms = float(np.mean(plan.timing()))
+    plan.close()
+    return ms
+
+
+@pytest.mark.parametrize("K", [2, 16])
+def test_autotune_pick_is_no_slower_than_the_default(K):
+    """The autotuner's (chunk, CTAs per SM) is a valid candidate, and the E-step
+    with it is no slower than with the library's heuristic default on the
+    same batch (5 % timing slack).  K = 16 runs the specialised E-step, whose
+    grid is fixed (only the chunk is tuned); K = 2 the generic one."""
+    R = 384
     truth = syn.batched_truth(9, R, K=K)
     counts = syn.region_counts(9, R)
     b = syn.batched_round(9, R, counts, 0, truth)
@@ -251,8 +270,14 @@ def test_autotune_returns_a_valid_candidate():
     gcfg = api.config(K, chunk=256)
     st = gpu_state(ost, gcfg)
     ws = api.workspace(gcfg, R, b.N)
-    chunk, ctas, ms = api.autotune(gcfg, dev_batch(b), st, ws)
-    assert chunk in (256, 512, 1024, 2048, 4096, 8192) and 1 <= ctas <= 4 and ms > 0
+    batch = dev_batch(b)
+    chunk, ctas, ms = api.autotune(gcfg, batch, st, ws)
+    assert chunk in (256, 512, 1024, 2048, 4096, 8192) and ms > 0
+    assert (ctas == 0) if K >= 3 else (1 <= ctas <= 4)
+    picked = _estep_ms(api.config(K, chunk=chunk, ctas_per_sm=ctas), batch, ost, R, b.N)
+    default = _estep_ms(api.config(K), batch, ost, R, b.N)
+    print(K, "autotune", chunk, ctas, picked, "default", default)
+    assert picked <= 1.05 * default
 
 
 def test_plan_on_host_batches_equals_device_batches():
