@@ -63,11 +63,11 @@ cudaError_t launch_query(cudaStream_t s, int op, int KP, int grid, const float* 
                          float* cond_pi, float* cond_m, float* cond_L, float* dir_out,
                          float* pdf_out, uint8_t* valid_out);
 
-// sampling / pdf with one thread per query (K <= 16); with perm, the j-th
-// processed query is perm[j], of region key[j]
+// sampling / pdf with one thread per query (K <= 16); with perm, slot j
+// processes query perm[j] (< 0: empty) and writes its record sorted_out[j]
 cudaError_t launch_query_q(cudaStream_t s, int op, int KP, int grid, const float* qtab, int K, int64_t R,
                            int64_t Q, const float* qx, const int32_t* region, const GridF& g, const int32_t* perm,
-                           const int32_t* key, uint64_t seed, const float* uni, const float* dir_in,
+                           float4* sorted_out, uint64_t seed, const float* uni, const float* dir_in,
                            float* dir_out, float* pdf_out, uint8_t* valid_out);
 // sampling / pdf with the queries binned by region in the caller's workspace
 // (K <= 16); qbin_workspace_bytes(R, Q) bytes, 256-byte aligned

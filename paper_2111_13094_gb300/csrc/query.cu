@@ -25,6 +25,10 @@ namespace sdmm {
 // another: the component choice, the Gaussian draw and the exp map run once
 // per query instead of in one lane of a component group.
 //
+// With `perm` (the library's binning) query perm[j] is processed at slot j
+// (perm[j] < 0: an empty padding slot) and its outputs go to the slot's record
+// sorted_out[j]: (direction, pdf, or -1 if not valid) for sampling, (pdf, ...)
+// for the pdf; k_qbin_unpermute then moves them to the query's own index.
 // A warp takes 32 queries at a time.  When they all fall in one region
 // (queries sorted by region), it copies that region's K records into shared
 // memory with coalesced 16-byte loads (only when the region changes) and every
@@ -32,17 +36,18 @@ namespace sdmm {
 // (queries in any order, or a region boundary) processes them with one lane
 // per component instead (warp_by_components), which reads each query's
 // records once, coalesced.  With `perm`, the warp's j-th query is perm[j] and
-// its region is key[j] (the library's binning of queries given in any order);
-// outputs always go to the query's own index.
+// outputs go to the slot's record (the library's binning of queries given in
+// any order), else to the query's own index.
 constexpr int kQWarps = 4;
 
 template <int KP, int OP>
-__device__ __forceinline__ void warp_by_components(const float* __restrict__ qtab, int K, int n, int64_t il,
+__device__ __forceinline__ void warp_by_components(const float* __restrict__ qtab, int K, unsigned active, int64_t il,
                                                    float x0, float x1, float x2, int rr, float a0, float a1,
                                                    float a2, float* P, int& cur_r, float* __restrict__ cond_pi,
                                                    float* __restrict__ cond_m, float* __restrict__ cond_L,
                                                    float* __restrict__ dir_out, float* __restrict__ pdf_out,
-                                                   uint8_t* __restrict__ valid_out);
+                                                   uint8_t* __restrict__ valid_out, float4* __restrict__ sorted_out,
+                                                   int64_t slot0);
 
 constexpr int kQCtas = 5;        // resident CTAs per SM (registers and shared memory allow five)
 
@@ -50,7 +55,7 @@ template <int KM, int OP>
 __global__ void __launch_bounds__(kQWarps * 32, kQCtas)
     k_query_q(const float* __restrict__ qtab, int K, int64_t R, int64_t Q,
               const float* __restrict__ qx, const int32_t* __restrict__ region, GridF grid,
-              const int32_t* __restrict__ perm, const int32_t* __restrict__ key, uint64_t seed,
+              const int32_t* __restrict__ perm, float4* __restrict__ sorted_out, uint64_t seed,
               const float* __restrict__ uni, const float* __restrict__ dir_in, float* __restrict__ dir_out,
               float* __restrict__ pdf_out, uint8_t* __restrict__ valid_out) {
     static_assert(OP == OP_SAMPLE || OP == OP_PDF, "sampling and pdf only");
@@ -68,21 +73,20 @@ __global__ void __launch_bounds__(kQWarps * 32, kQCtas)
     const int64_t wstride = (int64_t)gridDim.x * kQWarps * 32;
     for (int64_t base = ((int64_t)blockIdx.x * kQWarps + warp) * 32; base < Q; base += wstride) {
         const int64_t j = base + lane;
-        const bool in = j < Q;
+        bool in = j < Q;
         int64_t i = j;
         int r = -1;
         float x0 = 0.f, x1 = 0.f, x2 = 0.f;
+        if (in && perm != nullptr) {           // sorted positions; -1 marks padding
+            i = perm[j];
+            in = i >= 0;
+        }
         if (in) {
-            if (perm != nullptr) {
-                i = perm[j];
-                r = key[j];
-            } else if (region != nullptr) {
-                r = region[j];
-            }
+            if (region != nullptr) r = region[i];
             x0 = qx[3 * i];
             x1 = qx[3 * i + 1];
             x2 = qx[3 * i + 2];
-            if (perm == nullptr && region == nullptr) {
+            if (region == nullptr) {
                 const float xs[3] = {x0, x1, x2};
                 int id[3];
 #pragma unroll
@@ -95,7 +99,9 @@ __global__ void __launch_bounds__(kQWarps * 32, kQCtas)
         }
         const bool ok = in && r >= 0 && r < R;
         const int rr = ok ? r : 0;
-        const int r0 = __shfl_sync(FULL, rr, 0);
+        const unsigned act = __ballot_sync(FULL, in);
+        if (act == 0u) continue;
+        const int r0 = __shfl_sync(FULL, rr, __ffs(act) - 1);   // region of the first query
         if (!__all_sync(FULL, !in || rr == r0)) {
             // queries of several regions (given in any order): one lane per
             // component, each query's records read once, coalesced
@@ -122,9 +128,8 @@ __global__ void __launch_bounds__(kQWarps * 32, kQCtas)
             }
             float P[kQ];
             int cur_r = -1;
-            warp_by_components<KM, OP>(qtab, K, (int)min((int64_t)32, Q - base), i, x0, x1, x2, ok ? r : -1,
-                                       a0, a1, a2, P, cur_r, nullptr, nullptr, nullptr, dir_out, pdf_out,
-                                       valid_out);
+            warp_by_components<KM, OP>(qtab, K, act, i, x0, x1, x2, ok ? r : -1, a0, a1, a2, P, cur_r,
+                                       nullptr, nullptr, nullptr, dir_out, pdf_out, valid_out, sorted_out, base);
             continue;
         }
         // one region for the warp: its records into shared memory
@@ -244,7 +249,10 @@ __global__ void __launch_bounds__(kQWarps * 32, kQCtas)
             p += cut ? 0.f : pk_;
         }
         p = se > 0.f ? __fdividef(p, se) : 0.f;
-        if (OP == OP_SAMPLE) {
+        if (sorted_out != nullptr) {             // the slot's record (binned queries), coalesced
+            sorted_out[j] = OP == OP_SAMPLE ? make_float4(w0, w1, w2, valid ? p : -1.f)
+                                            : make_float4(ok ? p : 0.f, 0.f, 0.f, 0.f);
+        } else if (OP == OP_SAMPLE) {
             dir_out[3 * i] = w0;
             dir_out[3 * i + 1] = w1;
             dir_out[3 * i + 2] = w2;
@@ -257,24 +265,27 @@ __global__ void __launch_bounds__(kQWarps * 32, kQCtas)
 }
 
 // The queries held by the lanes of one warp (lane l: query il with position
-// x, region rr (-1: none) and uniforms or direction a), n of them, processed
+// x, region rr (-1: none) and uniforms or direction a; the lanes in `active`
+// hold a query), processed
 // SPI = 32/KP at a time with one lane per component; the query's inputs are
 // broadcast by shuffles and the component's query record P stays in
 // registers while consecutive queries share a region (cur_r).
 template <int KP, int OP>
-__device__ __forceinline__ void warp_by_components(const float* __restrict__ qtab, int K, int n, int64_t il,
+__device__ __forceinline__ void warp_by_components(const float* __restrict__ qtab, int K, unsigned active, int64_t il,
                                                    float x0, float x1, float x2, int rr, float a0, float a1,
                                                    float a2, float* P, int& cur_r, float* __restrict__ cond_pi,
                                                    float* __restrict__ cond_m, float* __restrict__ cond_L,
                                                    float* __restrict__ dir_out, float* __restrict__ pdf_out,
-                                                   uint8_t* __restrict__ valid_out) {
+                                                   uint8_t* __restrict__ valid_out, float4* __restrict__ sorted_out,
+                                                   int64_t slot0) {
     constexpr int SPI = 32 / KP;
     constexpr unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const int k = lane & (KP - 1), h = lane / KP, base_lane = h * KP;
+    const int n = 32 - __clz(active);           // slots up to the last active lane
     for (int t = 0; t < n; t += SPI) {
         const int j = t + h;
-        const bool act = j < n;
+        const bool act = j < 32 && ((active >> j) & 1u);
         const int src = act ? j : t;
         const float qx0 = __shfl_sync(FULL, x0, src), qx1 = __shfl_sync(FULL, x1, src),
                     qx2 = __shfl_sync(FULL, x2, src);
@@ -400,7 +411,10 @@ __device__ __forceinline__ void warp_by_components(const float* __restrict__ qta
 #pragma unroll
         for (int o = KP / 2; o > 0; o >>= 1) p += __shfl_xor_sync(FULL, p, o);
         if (act && k == 0) {
-            if (OP == OP_SAMPLE) {
+            if (sorted_out != nullptr) {         // the slot's record (binned queries)
+                sorted_out[slot0 + j] = OP == OP_SAMPLE ? make_float4(w0, w1, w2, valid ? p : -1.f)
+                                                        : make_float4(ok ? p : 0.f, 0.f, 0.f, 0.f);
+            } else if (OP == OP_SAMPLE) {
                 dir_out[3 * qi] = w0;
                 dir_out[3 * qi + 1] = w1;
                 dir_out[3 * qi + 2] = w2;
@@ -468,8 +482,8 @@ __global__ void __launch_bounds__(256)
                 a2 = dir_in[3 * i + 2];
             }
         }
-        warp_by_components<KP, OP>(qtab, K, (int)min((int64_t)32, Q - g), i, x0, x1, x2, rr, a0, a1, a2, P,
-                                   cur_r, cond_pi, cond_m, cond_L, dir_out, pdf_out, valid_out);
+        warp_by_components<KP, OP>(qtab, K, __ballot_sync(0xffffffffu, i < Q), i, x0, x1, x2, rr, a0, a1, a2, P,
+                                   cur_r, cond_pi, cond_m, cond_L, dir_out, pdf_out, valid_out, nullptr, 0);
     }
 }
 
@@ -501,9 +515,17 @@ static cudaError_t launch_query_op(int KP, cudaStream_t s, int grid, const float
 // Binning of queries given in any order: a counting sort by region.
 //   k_qbin_keys     region of every query (array or grid; out of range: bin R)
 //                   and the per-bin counts (warp-aggregated atomics)
-//   k_qbin_scan     exclusive prefix sum of the R + 1 counts (one CTA)
-//   k_qbin_scatter  each query's position in its bin (warp-aggregated atomic
-//                   cursor): perm[pos] = query index, key[pos] = its region
+//   k_qbin_scan     exclusive prefix sum of the R + 1 counts, each rounded up
+//                   to a multiple of 32 (one CTA), so that every bin starts
+//                   at a multiple of 32 and no warp of the sampling kernel
+//                   spans two regions
+//   k_qbin_scatter  each query's position (slot) in its bin (warp-aggregated
+//                   atomic cursor): perm[slot] = query index and inv[query] =
+//                   slot; the padding slots keep perm = -1 (no query)
+//   k_qbin_unpermute  the sampling kernel writes each slot's outputs as one
+//                   16-byte record in slot order (coalesced); query i then
+//                   gathers its record from slot inv[i] and writes its outputs
+//                   in query order, so no output is written at random
 // The order within a bin depends on the atomics; no result does, since every
 // query's output depends only on its own inputs and index.
 __global__ void __launch_bounds__(256) k_qbin_keys(int64_t Q, int64_t R, const float* __restrict__ qx,
@@ -543,7 +565,7 @@ __global__ void __launch_bounds__(1024) k_qbin_scan(int64_t n, int32_t* __restri
     __syncthreads();
     for (int64_t base = 0; base < n; base += 1024) {
         const int64_t e = base + tid;
-        const int32_t c = e < n ? v[e] : 0;
+        const int32_t c = e < n ? (v[e] + 31) & ~31 : 0;   // bin sizes padded to whole warps
         int32_t x = c;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
@@ -572,7 +594,7 @@ __global__ void __launch_bounds__(1024) k_qbin_scan(int64_t n, int32_t* __restri
 
 __global__ void __launch_bounds__(256) k_qbin_scatter(int64_t Q, const int32_t* __restrict__ key_in,
                                                       int32_t* __restrict__ cursor, int32_t* __restrict__ perm,
-                                                      int32_t* __restrict__ key_out) {
+                                                      int32_t* __restrict__ inv) {
     const int lane = threadIdx.x & 31;
     const int64_t wstride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < Q; base += wstride) {
@@ -585,14 +607,39 @@ __global__ void __launch_bounds__(256) k_qbin_scatter(int64_t Q, const int32_t* 
         pos = __shfl_sync(0xffffffffu, pos, leader) + __popc(m & ((1u << lane) - 1u));
         if (i < Q) {
             perm[pos] = (int32_t)i;
-            key_out[pos] = r;
+            inv[i] = pos;
         }
     }
 }
 
+// The slots' records back to the queries' own indices: query i reads its
+// slot inv[i] (a 16-byte gather) and writes its outputs in order.
+template <int OP>
+__global__ void __launch_bounds__(256) k_qbin_unpermute(int64_t Q, const int32_t* __restrict__ inv,
+                                                        const float4* __restrict__ rec, float* __restrict__ dir_out,
+                                                        float* __restrict__ pdf_out, uint8_t* __restrict__ valid_out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < Q; i += stride) {
+        const float4 v = rec[inv[i]];
+        if (OP == OP_SAMPLE) {
+            dir_out[3 * i] = v.x;
+            dir_out[3 * i + 1] = v.y;
+            dir_out[3 * i + 2] = v.z;
+            pdf_out[i] = fmaxf(v.w, 0.f);
+            valid_out[i] = (uint8_t)(v.w >= 0.f);
+        } else {
+            pdf_out[i] = v.x;
+        }
+    }
+}
+
+// sorted positions, padding included: Q + 31 per bin at most
+static int64_t qbin_slots(int64_t R, int64_t Q) { return Q + 31 * (R + 1); }
+
 size_t qbin_workspace_bytes(int64_t R, int64_t Q) {
     auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
-    return up(sizeof(int32_t) * (size_t)(R + 1)) + 3 * up(sizeof(int32_t) * (size_t)Q);
+    return up(sizeof(int32_t) * (size_t)(R + 1)) + 2 * up(sizeof(int32_t) * (size_t)Q) +
+           up(sizeof(int32_t) * (size_t)qbin_slots(R, Q)) + up(sizeof(float4) * (size_t)qbin_slots(R, Q));
 }
 
 cudaError_t launch_query_binned(cudaStream_t s, int op, int KP, int grid, const float* qtab, int K, int64_t R,
@@ -600,28 +647,38 @@ cudaError_t launch_query_binned(cudaStream_t s, int op, int KP, int grid, const 
                                 const float* uni, const float* dir_in, float* dir_out, float* pdf_out,
                                 uint8_t* valid_out, void* ws) {
     auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const int64_t slots = qbin_slots(R, Q);
     unsigned char* p = static_cast<unsigned char*>(ws);
     int32_t* counts = reinterpret_cast<int32_t*>(p);
     p += up(sizeof(int32_t) * (size_t)(R + 1));
     int32_t* key = reinterpret_cast<int32_t*>(p);
     p += up(sizeof(int32_t) * (size_t)Q);
-    int32_t* perm = reinterpret_cast<int32_t*>(p);
+    int32_t* inv = reinterpret_cast<int32_t*>(p);
     p += up(sizeof(int32_t) * (size_t)Q);
-    int32_t* key_sorted = reinterpret_cast<int32_t*>(p);
+    int32_t* perm = reinterpret_cast<int32_t*>(p);
+    p += up(sizeof(int32_t) * (size_t)slots);
+    float4* rec = reinterpret_cast<float4*>(p);
     cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(int32_t) * (size_t)(R + 1), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(perm, 0xff, sizeof(int32_t) * (size_t)slots, s);   // -1: padding
     if (e != cudaSuccess) return e;
     const int gb = (int)std::max<int64_t>(1, std::min<int64_t>((Q + 255) / 256, (int64_t)grid * 4));
     k_qbin_keys<<<gb, 256, 0, s>>>(Q, R, qx, region, g, key, counts);
     k_qbin_scan<<<1, 1024, 0, s>>>(R + 1, counts);
-    k_qbin_scatter<<<gb, 256, 0, s>>>(Q, key, counts, perm, key_sorted);
+    k_qbin_scatter<<<gb, 256, 0, s>>>(Q, key, counts, perm, inv);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    return launch_query_q(s, op, KP, grid, qtab, K, R, Q, qx, region, g, perm, key_sorted, seed, uni, dir_in,
-                          dir_out, pdf_out, valid_out);
+    e = launch_query_q(s, op, KP, grid, qtab, K, R, slots, qx, region, g, perm, rec, seed, uni, dir_in, dir_out,
+                       pdf_out, valid_out);
+    if (e != cudaSuccess) return e;
+    if (op == OP_SAMPLE)
+        k_qbin_unpermute<OP_SAMPLE><<<gb, 256, 0, s>>>(Q, inv, rec, dir_out, pdf_out, valid_out);
+    else
+        k_qbin_unpermute<OP_PDF><<<gb, 256, 0, s>>>(Q, inv, rec, dir_out, pdf_out, valid_out);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_query_q(cudaStream_t s, int op, int KP, int grid, const float* qtab, int K, int64_t R,
                            int64_t Q, const float* qx, const int32_t* region, const GridF& g, const int32_t* perm,
-                           const int32_t* key, uint64_t seed, const float* uni, const float* dir_in,
+                           float4* sorted_out, uint64_t seed, const float* uni, const float* dir_in,
                            float* dir_out, float* pdf_out, uint8_t* valid_out) {
     // a persistent grid: every resident CTA walks the queries with a stride
     int dev = 0, nsm = 0;
@@ -634,10 +691,10 @@ cudaError_t launch_query_q(cudaStream_t s, int op, int KP, int grid, const float
 #define SDMM_QQ(M)                                                                                           \
     case M:                                                                                                  \
         if (op == OP_SAMPLE)                                                                                 \
-            k_query_q<M, OP_SAMPLE><<<gq, kQWarps * 32, 0, s>>>(qtab, K, R, Q, qx, region, g, perm, key, seed, \
+            k_query_q<M, OP_SAMPLE><<<gq, kQWarps * 32, 0, s>>>(qtab, K, R, Q, qx, region, g, perm, sorted_out, seed, \
                                                                 uni, dir_in, dir_out, pdf_out, valid_out);   \
         else                                                                                                 \
-            k_query_q<M, OP_PDF><<<gq, kQWarps * 32, 0, s>>>(qtab, K, R, Q, qx, region, g, perm, key, seed,    \
+            k_query_q<M, OP_PDF><<<gq, kQWarps * 32, 0, s>>>(qtab, K, R, Q, qx, region, g, perm, sorted_out, seed,    \
                                                              uni, dir_in, dir_out, pdf_out, valid_out);      \
         break;
     switch (KP) {
