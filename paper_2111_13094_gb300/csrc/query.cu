@@ -29,13 +29,13 @@ namespace sdmm {
 // (perm[j] < 0: an empty padding slot) and its outputs go to the slot's record
 // sorted_out[j]: (direction, pdf, or -1 if not valid) for sampling, (pdf, ...)
 // for the pdf; k_qbin_unpermute then moves them to the query's own index.
-// A warp takes 32 queries at a time.  When they all fall in one region
-// (queries sorted by region), it copies that region's K records into shared
-// memory with coalesced 16-byte loads (only when the region changes) and every
-// thread reads them from there.  A warp whose queries span several regions
-// (queries in any order, or a region boundary) processes them with one lane
-// per component instead (warp_by_components), which reads each query's
-// records once, coalesced.  With `perm`, the warp's j-th query is perm[j] and
+// A warp takes 32 queries at a time.  When they fall in at most two regions,
+// those of its first and last query (queries sorted by region), it copies a
+// region's K records into shared memory with coalesced 16-byte loads (only
+// when the region changes) and the threads of that region read them from
+// there, one pass per region.  A warp whose queries span more regions
+// (queries in any order) processes them with one lane per component instead
+// (warp_by_components), which reads each query's records once, coalesced.  With `perm`, the warp's j-th query is perm[j] and
 // outputs go to the slot's record (the library's binning of queries given in
 // any order), else to the query's own index.
 constexpr int kQWarps = 4;
@@ -102,7 +102,8 @@ __global__ void __launch_bounds__(kQWarps * 32, kQCtas)
         const unsigned act = __ballot_sync(FULL, in);
         if (act == 0u) continue;
         const int r0 = __shfl_sync(FULL, rr, __ffs(act) - 1);   // region of the first query
-        if (!__all_sync(FULL, !in || rr == r0)) {
+        const int r1 = __shfl_sync(FULL, rr, 31 - __clz(act));  // and of the last
+        if (!__all_sync(FULL, !in || rr == r0 || rr == r1)) {
             // queries of several regions (given in any order): one lane per
             // component, each query's records read once, coalesced
             float a0 = 0.f, a1 = 0.f, a2 = 0.f;
@@ -132,134 +133,141 @@ __global__ void __launch_bounds__(kQWarps * 32, kQCtas)
                                        nullptr, nullptr, nullptr, dir_out, pdf_out, valid_out, sorted_out, base);
             continue;
         }
-        // one region for the warp: its records into shared memory
-        if (r0 != staged) {
-            __syncwarp();
-            const float4* src = q4 + (int64_t)r0 * n4;
-            for (int e = lane; e < n4; e += 32) s_rec[warp][e] = __ldg(src + e);
-            __syncwarp();
-            staged = r0;
-        }
-        if (!in) continue;
-        const float4* rec = &s_rec[warp][0];
-
-        // ---- pass 1: conditioning on the position (Sec. 3.2), every component:
-        // lw = log2 of pi'_k up to a common constant, m = C^T z
-        float mx = -INFINITY;
-#pragma unroll 4
-        for (int k = 0; k < K; ++k) {
-            const float4* rk = rec + k * Q4;
-            const float4 a = rk[0], f3 = rk[3], f4 = rk[4], f5 = rk[5], f7 = rk[7], f8 = rk[8];
-            const float e0 = (x0 - a.x) - f8.x, e1 = (x1 - a.y) - f8.y, e2 = (x2 - a.z) - f8.z;
-            // A^-1 packed at 12..17, C^T rows at 18..20 and 21..23, cx at 30
-            const float z0 = f3.x * e0;
-            const float z1 = f3.y * e0 + f3.z * e1;
-            const float z2 = f3.w * e0 + f4.x * e1 + f4.y * e2;
-            const float lw = fmaf(-0.5f, z0 * z0 + z1 * z1 + z2 * z2, f7.z) * kL2e;
-            cm[k * CS] = make_float4(lw, f4.z * z0 + f4.w * z1 + f5.x * z2, f5.y * z0 + f5.z * z1 + f5.w * z2, 0.f);
-            mx = fmaxf(mx, lw);
-        }
-        // normalisation: w'_k = 2^(lw - max), se = sum w'_k
-        float se = 0.f;
-#pragma unroll 4
-        for (int k = 0; k < K; ++k) {
-            const float w = mx > -INFINITY ? tc::ex2_approx(cm[k * CS].x - mx) : 0.f;
-            cm[k * CS].x = w;
-            se += w;
-        }
-
-        float w0, w1, w2;
-        int valid = 1;
-        if (OP == OP_SAMPLE) {
-            float u0, u1, u2;
-            if (uni != nullptr) {
-                u0 = uni[3 * i];
-                u1 = uni[3 * i + 1];
-                u2 = uni[3 * i + 2];
-            } else {
-                const uint4 o = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)((uint64_t)i >> 32), 0u, 0u),
-                                              make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
-                u0 = u24(o.x);
-                u1 = u24(o.y);
-                u2 = u24(o.z);
+        // one or two regions for the warp (queries sorted by region; a warp
+        // may straddle a region boundary): one pass per region
+#pragma unroll 1
+        for (int pass = 0; pass < 2; ++pass) {
+            // this pass's region: its records into shared memory
+            const int rp = pass == 0 ? r0 : r1;
+            if (pass == 1 && r1 == r0) break;
+            if (rp != staged) {
+                __syncwarp();
+                const float4* src = q4 + (int64_t)rp * n4;
+                for (int e = lane; e < n4; e += 32) s_rec[warp][e] = __ldg(src + e);
+                __syncwarp();
+                staged = rp;
             }
-            // component by inverse CDF on u0 (Sec. 3.1 "Sampling", step i): the
-            // first k with u0 se < cumsum; rounding past the end takes the last
-            // component of positive weight
-            const float thr = u0 * se;
-            float cum = 0.f;
-            int kk = -1, last = -1;
+            if (!in || rr != rp) continue;
+            const float4* rec = &s_rec[warp][0];
+
+            // ---- pass 1: conditioning on the position (Sec. 3.2), every component:
+            // lw = log2 of pi'_k up to a common constant, m = C^T z
+            float mx = -INFINITY;
 #pragma unroll 4
             for (int k = 0; k < K; ++k) {
-                const float w = cm[k * CS].x;
-                cum += w;
-                last = w > 0.f ? k : last;
-                kk = (kk < 0 && thr < cum) ? k : kk;
+                const float4* rk = rec + k * Q4;
+                const float4 a = rk[0], f3 = rk[3], f4 = rk[4], f5 = rk[5], f7 = rk[7], f8 = rk[8];
+                const float e0 = (x0 - a.x) - f8.x, e1 = (x1 - a.y) - f8.y, e2 = (x2 - a.z) - f8.z;
+                // A^-1 packed at 12..17, C^T rows at 18..20 and 21..23, cx at 30
+                const float z0 = f3.x * e0;
+                const float z1 = f3.y * e0 + f3.z * e1;
+                const float z2 = f3.w * e0 + f4.x * e1 + f4.y * e2;
+                const float lw = fmaf(-0.5f, z0 * z0 + z1 * z1 + z2 * z2, f7.z) * kL2e;
+                cm[k * CS] = make_float4(lw, f4.z * z0 + f4.w * z1 + f5.x * z2, f5.y * z0 + f5.z * z1 + f5.w * z2, 0.f);
+                mx = fmaxf(mx, lw);
             }
-            if (kk < 0) kk = last >= 0 ? last : 0;
-            const float4 sel = cm[kk * CS];
-            // Gaussian draw in the chart (step ii), exp map (step iii)
-            const float4* rk = rec + kk * Q4;
-            const float4 t4 = rk[0];   // mu_x, t.x
-            const float4 t5 = rk[1];   // t.y t.z b.x b.y
-            const float4 t6 = rk[2];   // b.z mu_w
-            const float4 dd = rk[6];   // D (d00 d10 d11), D^-1 00
-            const float rad = sqrtf(-2.f * logf(1.f - u1));
-            float sn, cs;
-            sincospif(2.f * u2, &sn, &cs);
-            const float g0 = rad * cs, g1 = rad * sn;
-            const float n0 = sel.y + dd.x * g0;
-            const float n1 = sel.z + dd.y * g0 + dd.z * g1;
-            const float rn = sqrtf(n0 * n0 + n1 * n1);
-            valid = (rn < kPiF) && ok && last >= 0;
-            float sr, cr;
-            sincosf(rn, &sr, &cr);
-            const float sc = rn < 1e-3f ? 1.f - rn * rn * (1.f / 6.f) : __fdividef(sr, rn);
-            const float c0 = n0 * sc, c1 = n1 * sc;
-            w0 = c0 * t4.w + c1 * t5.z + cr * t6.y;
-            w1 = c0 * t5.x + c1 * t5.w + cr * t6.z;
-            w2 = c0 * t5.y + c1 * t6.x + cr * t6.w;
-        } else {
-            w0 = dir_in[3 * i];
-            w1 = dir_in[3 * i + 1];
-            w2 = dir_in[3 * i + 2];
-        }
-
-        // ---- pass 2: solid-angle pdf of the conditioned mixture at w
-        // (Sec. 3.1 Eq. solidangle-pdf): sum_k pi'_k N_2(log_k w; m_k, D D^T) / sinc
-        float p = 0.f;
+            // normalisation: w'_k = 2^(lw - max), se = sum w'_k
+            float se = 0.f;
 #pragma unroll 4
-        for (int k = 0; k < K; ++k) {
-            const float4* rk = rec + k * Q4;
-            const float4 a = rk[0], b = rk[1], c = rk[2], f6 = rk[6], f7 = rk[7];
-            const float4 wm = cm[k * CS];
-            // t = (a.w, b.x, b.y), b = (b.z, b.w, c.x), mu = (c.y, c.z, c.w)
-            const float u = a.w * w0 + b.x * w1 + b.y * w2;
-            const float v = b.z * w0 + b.w * w1 + c.x * w2;
-            const float cz = c.y * w0 + c.z * w1 + c.w * w2;
-            const float s2v = u * u + v * v;
-            // antipode of the mean (and within 1e-19 of it): outside the chart
-            const bool cut = !(s2v >= 1.17549435e-38f) && cz < 0.f;
-            const float gg = cut ? 1.f : g_of_cos(cz, tc::rsqrt_approx(s2v));
-            const float d0 = gg * u - wm.y, d1 = gg * v - wm.z;
-            // D^-1 (f6.w, f7.x, f7.y), cn at 31
-            const float y0 = f6.w * d0;
-            const float y1 = f7.x * d0 + f7.y * d1;
-            const float pk_ = wm.x * tc::ex2_approx(fmaf(-0.5f, y0 * y0 + y1 * y1, f7.w) * kL2e) * gg;
-            p += cut ? 0.f : pk_;
-        }
-        p = se > 0.f ? __fdividef(p, se) : 0.f;
-        if (sorted_out != nullptr) {             // the slot's record (binned queries), coalesced
-            sorted_out[j] = OP == OP_SAMPLE ? make_float4(w0, w1, w2, valid ? p : -1.f)
-                                            : make_float4(ok ? p : 0.f, 0.f, 0.f, 0.f);
-        } else if (OP == OP_SAMPLE) {
-            dir_out[3 * i] = w0;
-            dir_out[3 * i + 1] = w1;
-            dir_out[3 * i + 2] = w2;
-            valid_out[i] = (uint8_t)valid;
-            pdf_out[i] = valid ? p : 0.f;
-        } else {
-            pdf_out[i] = ok ? p : 0.f;
+            for (int k = 0; k < K; ++k) {
+                const float w = mx > -INFINITY ? tc::ex2_approx(cm[k * CS].x - mx) : 0.f;
+                cm[k * CS].x = w;
+                se += w;
+            }
+
+            float w0, w1, w2;
+            int valid = 1;
+            if (OP == OP_SAMPLE) {
+                float u0, u1, u2;
+                if (uni != nullptr) {
+                    u0 = uni[3 * i];
+                    u1 = uni[3 * i + 1];
+                    u2 = uni[3 * i + 2];
+                } else {
+                    const uint4 o = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)((uint64_t)i >> 32), 0u, 0u),
+                                                  make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+                    u0 = u24(o.x);
+                    u1 = u24(o.y);
+                    u2 = u24(o.z);
+                }
+                // component by inverse CDF on u0 (Sec. 3.1 "Sampling", step i): the
+                // first k with u0 se < cumsum; rounding past the end takes the last
+                // component of positive weight
+                const float thr = u0 * se;
+                float cum = 0.f;
+                int kk = -1, last = -1;
+#pragma unroll 4
+                for (int k = 0; k < K; ++k) {
+                    const float w = cm[k * CS].x;
+                    cum += w;
+                    last = w > 0.f ? k : last;
+                    kk = (kk < 0 && thr < cum) ? k : kk;
+                }
+                if (kk < 0) kk = last >= 0 ? last : 0;
+                const float4 sel = cm[kk * CS];
+                // Gaussian draw in the chart (step ii), exp map (step iii)
+                const float4* rk = rec + kk * Q4;
+                const float4 t4 = rk[0];   // mu_x, t.x
+                const float4 t5 = rk[1];   // t.y t.z b.x b.y
+                const float4 t6 = rk[2];   // b.z mu_w
+                const float4 dd = rk[6];   // D (d00 d10 d11), D^-1 00
+                const float rad = sqrtf(-2.f * logf(1.f - u1));
+                float sn, cs;
+                sincospif(2.f * u2, &sn, &cs);
+                const float g0 = rad * cs, g1 = rad * sn;
+                const float n0 = sel.y + dd.x * g0;
+                const float n1 = sel.z + dd.y * g0 + dd.z * g1;
+                const float rn = sqrtf(n0 * n0 + n1 * n1);
+                valid = (rn < kPiF) && ok && last >= 0;
+                float sr, cr;
+                sincosf(rn, &sr, &cr);
+                const float sc = rn < 1e-3f ? 1.f - rn * rn * (1.f / 6.f) : __fdividef(sr, rn);
+                const float c0 = n0 * sc, c1 = n1 * sc;
+                w0 = c0 * t4.w + c1 * t5.z + cr * t6.y;
+                w1 = c0 * t5.x + c1 * t5.w + cr * t6.z;
+                w2 = c0 * t5.y + c1 * t6.x + cr * t6.w;
+            } else {
+                w0 = dir_in[3 * i];
+                w1 = dir_in[3 * i + 1];
+                w2 = dir_in[3 * i + 2];
+            }
+
+            // ---- pass 2: solid-angle pdf of the conditioned mixture at w
+            // (Sec. 3.1 Eq. solidangle-pdf): sum_k pi'_k N_2(log_k w; m_k, D D^T) / sinc
+            float p = 0.f;
+#pragma unroll 4
+            for (int k = 0; k < K; ++k) {
+                const float4* rk = rec + k * Q4;
+                const float4 a = rk[0], b = rk[1], c = rk[2], f6 = rk[6], f7 = rk[7];
+                const float4 wm = cm[k * CS];
+                // t = (a.w, b.x, b.y), b = (b.z, b.w, c.x), mu = (c.y, c.z, c.w)
+                const float u = a.w * w0 + b.x * w1 + b.y * w2;
+                const float v = b.z * w0 + b.w * w1 + c.x * w2;
+                const float cz = c.y * w0 + c.z * w1 + c.w * w2;
+                const float s2v = u * u + v * v;
+                // antipode of the mean (and within 1e-19 of it): outside the chart
+                const bool cut = !(s2v >= 1.17549435e-38f) && cz < 0.f;
+                const float gg = cut ? 1.f : g_of_cos(cz, tc::rsqrt_approx(s2v));
+                const float d0 = gg * u - wm.y, d1 = gg * v - wm.z;
+                // D^-1 (f6.w, f7.x, f7.y), cn at 31
+                const float y0 = f6.w * d0;
+                const float y1 = f7.x * d0 + f7.y * d1;
+                const float pk_ = wm.x * tc::ex2_approx(fmaf(-0.5f, y0 * y0 + y1 * y1, f7.w) * kL2e) * gg;
+                p += cut ? 0.f : pk_;
+            }
+            p = se > 0.f ? __fdividef(p, se) : 0.f;
+            if (sorted_out != nullptr) {             // the slot's record (binned queries), coalesced
+                sorted_out[j] = OP == OP_SAMPLE ? make_float4(w0, w1, w2, valid ? p : -1.f)
+                                                : make_float4(ok ? p : 0.f, 0.f, 0.f, 0.f);
+            } else if (OP == OP_SAMPLE) {
+                dir_out[3 * i] = w0;
+                dir_out[3 * i + 1] = w1;
+                dir_out[3 * i + 2] = w2;
+                valid_out[i] = (uint8_t)valid;
+                pdf_out[i] = valid ? p : 0.f;
+            } else {
+                pdf_out[i] = ok ? p : 0.f;
+            }
         }
     }
 }
