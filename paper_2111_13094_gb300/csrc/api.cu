@@ -274,6 +274,8 @@ sdmm_status enqueue_fit(const FitLaunch& f, cudaStream_t s, std::vector<cudaEven
     const bool tcore = tensor_core(&f.cfg);
     const int euclid = f.cfg.dir_coords == SDMM_DIR_EUCLIDEAN;
     const int mstep_threads = f.R > 3 * (int64_t)std::max(1, sm_count()) ? 32 : 128;
+    // the specialised E-step leaves its statistics in whitened coordinates
+    const int ystats = !tcore && estep_fast_supported(KP);
     SDMM_CUDA(launch_build_chunks(s, f.w.hdr, f.w.cb, f.w.cr, f.w.units, f.L.chunk, f.cfg.min_samples,
                                   f.L.max_chunks),
               "build_chunks");
@@ -295,7 +297,8 @@ sdmm_status enqueue_fit(const FitLaunch& f, cudaStream_t s, std::vector<cudaEven
         }
         if (evs) SDMM_CUDA(cudaEventRecordWithFlags((*evs)[2 * it + 1], s, cudaEventRecordExternal), "event");
         if (f.w.partial2 != nullptr) {   // accurate covariance update: second pass in the new charts
-            SDMM_CUDA(launch_new_charts(s, f.R, f.w.hdr, f.w.cb, f.w.partial, f.L.ps, f.cfg, f.st, f.w.chart2),
+            SDMM_CUDA(launch_new_charts(s, f.R, f.w.hdr, f.w.cb, f.w.partial, f.L.ps, f.cfg, f.st, f.w.chart2,
+                                        ystats),
                       "new_charts");
             SDMM_CUDA(launch_accumulate(s, MODE_TWO, KP, f.grid, f.w.hdr, f.w.cb, f.w.cr,
                                         f.st.etab, f.cfg.K, f.L.chunk, f.cfg.estep_density, f.w.partial2,
@@ -303,7 +306,7 @@ sdmm_status enqueue_fit(const FitLaunch& f, cudaStream_t s, std::vector<cudaEven
                       "accumulate_two");
         }
         SDMM_CUDA(launch_reduce_mstep(s, f.R, f.w.hdr, f.w.cb, f.w.partial, f.L.ps, f.cfg, f.st, it,
-                                      tcore ? f.w.xref : nullptr, f.w.partial2, f.L.ps2, mstep_threads),
+                                      tcore ? f.w.xref : nullptr, f.w.partial2, f.L.ps2, mstep_threads, ystats),
                   "reduce_mstep");
     }
     return SDMM_OK;

@@ -15,6 +15,11 @@
 //     spatial mean, FP32): the sample's offset is formed once per sample when
 //     it is staged, each component's mean offset once per region, so the pair
 //     needs one subtraction per coordinate, with no hi/lo correction;
+//   * the statistics are taken in the whitened chart coordinates
+//     y = sqrt(log2(e) / 2) L^-1 d, which the Mahalanobis term computes
+//     anyway: y = L'^-1 (x', g u, g v) - b with b = L'^-1 (mean offsets) per
+//     component, so no d is formed; the M-step takes them back to the chart
+//     (s1 = L s1_y / c, s2 = L s2_y L^T / c^2, FP64);
 //   * two samples per lane in flight (samples t + h and t + SPI + h), so the
 //     two log-sum-exp butterflies and the two MUFU chains overlap;
 //   * the next batch of 32 samples is loaded while the current one is processed.
@@ -79,10 +84,10 @@ __global__ void __launch_bounds__(kEW * 32, kECtas)
     const int n_chunks = ws->n_chunks;
     const int64_t R = ws->desc.R;
 
-    // this lane's component: R_mu rows (t, b, mu), mean offset from the
-    // reference point (3) and, with OFFS (the objective at offset means), the
-    // in-chart direction offset (2), scaled L^-1, base-2 constant shifted by
-    // the region bound
+    // this lane's component: R_mu rows (t, b, mu), mo = the scaled L^-1 times
+    // the mean's offset from the reference point and, with OFFS (the
+    // objective at offset means, the Euclidean mean), the in-chart direction
+    // offset; li = the scaled L^-1; base-2 constant shifted by the region bound
     float rt[9], mo[5], li[15];
 #pragma unroll
     for (int q = 0; q < 9; ++q) rt[q] = 0.f;
@@ -95,8 +100,8 @@ __global__ void __launch_bounds__(kEW * 32, kECtas)
     int prev_r = -1;
 
     // log2 of the chart density of one sample at this lane's component,
-    // relative to the region bound; d receives the tangent vector
-    auto logp2 = [&](const float4 sa, const float4 sb, float d[5]) -> float {
+    // relative to the region bound; y receives the whitened tangent vector
+    auto logp2 = [&](const float4 sa, const float4 sb, float y[5]) -> float {
         const float u = rt[0] * sb.x + rt[1] * sb.y + rt[2] * sb.z;
         const float v = rt[3] * sb.x + rt[4] * sb.y + rt[5] * sb.z;
         const float cz = rt[6] * sb.x + rt[7] * sb.y + rt[8] * sb.z;
@@ -104,21 +109,18 @@ __global__ void __launch_bounds__(kEW * 32, kECtas)
         // 1/sin(theta) clamped so that g stays finite (and d with it) at the
         // antipode of the mean, which has no chart: its density is 0 below
         const float gg = EUCL ? 1.f : g_of_cos_fit(cz, fminf(tc::rsqrt_approx(s2), 1e18f));
-        d[0] = sa.x - mo[0];
-        d[1] = sa.y - mo[1];
-        d[2] = sa.z - mo[2];
-        d[3] = OFFS ? gg * u - mo[3] : gg * u;
-        d[4] = OFFS ? gg * v - mo[4] : gg * v;
-        const float y0 = li[0] * d[0];
-        const float y1 = li[1] * d[0] + li[2] * d[1];
-        const float y2 = li[3] * d[0] + li[4] * d[1] + li[5] * d[2];
-        const float y3 = li[6] * d[0] + li[7] * d[1] + li[8] * d[2] + li[9] * d[3];
-        const float y4 = li[10] * d[0] + li[11] * d[1] + li[12] * d[2] + li[13] * d[3] + li[14] * d[4];
-        float l2 = fmaf(-y0, y0, c2);
-        l2 = fmaf(-y1, y1, l2);
-        l2 = fmaf(-y2, y2, l2);
-        l2 = fmaf(-y3, y3, l2);
-        l2 = fmaf(-y4, y4, l2);
+        const float gu = gg * u, gv = gg * v;
+        y[0] = fmaf(li[0], sa.x, -mo[0]);
+        y[1] = fmaf(li[2], sa.y, fmaf(li[1], sa.x, -mo[1]));
+        y[2] = fmaf(li[5], sa.z, fmaf(li[4], sa.y, fmaf(li[3], sa.x, -mo[2])));
+        y[3] = fmaf(li[9], gu, fmaf(li[8], sa.z, fmaf(li[7], sa.y, fmaf(li[6], sa.x, -mo[3]))));
+        y[4] = fmaf(li[14], gv, fmaf(li[13], gu, fmaf(li[12], sa.z, fmaf(li[11], sa.y,
+                                                                           fmaf(li[10], sa.x, -mo[4])))));
+        float l2 = fmaf(-y[0], y[0], c2);
+        l2 = fmaf(-y[1], y[1], l2);
+        l2 = fmaf(-y[2], y[2], l2);
+        l2 = fmaf(-y[3], y[3], l2);
+        l2 = fmaf(-y[4], y[4], l2);
         if (SOLID) l2 += tc::lg2_approx(gg);                       // p^t / sinc: + log2(theta / sin)
         if (EUCL) return l2;
         const bool cut = !(s2 >= 1.17549435e-38f) && cz < 0.f;   // to within 1e-19 rad
@@ -158,13 +160,18 @@ __global__ void __launch_bounds__(kEW * 32, kECtas)
                 }
 #pragma unroll
                 for (int q = 0; q < 9; ++q) rt[q] = p[3 + q];
-                mo[0] = (p[0] - xr0) + p[32];
-                mo[1] = (p[1] - xr1) + p[33];
-                mo[2] = (p[2] - xr2) + p[34];
-                mo[3] = p[28];
-                mo[4] = p[29];
 #pragma unroll
                 for (int q = 0; q < 15; ++q) li[q] = p[12 + q] * kHalfLog2eSqrt;
+                // the mean relative to the reference point, whitened
+                const float m[5] = {(p[0] - xr0) + p[32], (p[1] - xr1) + p[33], (p[2] - xr2) + p[34],
+                                    OFFS ? p[28] : 0.f, OFFS ? p[29] : 0.f};
+#pragma unroll
+                for (int a = 0; a < 5; ++a) {
+                    float acc_m = 0.f;
+#pragma unroll
+                    for (int b = 0; b <= a; ++b) acc_m = fmaf(li[pk(a, b)], m[b], acc_m);
+                    mo[a] = acc_m;
+                }
                 c5 = p[27];
             } else {                         // padding lane: density 0
 #pragma unroll
@@ -187,14 +194,15 @@ __global__ void __launch_bounds__(kEW * 32, kECtas)
         for (int s = 0; s < kStat; ++s) acc[s] = 0.f;
         float wsum = 0.f, wll = 0.f;
 
-        auto accumulate = [&](const float wr, const float d[5]) {
+        // statistics [1, y, y y^T] of one pair, weighted by w r
+        auto accumulate = [&](const float wr, const float y[5]) {
             acc[0] += wr;
 #pragma unroll
             for (int a = 0; a < 5; ++a) {
-                const float wa = wr * d[a];
+                const float wa = wr * y[a];
                 acc[1 + a] += wa;
 #pragma unroll
-                for (int b = 0; b <= a; ++b) acc[6 + pk(a, b)] = fmaf(wa, d[b], acc[6 + pk(a, b)]);
+                for (int b = 0; b <= a; ++b) acc[6 + pk(a, b)] = fmaf(wa, y[b], acc[6 + pk(a, b)]);
             }
         };
 
@@ -229,8 +237,8 @@ __global__ void __launch_bounds__(kEW * 32, kECtas)
                 const int ja = t + h, jb = t + SPI + h;   // both < 32; past n they carry weight 0
                 const float4 xa = s_x[warp][ja], wa = s_w[warp][ja];
                 const float4 xb = s_x[warp][jb], wb = s_w[warp][jb];
-                float da[5], db[5];
-                const float la = logp2(xa, wa, da), lb = logp2(xb, wb, db);
+                float ya[5], yb[5];
+                const float la = logp2(xa, wa, ya), lb = logp2(xb, wb, yb);
                 float refa = 0.f, refb = 0.f;       // shift on top of the region bound
                 if (SOLID) {
                     refa = la, refb = lb;
@@ -257,8 +265,8 @@ __global__ void __launch_bounds__(kEW * 32, kECtas)
                 const float ia = tc::rcp_approx(sa), ib = tc::rcp_approx(sb);
                 const float ra = sa >= kSumMin ? xa.w * ea * ia : 0.f;
                 const float rb = sb >= kSumMin ? xb.w * eb * ib : 0.f;
-                accumulate(ra, da);
-                accumulate(rb, db);
+                accumulate(ra, ya);
+                accumulate(rb, yb);
             }
             __syncwarp();
             // samples whose shifted sum underflowed: again with the exact maximum
@@ -271,8 +279,8 @@ __global__ void __launch_bounds__(kEW * 32, kECtas)
                 const bool act = jj < 32u;
                 const int j = act ? (int)jj : 0;
                 const float4 xa = s_x[warp][j], wa = s_w[warp][j];
-                float da[5];
-                const float l2 = logp2(xa, wa, da);
+                float ya[5];
+                const float l2 = logp2(xa, wa, ya);
                 float ref = l2;
 #pragma unroll
                 for (int o = KP / 2; o > 0; o >>= 1) ref = fmaxf(ref, __shfl_xor_sync(FULL, ref, o));
@@ -282,7 +290,7 @@ __global__ void __launch_bounds__(kEW * 32, kECtas)
                 for (int o = KP / 2; o > 0; o >>= 1) se += __shfl_xor_sync(FULL, se, o);
                 if (k == 0 && act) s_lse[warp][j] = make_float2(se, lmax + ref * kLn2F);
                 const float rr = (act && se >= kSumMin) ? __fdividef(xa.w * e, se) : 0.f;
-                accumulate(rr, da);
+                accumulate(rr, ya);
             }
             __syncwarp();
             // lane i: log-likelihood, weight and weighted log-likelihood of sample g + i

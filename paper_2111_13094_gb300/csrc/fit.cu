@@ -396,6 +396,37 @@ __device__ inline void reduce_partials(const float* __restrict__ partial, int ps
     }
 }
 
+// Statistics of the specialised E-step (k_estep) come in the whitened chart
+// coordinates y = c L^-1 d of each component (c = sqrt(log2(e) / 2), the
+// FP32 constant of that kernel): back to the chart, s1 = L s1_y / c and
+// s2 = L s2_y L^T / c^2 (sk = [s0, s1 (5), s2 (15, packed)], FP64).
+__device__ inline void whitened_to_chart(const double* __restrict__ L, double* __restrict__ sk) {
+    const double c = (double)0.849321800288019f;
+    double Y[5][5], T[5][5];
+    for (int a = 0; a < 5; ++a)
+        for (int b = 0; b <= a; ++b) Y[a][b] = Y[b][a] = sk[6 + pk(a, b)];
+    double s1[5];
+    for (int i = 0; i < 5; ++i) {
+        double v = 0.0;
+        for (int j = 0; j <= i; ++j) v += L[pk(i, j)] * sk[1 + j];
+        s1[i] = v / c;
+    }
+    for (int i = 0; i < 5; ++i)
+        for (int j = 0; j < 5; ++j) {
+            double v = 0.0;
+            for (int m = 0; m <= i; ++m) v += L[pk(i, m)] * Y[m][j];
+            T[i][j] = v;
+        }
+    for (int i = 0; i < 5; ++i) {
+        sk[1 + i] = s1[i];
+        for (int j = 0; j <= i; ++j) {
+            double v = 0.0;
+            for (int m = 0; m <= j; ++m) v += T[i][m] * L[pk(j, m)];
+            sk[6 + pk(i, j)] = v / (c * c);
+        }
+    }
+}
+
 __device__ inline double prior_beta(const sdmm_config& cfg, const double* prior_scale,
                                     int64_t r, int64_t seen) {
     if (cfg.prior_scale_mode == SDMM_PRIOR_SCALE_ARRAY && prior_scale != nullptr)
@@ -474,7 +505,7 @@ __global__ void __launch_bounds__(128) k_new_charts(WsHeader* __restrict__ ws,
                                                     const int64_t* __restrict__ chunk_base,
                                                     const float* __restrict__ partial, int ps,
                                                     sdmm_config cfg, sdmm_state st,
-                                                    float* __restrict__ chart2) {
+                                                    float* __restrict__ chart2, int ystats) {
     const int64_t r = blockIdx.x;
     const int K = cfg.K;
     const int tid = threadIdx.x;
@@ -485,6 +516,7 @@ __global__ void __launch_bounds__(128) k_new_charts(WsHeader* __restrict__ ws,
     __syncthreads();
     if (tid < K) {
         const int64_t rk = r * K + tid;
+        if (ystats) whitened_to_chart(st.L + rk * 15, s_st + tid * kStat);
         const double s0 = s_st[tid * kStat];
         double m[5], nmx[3], omw[3], nmw[3], t[3], b[3];
         for (int c = 0; c < 5; ++c) m[c] = (s0 > 0.0 && isfinite(s0)) ? s_st[tid * kStat + 1 + c] / s0 : 0.0;
@@ -514,7 +546,8 @@ __global__ void __launch_bounds__(128) k_reduce_mstep(WsHeader* __restrict__ ws,
                                                       const float* __restrict__ partial, int ps,
                                                       sdmm_config cfg, sdmm_state st, int iter,
                                                       const float* __restrict__ xref,
-                                                      const float* __restrict__ partial2, int ps2) {
+                                                      const float* __restrict__ partial2, int ps2,
+                                                      int ystats) {
     const int64_t r = blockIdx.x;
     const int K = cfg.K;
     const int tid = threadIdx.x;
@@ -566,6 +599,10 @@ __global__ void __launch_bounds__(128) k_reduce_mstep(WsHeader* __restrict__ ws,
         }
     } else {
         reduce_partials(partial, ps, c0, c1, K * kStat + 2, s_st);
+        if (ystats) {
+            __syncthreads();
+            for (int k = tid; k < K; k += blockDim.x) whitened_to_chart(st.L + (r * K + k) * 15, s_st + k * kStat);
+        }
     }
     if (TWO) reduce_partials(partial2, ps2, c0, c1, K * 15, s_two);
     __syncthreads();
@@ -1056,15 +1093,15 @@ cudaError_t launch_accumulate(cudaStream_t s, int mode, int KP, int grid, WsHead
 
 cudaError_t launch_new_charts(cudaStream_t s, int64_t R, WsHeader* ws, const int64_t* cb,
                               const float* partial, int ps, const sdmm_config& cfg,
-                              const sdmm_state& st, float* chart2) {
-    k_new_charts<<<(unsigned)R, 128, 0, s>>>(ws, cb, partial, ps, cfg, st, chart2);
+                              const sdmm_state& st, float* chart2, int ystats) {
+    k_new_charts<<<(unsigned)R, 128, 0, s>>>(ws, cb, partial, ps, cfg, st, chart2, ystats);
     return cudaGetLastError();
 }
 
 cudaError_t launch_reduce_mstep(cudaStream_t s, int64_t R, WsHeader* ws, const int64_t* cb,
                                 const float* partial, int ps, const sdmm_config& cfg,
                                 const sdmm_state& st, int iter, const float* xref,
-                                const float* partial2, int ps2, int threads) {
+                                const float* partial2, int ps2, int threads, int ystats) {
     // one CTA per region: thread k < K updates component k, all threads share
     // the reduction of the unit partials.  The caller picks the width: one
     // warp when the regions outnumber what 128-thread CTAs keep resident
@@ -1072,13 +1109,13 @@ cudaError_t launch_reduce_mstep(cudaStream_t s, int64_t R, WsHeader* ws, const i
     // faster reduction of many units) for a few large regions.
     if (xref != nullptr)
         k_reduce_mstep<true, false><<<(unsigned)R, threads, 0, s>>>(ws, cb, partial, ps, cfg, st, iter, xref,
-                                                                   nullptr, 0);
+                                                                   nullptr, 0, 0);
     else if (partial2 != nullptr)
         k_reduce_mstep<false, true><<<(unsigned)R, threads, 0, s>>>(ws, cb, partial, ps, cfg, st, iter, xref,
-                                                                   partial2, ps2);
+                                                                   partial2, ps2, ystats);
     else
         k_reduce_mstep<false, false><<<(unsigned)R, threads, 0, s>>>(ws, cb, partial, ps, cfg, st, iter, xref,
-                                                                    nullptr, 0);
+                                                                    nullptr, 0, ystats);
     return cudaGetLastError();
 }
 

@@ -32,13 +32,16 @@ bool estep_fast_supported(int KP);
 cudaError_t launch_estep_fast(cudaStream_t s, int KP, int grid, WsHeader* ws, const int64_t* cb,
                               const int32_t* cr, const float* etab, int K, int chunk, float* partial,
                               int ps, int write_ll, int variant);
+// ystats: the E-step partials are in whitened coordinates (k_estep); the
+// reductions take them back to the chart
 cudaError_t launch_new_charts(cudaStream_t s, int64_t R, WsHeader* ws, const int64_t* cb,
                               const float* partial, int ps, const sdmm_config& cfg,
-                              const sdmm_state& st, float* chart2);
+                              const sdmm_state& st, float* chart2, int ystats);
 cudaError_t launch_reduce_mstep(cudaStream_t s, int64_t R, WsHeader* ws, const int64_t* cb,
                                 const float* partial, int ps, const sdmm_config& cfg,
                                 const sdmm_state& st, int iter, const float* xref,
-                                const float* partial2 = nullptr, int ps2 = 0, int threads = 128);
+                                const float* partial2 = nullptr, int ps2 = 0, int threads = 128,
+                                int ystats = 0);
 // contraction form on the tensor cores
 size_t tc_smem_bytes(int K, int prec);
 
