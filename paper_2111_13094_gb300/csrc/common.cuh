@@ -171,11 +171,12 @@ __device__ inline bool cholesky5_f64(const double S[15], double L[15]) {
         for (int p = 0; p < j; ++p) d -= L[pk(j, p)] * L[pk(j, p)];
         if (!(d > 0.0) || !isfinite(d)) return false;
         const double ljj = sqrt(d);
+        const double il = 1.0 / ljj;
         L[pk(j, j)] = ljj;
         for (int i = j + 1; i < 5; ++i) {
             double e = S[pk(i, j)];
             for (int p = 0; p < j; ++p) e -= L[pk(i, p)] * L[pk(j, p)];
-            L[pk(i, j)] = e / ljj;
+            L[pk(i, j)] = e * il;
         }
     }
     return true;
@@ -183,12 +184,12 @@ __device__ inline bool cholesky5_f64(const double S[15], double L[15]) {
 
 // Inverse of a packed lower-triangular 5x5 (also lower triangular).
 __device__ inline void lower_inverse5_f64(const double L[15], double Li[15]) {
+    for (int j = 0; j < 5; ++j) Li[pk(j, j)] = 1.0 / L[pk(j, j)];
     for (int j = 0; j < 5; ++j) {
-        Li[pk(j, j)] = 1.0 / L[pk(j, j)];
         for (int i = j + 1; i < 5; ++i) {
             double s = 0.0;
             for (int p = j; p < i; ++p) s += L[pk(i, p)] * Li[pk(p, j)];
-            Li[pk(i, j)] = -s / L[pk(i, i)];
+            Li[pk(i, j)] = -s * Li[pk(i, i)];
         }
     }
 }

@@ -402,6 +402,7 @@ __device__ inline void reduce_partials(const float* __restrict__ partial, int ps
 // s2 = L s2_y L^T / c^2 (sk = [s0, s1 (5), s2 (15, packed)], FP64).
 __device__ inline void whitened_to_chart(const double* __restrict__ L, double* __restrict__ sk) {
     const double c = (double)0.849321800288019f;
+    const double ic = 1.0 / c, ic2 = ic * ic;      // folded at compile time: no FP64 division per entry
     double Y[5][5], T[5][5];
     for (int a = 0; a < 5; ++a)
         for (int b = 0; b <= a; ++b) Y[a][b] = Y[b][a] = sk[6 + pk(a, b)];
@@ -409,7 +410,7 @@ __device__ inline void whitened_to_chart(const double* __restrict__ L, double* _
     for (int i = 0; i < 5; ++i) {
         double v = 0.0;
         for (int j = 0; j <= i; ++j) v += L[pk(i, j)] * sk[1 + j];
-        s1[i] = v / c;
+        s1[i] = v * ic;
     }
     for (int i = 0; i < 5; ++i)
         for (int j = 0; j < 5; ++j) {
@@ -422,7 +423,7 @@ __device__ inline void whitened_to_chart(const double* __restrict__ L, double* _
         for (int j = 0; j <= i; ++j) {
             double v = 0.0;
             for (int m = 0; m <= j; ++m) v += T[i][m] * L[pk(j, m)];
-            sk[6 + pk(i, j)] = v / (c * c);
+            sk[6 + pk(i, j)] = v * ic2;
         }
     }
 }
@@ -637,10 +638,11 @@ __global__ void __launch_bounds__(128) k_reduce_mstep(WsHeader* __restrict__ ws,
         hS0 = (1.0 - eta) * st.S0[rk] + eta * (sk[0] * invW);
         double m[5], hS2[15];
         bool fin = isfinite(hS0);
+        const double inv0 = hS0 > 0.0 ? 1.0 / hS0 : 0.0;
         for (int c = 0; c < 5; ++c) {
             const double h1 = eta * (sk[1 + c] * invW);
             fin = fin && isfinite(h1);
-            m[c] = hS0 > 0.0 ? h1 / hS0 : 0.0;
+            m[c] = h1 * inv0;
         }
         for (int p = 0; p < 15; ++p) {
             hS2[p] = (1.0 - eta) * st.S2[rk * 15 + p] + eta * (sk[6 + p] * invW);
@@ -691,11 +693,11 @@ __global__ void __launch_bounds__(128) k_reduce_mstep(WsHeader* __restrict__ ws,
             // MAP covariance (Sec. 4.3)
             const double Bd[5] = {a * cfg.prior_B_pos, a * cfg.prior_B_pos, a * cfg.prior_B_pos,
                                   a * cfg.prior_B_dir, a * cfg.prior_B_dir};
-            const double den = beta * a + hS0;
+            const double iden = 1.0 / (beta * a + hS0);
             double Sig[15];
             for (int i = 0; i < 5; ++i)
                 for (int j = 0; j <= i; ++j)
-                    Sig[pk(i, j)] = ((i == j ? beta * Bd[i] : 0.0) + nS2[pk(i, j)]) / den;
+                    Sig[pk(i, j)] = ((i == j ? beta * Bd[i] : 0.0) + nS2[pk(i, j)]) * iden;
             if (!cholesky5_f64(Sig, nL)) {
                 // numerical floor: smallest tau * B / a (tau = 1e-6 ... 1) that
                 // makes the covariance positive definite; the region is flagged
