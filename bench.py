@@ -619,9 +619,10 @@ def query_leg(args, api, torch, dev, stream, seed, world, cfg, peaks, src, n_sm,
     bw_b, bmu_b, bL_b = bw[order].contiguous(), bmu[order].contiguous(), bL[order].contiguous()
     t_prod_b = _timed(lambda: api.product_sample(cfg, qst, qx_b, bw_b, bmu_b, bL_b, region=reg_b, seed=7), stream)
     qres["product"] = {"value": world * Q / (t_prod * 1e-3), "unit": "queries/s", "kernel_ms": t_prod,
-                       "binned_value": world * Q / (t_prod_b * 1e-3), "binned_kernel_ms": t_prod_b,
-                       "config": "the same 16M queries, 3 BSDF lobes each (wide, narrow, random), "
-                                 "2K pairs per query: condition + pair products + sample + product pdf, FP32"}
+                       "presorted_value": world * Q / (t_prod_b * 1e-3), "presorted_kernel_ms": t_prod_b,
+                       "config": f"the same {Q} queries, 3 BSDF lobes each (wide, narrow, random), "
+                                 "2K pairs per query: condition + pair products + sample + product pdf, FP32; "
+                                 "presorted: the queries ordered by region beforehand"}
     del bw, bmu, bL, bw_b, bmu_b, bL_b, qst, out, qws
     return qres
 

@@ -77,18 +77,29 @@ __device__ inline void exp_map_f64(const double mu[3], const double nu[2], doubl
     for (int c = 0; c < 3; ++c) out[c] = t[c] * a0 + b[c] * a1 + mu[c] * a2;
 }
 
-// Chart-change Jacobian J = J_log_{mu_new}(mu_new) * J_exp_{mu_old}(nu)
-// (App. A; at the chart centre J_log is the projection onto (t, b) of mu_new).
-__device__ inline void chart_jacobian_f64(const double mu_old[3], const double nu[2],
-                                          const double mu_new[3], double J[4]) {
+// New mean mu_new = exp_{mu_old}(nu) and the chart-change Jacobian
+// J = J_log_{mu_new}(mu_new) * J_exp_{mu_old}(nu) (App. A; at the chart centre
+// J_log is the projection onto (t, b) of mu_new), sharing one sincos.
+__device__ inline void exp_map_jacobian_f64(const double mu_old[3], const double nu[2], double mu_new[3],
+                                            double J[4]) {
     double t0[3], b0[3], t1[3], b1[3];
     basis_f64(mu_old, t0, b0);
-    basis_f64(mu_new, t1, b1);
     const double r2 = nu[0] * nu[0] + nu[1] * nu[1];
     const double r = sqrt(r2);
-    const double s = sinc_f64(r);
-    const double c = (r < 1e-2) ? (-1.0 / 3.0 + r2 / 30.0 - r2 * r2 / 840.0) : (cos(r) - s) / r2;
-    // d exp / d nu in the old chart's coordinates (3x2), then to world
+    double sr, cr;
+    sincos(r, &sr, &cr);
+    double s, c;
+    if (r < 1e-2) {
+        s = 1.0 - r2 / 6.0 + r2 * r2 / 120.0;
+        c = -1.0 / 3.0 + r2 / 30.0 - r2 * r2 / 840.0;
+    } else {
+        const double ir = 1.0 / r;
+        s = sr * ir;
+        c = (cr - s) * (ir * ir);
+    }
+    const double a0 = nu[0] * s, a1 = nu[1] * s;
+    for (int q = 0; q < 3; ++q) mu_new[q] = t0[q] * a0 + b0[q] * a1 + mu_old[q] * cr;
+    basis_f64(mu_new, t1, b1);
     const double Jp[3][2] = {{s + nu[0] * nu[0] * c, nu[0] * nu[1] * c},
                              {nu[0] * nu[1] * c, s + nu[1] * nu[1] * c},
                              {-nu[0] * s, -nu[1] * s}};
@@ -208,8 +219,10 @@ __device__ inline void write_records(double pi, const double mux[3], const doubl
     }
     lower_inverse5_f64(L, Li);
     const double lpi = pi > 0.0 ? log(pi) : -INFINITY;
-    const double ldA = log(L[pk(0, 0)]) + log(L[pk(1, 1)]) + log(L[pk(2, 2)]);
-    const double ldD = log(L[pk(3, 3)]) + log(L[pk(4, 4)]);
+    // log det of the blocks as the log of the product of the pivots (two FP64
+    // logs instead of five; the pivots are far from the FP64 range's ends)
+    const double ldA = log(L[pk(0, 0)] * L[pk(1, 1)] * L[pk(2, 2)]);
+    const double ldD = log(L[pk(3, 3)] * L[pk(4, 4)]);
     for (int c = 0; c < 3; ++c) {
         er[0 + c] = qr[0 + c] = (float)mux[c];
         er[3 + c] = qr[3 + c] = (float)t[c];

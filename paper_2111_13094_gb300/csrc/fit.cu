@@ -657,12 +657,13 @@ __global__ void __launch_bounds__(128) k_reduce_mstep(WsHeader* __restrict__ ws,
                 omw[c] = st.mu_w[rk * 3 + c];
                 nmx[c] = omx[c] + m[c];
             }
+            double J[4] = {1.0, 0.0, 0.0, 1.0};        // chart change (Sec. 3.4), identity if Euclidean
             if (euclid) {                                 // ablation: translate (x, y)
                 nmw[0] = omw[0] + m[3];
                 nmw[1] = omw[1] + m[4];
                 nmw[2] = omw[2];
             } else {
-                exp_map_f64(omw, m + 3, nmw);             // Eq. tangent-space-mu-update
+                exp_map_jacobian_f64(omw, m + 3, nmw, J);   // Eq. tangent-space-mu-update
             }
             if (TWO) {
                 // accurate update (Eq. tangent-space-sigma-update): the second
@@ -674,8 +675,6 @@ __global__ void __launch_bounds__(128) k_reduce_mstep(WsHeader* __restrict__ ws,
                 for (int i = 0; i < 5; ++i)
                     for (int j = 0; j <= i; ++j) C[pk(i, j)] = hS2[pk(i, j)] - hS0 * m[i] * m[j];
                 // ... moved to the new chart: T C T^T, T = blockdiag(I3, J) (Sec. 3.4)
-                double J[4] = {1.0, 0.0, 0.0, 1.0};
-                if (!euclid) chart_jacobian_f64(omw, m + 3, nmw, J);
                 for (int i = 0; i < 3; ++i)
                     for (int j = 0; j <= i; ++j) nS2[pk(i, j)] = C[pk(i, j)];
                 for (int ia = 0; ia < 2; ++ia)
