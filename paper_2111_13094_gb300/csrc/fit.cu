@@ -388,8 +388,9 @@ __global__ void __launch_bounds__(kWarps * 32, 2)
 // ---------------------------------------------------------------------------
 // Sum of a region's unit partials in FP64, in unit order (deterministic).
 __device__ inline void reduce_partials(const float* __restrict__ partial, int ps, int64_t c0,
-                                       int64_t c1, int nv, double* __restrict__ out) {
-    for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+                                       int64_t c1, int nv, double* __restrict__ out, int t0 = threadIdx.x,
+                                       int nt = blockDim.x) {
+    for (int v = t0; v < nv; v += nt) {
         double s = 0.0;
         for (int64_t c = c0; c < c1; ++c) s += (double)partial[c * ps + v];
         out[v] = s;
@@ -541,33 +542,54 @@ __global__ void __launch_bounds__(128) k_new_charts(WsHeader* __restrict__ ws,
 }
 
 
-template <bool FEAT, bool TWO>
+// G regions per CTA: with one-warp CTAs and K <= 16, lanes 0-15 update the
+// components of one region and lanes 16-31 those of the next.  A warp's FP64
+// instruction occupies the SM's FP64 pipe equally long with 16 or 32 active
+// lanes, and this kernel is bound by that pipe, so two regions per warp halve
+// its time.  Threads of a group: gsz = blockDim.x / G; thread k < K of the
+// group updates component k; the group's threads share the reduction.
+template <bool FEAT, bool TWO, int G>
 __global__ void __launch_bounds__(128) k_reduce_mstep(WsHeader* __restrict__ ws,
                                                       const int64_t* __restrict__ chunk_base,
                                                       const float* __restrict__ partial, int ps,
                                                       sdmm_config cfg, sdmm_state st, int iter,
                                                       const float* __restrict__ xref,
                                                       const float* __restrict__ partial2, int ps2,
-                                                      int ystats) {
-    const int64_t r = blockIdx.x;
+                                                      int ystats, int64_t R) {
+    static_assert(G == 1 || (!FEAT && 32 % G == 0), "packed regions: plain statistics, one warp");
+    constexpr int KC = G == 1 ? SDMM_MAX_K : 32 / G;      // components per group, at most
     const int K = cfg.K;
-    const int tid = threadIdx.x;
-    __shared__ double s_st[SDMM_MAX_K * kStat + 2];
+    const int gsz = blockDim.x / G;
+    const int grp = threadIdx.x / gsz, tid = threadIdx.x - grp * gsz;
+    const int64_t r = (int64_t)blockIdx.x * G + grp;
+    const bool have = r < R;
+    __shared__ double s_stg[G][KC * kStat + 2];
     __shared__ double s_feat[FEAT ? 3 * SDMM_MAX_K * kFeat + 8 : 1];
-    __shared__ double s_S0[SDMM_MAX_K];
-    __shared__ double s_two[TWO ? SDMM_MAX_K * 15 : 1];   // second-pass moments (accurate update)
-    __shared__ int s_code[SDMM_MAX_K];
-    __shared__ int s_skip;
+    __shared__ double s_S0g[G][KC];
+    __shared__ double s_twog[TWO ? G : 1][TWO ? KC * 15 : 1];   // second-pass moments (accurate update)
+    __shared__ int s_codeg[G][KC];
+    __shared__ int s_skip[G];
+    double* const s_st = s_stg[grp];
+    double* const s_S0 = s_S0g[grp];
+    double* const s_two = s_twog[TWO ? grp : 0];
+    int* const s_code = s_codeg[grp];
 
     // the accumulate kernel of this step has finished: re-arm its work queue
-    if (r == 0 && tid == 0) ws->queue = 0;
-    const int64_t o0 = ws->desc.offsets[r], o1 = ws->desc.offsets[r + 1];
+    if (blockIdx.x == 0 && threadIdx.x == 0) ws->queue = 0;
+    int64_t o0 = 0, o1 = 0, c0 = 0, c1 = 0;
+    if (have) {
+        o0 = ws->desc.offsets[r];
+        o1 = ws->desc.offsets[r + 1];
+        c0 = chunk_base[r];
+        c1 = chunk_base[r + 1];
+    }
     const int64_t M = o1 - o0;
     const int64_t n_chunks = ws->n_chunks;
-    const int64_t c0 = chunk_base[r], c1 = chunk_base[r + 1];
     if (tid == 0) {
         int code = -1;  // -1: proceed
-        if (iter == 0) {
+        if (!have) {
+            code = 0;
+        } else if (iter == 0) {
             if (!(o0 >= 0 && o1 >= o0 && o1 <= ws->desc.N) || c1 > n_chunks)
                 code = SDMM_REGION_BAD_OFFSETS;
             else if (M < cfg.min_samples || M <= 0) code = SDMM_REGION_SKIPPED;
@@ -575,14 +597,15 @@ __global__ void __launch_bounds__(128) k_reduce_mstep(WsHeader* __restrict__ ws,
         } else if (st.status[r] != SDMM_REGION_OK && st.status[r] != SDMM_REGION_REPAIRED) {
             code = st.status[r];
         }
-        s_skip = code;
+        s_skip[grp] = code;
     }
     __syncthreads();
-    if (s_skip >= 0) return;
+    bool alive = s_skip[grp] < 0;
+    // (every thread reaches each __syncthreads below; dead groups only skip work)
     if (FEAT) {
-        reduce_partials(partial, ps, c0, c1, 3 * K * kFeat + 8, s_feat);
+        if (alive) reduce_partials(partial, ps, c0, c1, 3 * K * kFeat + 8, s_feat, tid, gsz);
         __syncthreads();
-        if (tid < K) {
+        if (alive && tid < K) {
             const int64_t rk = r * K + tid;
             double mp[3], muw[3];
             for (int c = 0; c < 3; ++c) {
@@ -593,44 +616,51 @@ __global__ void __launch_bounds__(128) k_reduce_mstep(WsHeader* __restrict__ ws,
                               s_feat + (2 * K + tid) * kFeat, mp, muw, s_st + tid * kStat,
                               cfg.dir_coords == SDMM_DIR_EUCLIDEAN);
         }
-        if (tid == 0) {   // W and sum w l arrive as four per-quadrant parts each
+        if (alive && tid == 0) {   // W and sum w l arrive as four per-quadrant parts each
             const double* wq = s_feat + 3 * K * kFeat;
             s_st[K * kStat] = (wq[0] + wq[1]) + (wq[2] + wq[3]);
             s_st[K * kStat + 1] = (wq[4] + wq[5]) + (wq[6] + wq[7]);
         }
     } else {
-        reduce_partials(partial, ps, c0, c1, K * kStat + 2, s_st);
+        if (alive) reduce_partials(partial, ps, c0, c1, K * kStat + 2, s_st, tid, gsz);
         if (ystats) {
             __syncthreads();
-            for (int k = tid; k < K; k += blockDim.x) whitened_to_chart(st.L + (r * K + k) * 15, s_st + k * kStat);
+            if (alive)
+                for (int k = tid; k < K; k += gsz) whitened_to_chart(st.L + (r * K + k) * 15, s_st + k * kStat);
         }
     }
-    if (TWO) reduce_partials(partial2, ps2, c0, c1, K * 15, s_two);
+    if (TWO && alive) reduce_partials(partial2, ps2, c0, c1, K * 15, s_two, tid, gsz);
     __syncthreads();
-    const double W = s_st[K * kStat];
-    if (tid == 0) {
+    const double W = alive ? s_st[K * kStat] : 0.0;
+    if (tid == 0 && alive) {
         int code = -1;
         if (ws->err != 0) code = SDMM_REGION_DEVICE_TIMEOUT;
         else if (!isfinite(W)) code = SDMM_REGION_NONFINITE;
         else if (!(W > 0.0)) code = SDMM_REGION_ZERO_WEIGHT;
         if (code >= 0) st.status[r] = code;
-        s_skip = code;
+        s_skip[grp] = code;
     }
     __syncthreads();
-    if (s_skip >= 0) return;
+    alive = alive && s_skip[grp] < 0;
 
-    const int64_t seen = (iter == 0) ? st.n_seen[r] + M : st.n_seen[r];
-    const double beta = prior_beta(cfg, ws->desc.prior_scale, r, seen);
-    const double eta = (cfg.eta_mode == SDMM_ETA_ONE)
-                           ? 1.0
-                           : pow(cfg.eta_beta * (double)st.step_j[r] + 1.0, -cfg.eta_alpha);
+    int64_t seen = 0;
+    double beta = 0.0, eta = 1.0;
+    if (alive) {
+        seen = (iter == 0) ? st.n_seen[r] + M : st.n_seen[r];
+        beta = prior_beta(cfg, ws->desc.prior_scale, r, seen);
+        if (cfg.eta_mode != SDMM_ETA_ONE) {
+            // (0.1 j + 1)^-alpha; the paper's alpha = 1/2 as one reciprocal square root
+            const double base = cfg.eta_beta * (double)st.step_j[r] + 1.0;
+            eta = cfg.eta_alpha == 0.5 ? rsqrt(base) : pow(base, -cfg.eta_alpha);
+        }
+    }
     const double q = cfg.prior_q / K, a = cfg.prior_a / K;
     const bool euclid = cfg.dir_coords == SDMM_DIR_EUCLIDEAN;
 
     double nmx[3], nmw[3], nL[15], nS2[15], hS0 = 0.0;
     int code = 0;
     const int64_t rk = r * K + tid;
-    if (tid < K) {
+    if (alive && tid < K) {
         const double* sk = s_st + tid * kStat;
         const double invW = 1.0 / W;
         // Robbins-Monro average of the normalised batch statistics; the
@@ -716,18 +746,19 @@ __global__ void __launch_bounds__(128) k_reduce_mstep(WsHeader* __restrict__ ws,
         s_S0[tid] = hS0;
     }
     __syncthreads();
-    if (tid == 0) {
+    if (alive && tid == 0) {
         int first = 0, repaired = 0;
         for (int kk = 0; kk < K && first == 0; ++kk) {
             if (s_code[kk] == SDMM_REGION_REPAIRED) repaired = 1;
             else first = s_code[kk];
         }
-        s_skip = first;
+        s_skip[grp] = first;
         if (first != 0) st.status[r] = first;
         s_code[0] = repaired;
     }
     __syncthreads();
-    if (s_skip != 0) return;
+    alive = alive && s_skip[grp] == 0;
+    if (!alive) return;                      // no barrier follows
     const bool repaired = s_code[0] != 0;
     if (tid < K) {
         double sumS0 = 0.0;
@@ -1108,15 +1139,25 @@ cudaError_t launch_reduce_mstep(cudaStream_t s, int64_t R, WsHeader* ws, const i
     // warp when the regions outnumber what 128-thread CTAs keep resident
     // (the per-component thread needs about 156 registers), four warps (a
     // faster reduction of many units) for a few large regions.
+    const unsigned g1 = (unsigned)R;
     if (xref != nullptr)
-        k_reduce_mstep<true, false><<<(unsigned)R, threads, 0, s>>>(ws, cb, partial, ps, cfg, st, iter, xref,
-                                                                   nullptr, 0, 0);
-    else if (partial2 != nullptr)
-        k_reduce_mstep<false, true><<<(unsigned)R, threads, 0, s>>>(ws, cb, partial, ps, cfg, st, iter, xref,
-                                                                   partial2, ps2, ystats);
+        k_reduce_mstep<true, false, 1><<<g1, threads, 0, s>>>(ws, cb, partial, ps, cfg, st, iter, xref,
+                                                              nullptr, 0, 0, R);
+    else if (threads == 32 && cfg.K <= 16) {
+        // two regions per warp (lanes 0-15 and 16-31)
+        const unsigned g2 = (unsigned)((R + 1) / 2);
+        if (partial2 != nullptr)
+            k_reduce_mstep<false, true, 2><<<g2, 32, 0, s>>>(ws, cb, partial, ps, cfg, st, iter, xref,
+                                                             partial2, ps2, ystats, R);
+        else
+            k_reduce_mstep<false, false, 2><<<g2, 32, 0, s>>>(ws, cb, partial, ps, cfg, st, iter, xref,
+                                                              nullptr, 0, ystats, R);
+    } else if (partial2 != nullptr)
+        k_reduce_mstep<false, true, 1><<<g1, threads, 0, s>>>(ws, cb, partial, ps, cfg, st, iter, xref,
+                                                              partial2, ps2, ystats, R);
     else
-        k_reduce_mstep<false, false><<<(unsigned)R, threads, 0, s>>>(ws, cb, partial, ps, cfg, st, iter, xref,
-                                                                    nullptr, 0, ystats);
+        k_reduce_mstep<false, false, 1><<<g1, threads, 0, s>>>(ws, cb, partial, ps, cfg, st, iter, xref,
+                                                               nullptr, 0, ystats, R);
     return cudaGetLastError();
 }
 
