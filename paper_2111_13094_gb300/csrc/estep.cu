@@ -189,21 +189,36 @@ __global__ void __launch_bounds__(kEW * 32, kECtas)
             c2 = (c5 - lmax) * kLog2eF;               // -inf for zero weights and padding lanes
         }
 
-        float acc[kStat];
-#pragma unroll
-        for (int s = 0; s < kStat; ++s) acc[s] = 0.f;
+        // the statistics [s0, s1 (5), s2 (15, packed)]; five pairs of them sit
+        // in float2 registers for the packed FP32 instructions of sm_100+
+        // (one instruction, two lanes' worth of FMA): s1 (0, 1) and (2, 3),
+        // s2 (0,0)+(1,1), (2,2)+(3,3) and (2,0)+(3,1)
+        float a_s0 = 0.f, a_s14 = 0.f, a_10 = 0.f, a_21 = 0.f, a_30 = 0.f, a_32 = 0.f;
+        float a_4[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+        float2 a_s101 = make_float2(0.f, 0.f), a_s123 = make_float2(0.f, 0.f);
+        float2 a_d01 = make_float2(0.f, 0.f), a_d23 = make_float2(0.f, 0.f), a_x = make_float2(0.f, 0.f);
         float wsum = 0.f, wll = 0.f;
 
-        // statistics [1, y, y y^T] of one pair, weighted by w r
+        // statistics [1, y, y y^T] of one pair, weighted by w r: the products
+        // w_a y_b (w_a = w r y_a, a >= b) of the scalar form, 20 instructions
         auto accumulate = [&](const float wr, const float y[5]) {
-            acc[0] += wr;
+            const float2 y01 = make_float2(y[0], y[1]), y23 = make_float2(y[2], y[3]);
+            const float2 wr2 = make_float2(wr, wr);
+            const float2 w01 = __fmul2_rn(wr2, y01), w23 = __fmul2_rn(wr2, y23);
+            const float w4 = wr * y[4];
+            a_s0 += wr;
+            a_s101 = __fadd2_rn(a_s101, w01);
+            a_s123 = __fadd2_rn(a_s123, w23);
+            a_s14 += w4;
+            a_d01 = __ffma2_rn(w01, y01, a_d01);
+            a_d23 = __ffma2_rn(w23, y23, a_d23);
+            a_x = __ffma2_rn(w23, y01, a_x);
+            a_10 = fmaf(w01.y, y[0], a_10);
+            a_21 = fmaf(w23.x, y[1], a_21);
+            a_30 = fmaf(w23.y, y[0], a_30);
+            a_32 = fmaf(w23.y, y[2], a_32);
 #pragma unroll
-            for (int a = 0; a < 5; ++a) {
-                const float wa = wr * y[a];
-                acc[1 + a] += wa;
-#pragma unroll
-                for (int b = 0; b <= a; ++b) acc[6 + pk(a, b)] = fmaf(wa, y[b], acc[6 + pk(a, b)]);
-            }
+            for (int b = 0; b < 5; ++b) a_4[b] = fmaf(w4, y[b], a_4[b]);
         };
 
         // raw values of this lane's sample of the next batch
@@ -305,6 +320,16 @@ __global__ void __launch_bounds__(kEW * 32, kECtas)
             }
             __syncwarp();
         }
+        // back to [s0, s1, s2 packed]
+        float acc[kStat];
+        acc[0] = a_s0;
+        acc[1] = a_s101.x, acc[2] = a_s101.y, acc[3] = a_s123.x, acc[4] = a_s123.y, acc[5] = a_s14;
+        acc[6 + pk(0, 0)] = a_d01.x, acc[6 + pk(1, 1)] = a_d01.y;
+        acc[6 + pk(2, 2)] = a_d23.x, acc[6 + pk(3, 3)] = a_d23.y;
+        acc[6 + pk(2, 0)] = a_x.x, acc[6 + pk(3, 1)] = a_x.y;
+        acc[6 + pk(1, 0)] = a_10, acc[6 + pk(2, 1)] = a_21, acc[6 + pk(3, 0)] = a_30, acc[6 + pk(3, 2)] = a_32;
+#pragma unroll
+        for (int b = 0; b < 5; ++b) acc[6 + pk(4, b)] = a_4[b];
         // combine the SPI sample slots of each component; W and sum w l over all lanes
 #pragma unroll
         for (int o = KP; o < 32; o <<= 1) {
