@@ -886,7 +886,9 @@ def config_ablations(api, torch, dev, stream, want_cpu, R=1024, M=16384, K=16, r
     del samples, batch
     # E-step density and directions: E-step kernel time from the plan's events
     for key, seed, MM, variants in (
-            ("estep_density", 50, M, (("chart", {}), ("solid_angle", {"estep_density": 1}))),
+            ("estep_density", 50, M, (("chart", {}), ("solid_angle", {"estep_density": 1}),
+                                      ("6xbf16_chart", {"precision": 4}),
+                                      ("6xbf16_solid_angle", {"precision": 4, "estep_density": 1}))),
             ("directions", 80, 65536, (("fp32_tangent", {}), ("fp32_euclidean", {"dir_coords": 1}),
                                        ("6xbf16_tangent", {"precision": 4}),
                                        ("6xbf16_euclidean", {"precision": 4, "dir_coords": 1})))):
@@ -918,6 +920,7 @@ def config_ablations(api, torch, dev, stream, want_cpu, R=1024, M=16384, K=16, r
         torch.cuda.empty_cache()
     d = out["estep_density"]
     d["ratio"] = d["solid_angle_estep_ms"] / d["chart_estep_ms"]
+    d["6xbf16_ratio"] = d["6xbf16_solid_angle_estep_ms"] / d["6xbf16_chart_estep_ms"]
     e = out["directions"]
     e["fp32_ratio"] = e["fp32_tangent_estep_ms"] / e["fp32_euclidean_estep_ms"]
     e["6xbf16_ratio"] = e["6xbf16_tangent_estep_ms"] / e["6xbf16_euclidean_estep_ms"]

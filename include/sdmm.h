@@ -116,7 +116,7 @@ typedef struct sdmm_config {
                                   caller's per-region array                   */
     int32_t precision;         /* SDMM_PREC_*: E-step arithmetic.  FP32: SIMT
                                   kernel.  TC_*: contraction form on the
-                                  tensor cores (K = 16 or 32, tangent
+                                  tensor cores (K = 16 or 32, either
                                   density): per-sample features times a
                                   per-region coefficient matrix in split
                                   3xBF16 (two BF16 pieces, three products),

@@ -109,8 +109,6 @@ sdmm_status check_config(const sdmm_config* cfg) {
         return fail(SDMM_ERR_INVALID_ARG, "precision %d", cfg->precision);
     if (cfg->precision != SDMM_PREC_FP32 && !(cfg->K == 16 || cfg->K == 32))
         return fail(SDMM_ERR_UNSUPPORTED, "tensor-core precision needs K = 16 or 32 (K = %d)", cfg->K);
-    if (cfg->precision != SDMM_PREC_FP32 && cfg->estep_density != SDMM_DENSITY_TANGENT)
-        return fail(SDMM_ERR_UNSUPPORTED, "tensor-core precision supports the tangent density only");
     if (cfg->chunk != 0 && (cfg->chunk < 256 || cfg->chunk > 65536 || cfg->chunk % 256 != 0))
         return fail(SDMM_ERR_INVALID_ARG, "chunk %d: 0 or a multiple of 256 in [256, 65536]", cfg->chunk);
     if (cfg->ctas_per_sm < 0 || cfg->ctas_per_sm > 4)
@@ -287,7 +285,8 @@ sdmm_status enqueue_fit(const FitLaunch& f, cudaStream_t s, std::vector<cudaEven
         if (tcore) {
             const int grid = std::max(1, sm_count()) * tc_ctas_per_sm(f.cfg.K, f.cfg.precision);   // persistent
             SDMM_CUDA(launch_tc_estep(s, f.cfg.K, f.cfg.precision, grid, f.w.hdr, f.w.cr, f.w.units, f.w.ctab,
-                                      f.w.xref, f.w.partial, f.L.ps, wll, euclid),
+                                      f.w.xref, f.w.partial, f.L.ps, wll, euclid,
+                                      f.cfg.estep_density == SDMM_DENSITY_SOLID_ANGLE),
                       "tc_estep");
         } else {
             SDMM_CUDA(launch_accumulate(s, MODE_FIT, KP, f.grid, f.w.hdr, f.w.cb, f.w.cr, f.st.etab, f.cfg.K,

@@ -547,9 +547,12 @@ __global__ void __launch_bounds__(128) k_new_charts(WsHeader* __restrict__ ws,
 // instruction occupies the SM's FP64 pipe equally long with 16 or 32 active
 // lanes, and this kernel is bound by that pipe, so two regions per warp halve
 // its time.  Threads of a group: gsz = blockDim.x / G; thread k < K of the
-// group updates component k; the group's threads share the reduction.
+// group updates component k; the group's threads share the reduction.  The
+// packed form is capped at 128 registers so that 16 one-warp CTAs fit on an
+// SM and the 4,096-region fit's 2,048 CTAs run in one wave (a few spilled
+// FP64 values cost less than a second, nearly empty wave).
 template <bool FEAT, bool TWO, int G>
-__global__ void __launch_bounds__(128) k_reduce_mstep(WsHeader* __restrict__ ws,
+__global__ void __launch_bounds__(G == 1 ? 128 : 32, G == 1 ? 1 : 16) k_reduce_mstep(WsHeader* __restrict__ ws,
                                                       const int64_t* __restrict__ chunk_base,
                                                       const float* __restrict__ partial, int ps,
                                                       sdmm_config cfg, sdmm_state st, int iter,

@@ -50,7 +50,7 @@ cudaError_t launch_tc_prepare(cudaStream_t s, int K, int64_t R, const sdmm_state
 int tc_ctas_per_sm(int K, int prec);
 cudaError_t launch_tc_estep(cudaStream_t s, int K, int prec, int grid, WsHeader* ws, const int32_t* cr,
                             const int64_t* units, const float* ctab, const float* xref, float* partial,
-                            int ps, int write_ll, int euclid = 0);
+                            int ps, int write_ll, int euclid = 0, int solid = 0);
 cudaError_t launch_reduce_objective(cudaStream_t s, int64_t R, const WsHeader* ws,
                                     const int64_t* cb, const float* partial, int ps,
                                     const sdmm_config& cfg, const sdmm_state& st, double* F,

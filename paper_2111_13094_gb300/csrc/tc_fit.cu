@@ -421,7 +421,8 @@ template <int K, int PREC, bool EU>
 __global__ void __launch_bounds__(kTcThreads, TcPlan<K, PREC>::kCtas)
     k_tc_estep(WsHeader* __restrict__ ws, const int32_t* __restrict__ chunk_region,
                const int64_t* __restrict__ units, const float* __restrict__ ctab,
-               const float* __restrict__ xref, float* __restrict__ partial, int ps, int write_ll) {
+               const float* __restrict__ xref, float* __restrict__ partial, int ps, int write_ll,
+               int solid) {
     using P = TcPlan<K, PREC>;
     constexpr int KG = P::kKG;
     constexpr int RPQ = P::kM2 / 4;                // GEMM 2 rows per TMEM lane quadrant
@@ -793,6 +794,9 @@ __global__ void __launch_bounds__(kTcThreads, TcPlan<K, PREC>::kCtas)
                 const bool cut = s2 == 0.f && cz < 0.f;    // cut locus: undefined chart
                 const float g = cut ? 1.f : g_of_cos(cz, tc::rsqrt_approx(s2));
                 float l = q[3] + g * (q[4] + g * q[5]);
+                // solid-angle density p^t / sinc |nu| (Sec. 3.1 Eq. solidangle-pdf):
+                // + log2(theta / sin theta); the per-sample maximum below is exact
+                if (solid) l += tc::lg2_approx(g);
                 if (cut) l = -INFINITY;
                 lk[j] = l;
                 gk[j] = g;
@@ -929,24 +933,26 @@ cudaError_t launch_tc_prepare(cudaStream_t s, int K, int64_t R, const sdmm_state
 template <int K, int PREC, bool EU>
 static cudaError_t launch_tc_estep_t(cudaStream_t s, int grid, WsHeader* ws, const int32_t* cr,
                                      const int64_t* units, const float* ctab, const float* xref,
-                                     float* partial, int ps, int write_ll) {
+                                     float* partial, int ps, int write_ll, int solid) {
     const int bytes = TcPlan<K, PREC>::kBytes;
     cudaError_t e =
         cudaFuncSetAttribute(k_tc_estep<K, PREC, EU>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
-    k_tc_estep<K, PREC, EU><<<grid, kTcThreads, bytes, s>>>(ws, cr, units, ctab, xref, partial, ps, write_ll);
+    k_tc_estep<K, PREC, EU><<<grid, kTcThreads, bytes, s>>>(ws, cr, units, ctab, xref, partial, ps, write_ll,
+                                                            solid);
     return cudaGetLastError();
 }
 
 cudaError_t launch_tc_estep(cudaStream_t s, int K, int prec, int grid, WsHeader* ws, const int32_t* cr,
                             const int64_t* units, const float* ctab, const float* xref, float* partial,
-                            int ps, int write_ll, int euclid) {
+                            int ps, int write_ll, int euclid, int solid) {
 #define SDMM_TC_CASE(KK, PP) \
     if (!euclid && K == KK && prec == PP) \
-        return launch_tc_estep_t<KK, PP, false>(s, grid, ws, cr, units, ctab, xref, partial, ps, write_ll);
+        return launch_tc_estep_t<KK, PP, false>(s, grid, ws, cr, units, ctab, xref, partial, ps, write_ll, \
+                                                solid);
 #define SDMM_TC_CASE_EU(KK, PP) \
     if (euclid && K == KK && prec == PP) \
-        return launch_tc_estep_t<KK, PP, true>(s, grid, ws, cr, units, ctab, xref, partial, ps, write_ll);
+        return launch_tc_estep_t<KK, PP, true>(s, grid, ws, cr, units, ctab, xref, partial, ps, write_ll, 0);
     SDMM_TC_CASE(16, SDMM_PREC_TC_3XBF16) SDMM_TC_CASE(16, SDMM_PREC_TC_TF32)
     SDMM_TC_CASE(16, SDMM_PREC_TC_3XTF32) SDMM_TC_CASE(32, SDMM_PREC_TC_3XBF16)
     SDMM_TC_CASE(32, SDMM_PREC_TC_TF32) SDMM_TC_CASE(32, SDMM_PREC_TC_3XTF32)

@@ -46,7 +46,7 @@ def block_err(g, o, ok=None):
     return float(e.max()) if e.size else 0.0
 
 
-def assert_params_close(g: orc.State, o: orc.State, regions=None, rtol=PARAM_RTOL):
+def assert_params_close(g: orc.State, o: orc.State, regions=None, rtol=PARAM_RTOL, L_rtol=None):
     ok = (o.status == 0)
     if regions is not None:
         ok = ok & np.isin(np.arange(o.R), regions)
@@ -60,7 +60,7 @@ def assert_params_close(g: orc.State, o: orc.State, regions=None, rtol=PARAM_RTO
         assert np.abs(g.mu_x[r] - o.mu_x[r]).max() < rtol * span, ("mu_x", r)
     assert np.abs(g.mu_w - o.mu_w)[ok].max(initial=0.0) < rtol, "mu_w"
     e = block_err(g.L[ok], o.L[ok])
-    assert e < rtol, ("L", e)
+    assert e < (rtol if L_rtol is None else L_rtol), ("L", e)
 
 
 def oracle_init(seed, b, K, cfg_over=None):
