@@ -524,7 +524,8 @@ static cudaError_t launch_query_op(int KP, cudaStream_t s, int grid, const float
 //   k_qbin_keys     region of every query (array or grid; out of range: bin R)
 //                   and the per-bin counts (warp-aggregated atomics)
 //   k_qbin_scan     exclusive prefix sum of the R + 1 counts, each rounded up
-//                   to a multiple of 32 (one CTA), so that every bin starts
+//                   to a multiple of 32 (one CTA, 8 counts per thread and
+//                   round), so that every bin starts
 //                   at a multiple of 32 and no warp of the sampling kernel
 //                   spans two regions
 //   k_qbin_scatter  each query's position (slot) in its bin (warp-aggregated
@@ -566,15 +567,24 @@ __global__ void __launch_bounds__(256) k_qbin_keys(int64_t Q, int64_t R, const f
 }
 
 __global__ void __launch_bounds__(1024) k_qbin_scan(int64_t n, int32_t* __restrict__ v) {
+    // each thread takes 8 consecutive counts per round (8,192 per round, so
+    // 65,537 bins in nine rounds of one block-wide scan)
+    constexpr int PER = 8;
     __shared__ int32_t s_warp[32];
     __shared__ int32_t s_carry;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) s_carry = 0;
     __syncthreads();
-    for (int64_t base = 0; base < n; base += 1024) {
-        const int64_t e = base + tid;
-        const int32_t c = e < n ? (v[e] + 31) & ~31 : 0;   // bin sizes padded to whole warps
-        int32_t x = c;
+    for (int64_t base = 0; base < n; base += 1024 * PER) {
+        const int64_t e0 = base + (int64_t)tid * PER;
+        int32_t c[PER];
+        int32_t x = 0;
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            c[q] = e0 + q < n ? (v[e0 + q] + 31) & ~31 : 0;   // bin sizes padded to whole warps
+            x += c[q];
+        }
+        const int32_t own = x;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
             const int32_t u = __shfl_up_sync(0xffffffffu, x, d);
@@ -593,7 +603,12 @@ __global__ void __launch_bounds__(1024) k_qbin_scan(int64_t n, int32_t* __restri
         }
         __syncthreads();
         const int32_t incl = x + (warp > 0 ? s_warp[warp - 1] : 0);
-        if (e < n) v[e] = s_carry + incl - c;
+        int32_t run = s_carry + incl - own;                   // exclusive prefix of this thread's first count
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            if (e0 + q < n) v[e0 + q] = run;
+            run += c[q];
+        }
         __syncthreads();
         if (tid == 1023) s_carry += incl;
         __syncthreads();
