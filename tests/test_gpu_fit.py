@@ -121,6 +121,39 @@ def test_prior_scale_array_and_region_statuses():
     assert_params_close(g, ost)
 
 
+@pytest.mark.parametrize("K", [8, 16])
+def test_two_regions_per_warp_mstep_with_odd_count_and_statuses(K):
+    """Enough regions for the one-warp M-step that updates two regions per
+    warp (K <= 16): an odd count (the last warp holds one region) and, in
+    both halves of the pairs, a skipped region, a zero-weight region and a
+    non-finite one; two steps, every region against the oracle."""
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    R = 3 * nsm + 5 + (3 * nsm + 5 + 1) % 2          # above 3 per SM, odd
+    rng = np.random.default_rng(41 + K)
+    counts = rng.integers(60, 1500, size=R)
+    counts[[2, 7]] = 8                                  # skipped (< 16 samples)
+    b = _small_batch(41 + K, K, counts)
+    s = b.samples.copy()
+    o = b.offsets
+    for r in (4, 9):
+        s[6, o[r]:o[r + 1]] = 0.0                       # zero weight
+    s[6, o[R - 1] + 2] = np.nan                         # non-finite, in the lone last region
+    s[6, o[12] + 1] = np.nan
+    ost = oracle_init(41 + K, b, K)                     # initialised on the clean batch
+    bb = syn.Batch(s, o, b.extent, b.truth)
+    gcfg = api.config(K)
+    st = gpu_state(ost, gcfg)
+    orc.fit_regions(orc.config(K), o, s, 2, ost)
+    api.fit_regions(gcfg, dev_batch(bb), 2, st, api.workspace(gcfg, R, s.shape[1]))
+    g = host(st)
+    assert list(ost.status[[2, 7, 4, 9, 12, R - 1]]) == [1, 1, 4, 4, 3, 3]
+    assert list(g.status) == list(ost.status)
+    assert_params_close(g, ost)
+    ok = ost.status == 0
+    assert np.array_equal(g.n_seen, ost.n_seen) and np.array_equal(g.step_j, ost.step_j)
+    assert np.allclose(g.Wbar[ok], ost.Wbar[ok], rtol=1e-5)
+
+
 def test_bad_offsets_flagged():
     K = 4
     b = _small_batch(32, K, [100, 100, 100])
