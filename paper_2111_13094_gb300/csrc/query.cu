@@ -63,11 +63,16 @@ __global__ void __launch_bounds__(kQWarps * 32, kQCtas)
     constexpr float kL2e = 1.44269504088896341f;
     constexpr int Q4 = kQ / 4;                                 // float4 per record
     __shared__ float4 s_rec[kQWarps][KM * Q4];                 // per warp: one region's records
-    __shared__ float4 s_cm[KM][kQWarps * 32];                  // per thread: (w'_k, m_k, -) per component
+    // per thread and component: the weight w'_k and the conditional mean m_k,
+    // in separate arrays so that a warp's 32 weights are one conflict-free
+    // wavefront (interleaved with the means they were four)
+    __shared__ float s_cw[KM][kQWarps * 32];
+    __shared__ float2 s_cmu[KM][kQWarps * 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const float4* __restrict__ q4 = reinterpret_cast<const float4*>(qtab);
     const int n4 = K * Q4;                                     // float4 of one region's records
-    float4* const cm = &s_cm[0][threadIdx.x];                  // component k at cm[k * kQWarps * 32]
+    float* const cw = &s_cw[0][threadIdx.x];                   // component k at cw[k * CS]
+    float2* const cmu = &s_cmu[0][threadIdx.x];                // and cmu[k * CS]
     constexpr int CS = kQWarps * 32;
     int staged = -1;
     const int64_t wstride = (int64_t)gridDim.x * kQWarps * 32;
@@ -163,15 +168,16 @@ __global__ void __launch_bounds__(kQWarps * 32, kQCtas)
                 const float z1 = f3.y * e0 + f3.z * e1;
                 const float z2 = f3.w * e0 + f4.x * e1 + f4.y * e2;
                 const float lw = fmaf(-0.5f, z0 * z0 + z1 * z1 + z2 * z2, f7.z) * kL2e;
-                cm[k * CS] = make_float4(lw, f4.z * z0 + f4.w * z1 + f5.x * z2, f5.y * z0 + f5.z * z1 + f5.w * z2, 0.f);
+                cw[k * CS] = lw;
+                cmu[k * CS] = make_float2(f4.z * z0 + f4.w * z1 + f5.x * z2, f5.y * z0 + f5.z * z1 + f5.w * z2);
                 mx = fmaxf(mx, lw);
             }
             // normalisation: w'_k = 2^(lw - max), se = sum w'_k
             float se = 0.f;
 #pragma unroll 4
             for (int k = 0; k < K; ++k) {
-                const float w = mx > -INFINITY ? tc::ex2_approx(cm[k * CS].x - mx) : 0.f;
-                cm[k * CS].x = w;
+                const float w = mx > -INFINITY ? tc::ex2_approx(cw[k * CS] - mx) : 0.f;
+                cw[k * CS] = w;
                 se += w;
             }
 
@@ -198,13 +204,13 @@ __global__ void __launch_bounds__(kQWarps * 32, kQCtas)
                 int kk = -1, last = -1;
 #pragma unroll 4
                 for (int k = 0; k < K; ++k) {
-                    const float w = cm[k * CS].x;
+                    const float w = cw[k * CS];
                     cum += w;
                     last = w > 0.f ? k : last;
                     kk = (kk < 0 && thr < cum) ? k : kk;
                 }
                 if (kk < 0) kk = last >= 0 ? last : 0;
-                const float4 sel = cm[kk * CS];
+                const float2 sel = cmu[kk * CS];
                 // Gaussian draw in the chart (step ii), exp map (step iii)
                 const float4* rk = rec + kk * Q4;
                 const float4 t4 = rk[0];   // mu_x, t.x
@@ -215,8 +221,8 @@ __global__ void __launch_bounds__(kQWarps * 32, kQCtas)
                 float sn, cs;
                 sincospif(2.f * u2, &sn, &cs);
                 const float g0 = rad * cs, g1 = rad * sn;
-                const float n0 = sel.y + dd.x * g0;
-                const float n1 = sel.z + dd.y * g0 + dd.z * g1;
+                const float n0 = sel.x + dd.x * g0;
+                const float n1 = sel.y + dd.y * g0 + dd.z * g1;
                 const float rn = sqrtf(n0 * n0 + n1 * n1);
                 valid = (rn < kPiF) && ok && last >= 0;
                 float sr, cr;
@@ -239,7 +245,8 @@ __global__ void __launch_bounds__(kQWarps * 32, kQCtas)
             for (int k = 0; k < K; ++k) {
                 const float4* rk = rec + k * Q4;
                 const float4 a = rk[0], b = rk[1], c = rk[2], f6 = rk[6], f7 = rk[7];
-                const float4 wm = cm[k * CS];
+                const float wk = cw[k * CS];
+                const float2 mk = cmu[k * CS];
                 // t = (a.w, b.x, b.y), b = (b.z, b.w, c.x), mu = (c.y, c.z, c.w)
                 const float u = a.w * w0 + b.x * w1 + b.y * w2;
                 const float v = b.z * w0 + b.w * w1 + c.x * w2;
@@ -248,11 +255,11 @@ __global__ void __launch_bounds__(kQWarps * 32, kQCtas)
                 // antipode of the mean (and within 1e-19 of it): outside the chart
                 const bool cut = !(s2v >= 1.17549435e-38f) && cz < 0.f;
                 const float gg = cut ? 1.f : g_of_cos(cz, tc::rsqrt_approx(s2v));
-                const float d0 = gg * u - wm.y, d1 = gg * v - wm.z;
+                const float d0 = gg * u - mk.x, d1 = gg * v - mk.y;
                 // D^-1 (f6.w, f7.x, f7.y), cn at 31
                 const float y0 = f6.w * d0;
                 const float y1 = f7.x * d0 + f7.y * d1;
-                const float pk_ = wm.x * tc::ex2_approx(fmaf(-0.5f, y0 * y0 + y1 * y1, f7.w) * kL2e) * gg;
+                const float pk_ = wk * tc::ex2_approx(fmaf(-0.5f, y0 * y0 + y1 * y1, f7.w) * kL2e) * gg;
                 p += cut ? 0.f : pk_;
             }
             p = se > 0.f ? __fdividef(p, se) : 0.f;
