@@ -35,14 +35,19 @@ __host__ __device__ inline int partial_stride(int K) { return ((K * kStat + 2) +
 //   [28..29] in-chart direction offset (0 except for objective evaluation)
 //   [32..34] FP32 remainder of mu_x: x - mu = (x - hi) - lo keeps the
 //            spatial difference accurate for narrow spatial components
-// Query record (SDMM_QTAB_FLOATS = 36 floats):
-//   [0..2] mu_x (FP32)  [3..5] t  [6..8] b  [9..11] mu_w  [12..17] A^-1 packed
-//   [18..23] C^T (2x3 row-major)  [24..26] D (d00, d10, d11)
-//   [27..29] D^-1  [30] cx = log pi - log det A - (3/2) log 2 pi
-//   [31] cn = -log det D - log 2 pi  [32..34] FP32 remainder of mu_x
+// Query record (SDMM_QTAB_FLOATS = 36 floats), in two groups of whole float4:
+// what conditioning on the position reads (float4 0-4), then what the pdf in
+// the component's chart and the draw read (float4 5-8):
+//   [0..2] mu_x (FP32)  [3] cx = log pi - log det A - (3/2) log 2 pi
+//   [4..6] FP32 remainder of mu_x  [7..12] A^-1 packed  [13..18] C^T (2x3
+//   row-major)  [19] 0  [20..22] t  [23..25] b  [26..28] mu_w
+//   [29..31] D^-1  [32] cn = -log det D - log 2 pi  [33..35] D (d00, d10, d11)
 // with L = [[A, 0], [C^T, D]] in (x, nu) order.
 constexpr int kE = SDMM_ETAB_FLOATS;
 constexpr int kQ = SDMM_QTAB_FLOATS;
+namespace qrec {
+constexpr int MUX = 0, CX = 3, REM = 4, AINV = 7, CT = 13, T = 20, B = 23, MUW = 26, DINV = 29, CN = 32, D = 33;
+}
 
 // R_mu with rows (t, b, mu): branchless orthonormal basis of Duff et al.,
 // "Building an Orthonormal Basis, Revisited", JCGT 6(1), 2017.
@@ -224,14 +229,14 @@ __device__ inline void write_records(double pi, const double mux[3], const doubl
     const double ldA = log(L[pk(0, 0)] * L[pk(1, 1)] * L[pk(2, 2)]);
     const double ldD = log(L[pk(3, 3)] * L[pk(4, 4)]);
     for (int c = 0; c < 3; ++c) {
-        er[0 + c] = qr[0 + c] = (float)mux[c];
-        er[3 + c] = qr[3 + c] = (float)t[c];
-        er[6 + c] = qr[6 + c] = (float)b[c];
-        er[9 + c] = qr[9 + c] = (float)muw[c];
+        er[0 + c] = qr[qrec::MUX + c] = (float)mux[c];
+        er[3 + c] = qr[qrec::T + c] = (float)t[c];
+        er[6 + c] = qr[qrec::B + c] = (float)b[c];
+        er[9 + c] = qr[qrec::MUW + c] = (float)muw[c];
     }
     for (int p = 0; p < 15; ++p) er[12 + p] = (float)Li[p];
     er[27] = (float)(lpi - ldA - ldD - 2.5 * kLog2Pi);
-    er[28] = er[29] = er[30] = er[31] = er[35] = qr[35] = 0.f;
+    er[28] = er[29] = er[30] = er[31] = er[35] = qr[19] = 0.f;
     double me[3] = {mux[0], mux[1], mux[2]};
     if (delta != nullptr) {
         for (int c = 0; c < 3; ++c) me[c] += delta[c];
@@ -245,21 +250,21 @@ __device__ inline void write_records(double pi, const double mux[3], const doubl
     for (int c = 0; c < 3; ++c) {
         er[c] = (float)me[c];
         er[32 + c] = (float)(me[c] - (double)er[c]);
-        qr[32 + c] = (float)(mux[c] - (double)qr[c]);
+        qr[qrec::REM + c] = (float)(mux[c] - (double)qr[qrec::MUX + c]);
     }
-    for (int p = 0; p < 6; ++p) qr[12 + p] = (float)Li[p];
+    for (int p = 0; p < 6; ++p) qr[qrec::AINV + p] = (float)Li[p];
     for (int c = 0; c < 3; ++c) {
-        qr[18 + c] = (float)L[pk(3, c)];
-        qr[21 + c] = (float)L[pk(4, c)];
+        qr[qrec::CT + c] = (float)L[pk(3, c)];
+        qr[qrec::CT + 3 + c] = (float)L[pk(4, c)];
     }
-    qr[24] = (float)L[pk(3, 3)];
-    qr[25] = (float)L[pk(4, 3)];
-    qr[26] = (float)L[pk(4, 4)];
-    qr[27] = (float)Li[pk(3, 3)];
-    qr[28] = (float)Li[pk(4, 3)];
-    qr[29] = (float)Li[pk(4, 4)];
-    qr[30] = (float)(lpi - ldA - 1.5 * kLog2Pi);
-    qr[31] = (float)(-ldD - kLog2Pi);
+    qr[qrec::D + 0] = (float)L[pk(3, 3)];
+    qr[qrec::D + 1] = (float)L[pk(4, 3)];
+    qr[qrec::D + 2] = (float)L[pk(4, 4)];
+    qr[qrec::DINV + 0] = (float)Li[pk(3, 3)];
+    qr[qrec::DINV + 1] = (float)Li[pk(4, 3)];
+    qr[qrec::DINV + 2] = (float)Li[pk(4, 4)];
+    qr[qrec::CX] = (float)(lpi - ldA - 1.5 * kLog2Pi);
+    qr[qrec::CN] = (float)(-ldD - kLog2Pi);
 }
 
 // Batch descriptor written into the workspace before each fit step sequence.

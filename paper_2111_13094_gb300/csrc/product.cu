@@ -49,9 +49,9 @@ __device__ inline Pair make_pair(const float* P, float cm0, float cm1, float lcp
     o.p10 = o.ln = 0.f;
     o.lw = -INFINITY;
     // the lobe's mean in the mu_k chart
-    const float u = P[3] * mu2[0] + P[4] * mu2[1] + P[5] * mu2[2];
-    const float v = P[6] * mu2[0] + P[7] * mu2[1] + P[8] * mu2[2];
-    const float c = P[9] * mu2[0] + P[10] * mu2[1] + P[11] * mu2[2];
+    const float u = P[20] * mu2[0] + P[21] * mu2[1] + P[22] * mu2[2];
+    const float v = P[23] * mu2[0] + P[24] * mu2[1] + P[25] * mu2[2];
+    const float c = P[26] * mu2[0] + P[27] * mu2[1] + P[28] * mu2[2];
     const float s2 = u * u + v * v;
     const float rs = rsqrtf(s2);
     const float s = s2 > 0.f ? s2 * rs : 0.f;
@@ -68,9 +68,9 @@ __device__ inline Pair make_pair(const float* P, float cm0, float cm1, float lcp
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
         const float e0 = q == 0 ? t2[0] : b2[0], e1 = q == 0 ? t2[1] : b2[1], e2 = q == 0 ? t2[2] : b2[2];
-        const float ta = P[3] * e0 + P[4] * e1 + P[5] * e2;
-        const float tb = P[6] * e0 + P[7] * e1 + P[8] * e2;
-        const float tc = P[9] * e0 + P[10] * e1 + P[11] * e2;
+        const float ta = P[20] * e0 + P[21] * e1 + P[22] * e2;
+        const float tb = P[23] * e0 + P[24] * e1 + P[25] * e2;
+        const float tc = P[26] * e0 + P[27] * e1 + P[28] * e2;
         J[0][q] = g * ta + u * tc * h;
         J[1][q] = g * tb + v * tc * h;
     }
@@ -78,7 +78,7 @@ __device__ inline Pair make_pair(const float* P, float cm0, float cm1, float lcp
     const float M00 = J[0][0] * L2[0] + J[0][1] * L2[1], M01 = J[0][1] * L2[2];
     const float M10 = J[1][0] * L2[0] + J[1][1] * L2[1], M11 = J[1][1] * L2[2];
     const float b00 = M00 * M00 + M01 * M01, b01 = M00 * M10 + M01 * M11, b11 = M10 * M10 + M11 * M11;
-    const float a00 = P[24] * P[24], a01 = P[24] * P[25], a11 = P[25] * P[25] + P[26] * P[26];
+    const float a00 = P[33] * P[33], a01 = P[33] * P[34], a11 = P[34] * P[34] + P[35] * P[35];
     // S = S1 + S2' and its inverse
     const float S00 = a00 + b00, S01 = a01 + b01, S11 = a11 + b11;
     const float det = S00 * S11 - S01 * S01;
@@ -194,19 +194,19 @@ __global__ void __launch_bounds__(256, 3)
                 } else {
 #pragma unroll
                     for (int q = 0; q < kQ; ++q) P[q] = 0.f;
-                    P[11] = 1.f;
-                    P[24] = P[26] = P[27] = P[29] = 1.f;
-                    P[30] = -INFINITY;
+                    P[28] = 1.f;
+                    P[33] = P[35] = P[29] = P[31] = 1.f;
+                    P[3] = -INFINITY;
                 }
             }
             // ---- conditioning on position (as in k_query)
-            const float e0 = (qx0 - P[0]) - P[32], e1 = (qx1 - P[1]) - P[33], e2 = (qx2 - P[2]) - P[34];
-            const float z0 = P[12] * e0;
-            const float z1 = P[13] * e0 + P[14] * e1;
-            const float z2 = P[15] * e0 + P[16] * e1 + P[17] * e2;
-            const float lw = P[30] - 0.5f * (z0 * z0 + z1 * z1 + z2 * z2);
-            const float m0 = P[18] * z0 + P[19] * z1 + P[20] * z2;
-            const float m1 = P[21] * z0 + P[22] * z1 + P[23] * z2;
+            const float e0 = (qx0 - P[0]) - P[4], e1 = (qx1 - P[1]) - P[5], e2 = (qx2 - P[2]) - P[6];
+            const float z0 = P[7] * e0;
+            const float z1 = P[8] * e0 + P[9] * e1;
+            const float z2 = P[10] * e0 + P[11] * e1 + P[12] * e2;
+            const float lw = P[3] - 0.5f * (z0 * z0 + z1 * z1 + z2 * z2);
+            const float m0 = P[13] * z0 + P[14] * z1 + P[15] * z2;
+            const float m1 = P[16] * z0 + P[17] * z1 + P[18] * z2;
             float mx = lw;
 #pragma unroll
             for (int o = KP / 2; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(FULL, mx, o));
@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(256, 3)
                     }
                     pr[q] = make_pair(P, m0, m1, lcpi, __ldg(bw + qb * J + jl), mu2, L2);
                 } else {
-                    pr[q] = make_pair(P, m0, m1, -INFINITY, 0.f, P + 9, P + 24);   // no pair
+                    pr[q] = make_pair(P, m0, m1, -INFINITY, 0.f, P + qrec::MUW, P + qrec::D);   // no pair
                 }
             }
             // ---- normalise the pair weights over the query's lanes
@@ -299,9 +299,9 @@ __global__ void __launch_bounds__(256, 3)
                     sincosf(rn, &sr, &cr);
                     const float sc = rn < 1e-3f ? 1.f - rn * rn * (1.f / 6.f) : __fdividef(sr, rn);
                     const float c0 = n0 * sc, c1 = n1 * sc;
-                    s0 = c0 * P[3] + c1 * P[6] + cr * P[9];
-                    s1 = c0 * P[4] + c1 * P[7] + cr * P[10];
-                    s2 = c0 * P[5] + c1 * P[8] + cr * P[11];
+                    s0 = c0 * P[20] + c1 * P[23] + cr * P[26];
+                    s1 = c0 * P[21] + c1 * P[24] + cr * P[27];
+                    s2 = c0 * P[22] + c1 * P[25] + cr * P[28];
                 }
                 const int from = base_lane + kk;
                 w0 = __shfl_sync(FULL, s0, from);
@@ -310,9 +310,9 @@ __global__ void __launch_bounds__(256, 3)
                 valid = __shfl_sync(FULL, vv, from) > 0.5f && ok && pos != 0u;
             }
             // ---- pdf of the product mixture at w: every pair's chart density / sinc
-            const float u = P[3] * w0 + P[4] * wv1 + P[5] * wv2;
-            const float v = P[6] * w0 + P[7] * wv1 + P[8] * wv2;
-            const float cz = P[9] * w0 + P[10] * wv1 + P[11] * wv2;
+            const float u = P[20] * w0 + P[21] * wv1 + P[22] * wv2;
+            const float v = P[23] * w0 + P[24] * wv1 + P[25] * wv2;
+            const float cz = P[26] * w0 + P[27] * wv1 + P[28] * wv2;
             const float s2v = u * u + v * v;
             const bool cut = s2v == 0.f && cz < 0.f;          // antipode: outside the chart
             const float gg = cut ? 1.f : g_of_cos(cz, rsqrtf(s2v));

@@ -160,16 +160,17 @@ __global__ void __launch_bounds__(kQWarps * 32, kQCtas)
             float mx = -INFINITY;
 #pragma unroll 4
             for (int k = 0; k < K; ++k) {
+                // the record's conditioning group, float4 0-4: (mu_x, cx), (remainder,
+                // A^-1 0), A^-1 1..4, (A^-1 5, C^T row 0), (C^T row 1, 0)
                 const float4* rk = rec + k * Q4;
-                const float4 a = rk[0], f3 = rk[3], f4 = rk[4], f5 = rk[5], f7 = rk[7], f8 = rk[8];
-                const float e0 = (x0 - a.x) - f8.x, e1 = (x1 - a.y) - f8.y, e2 = (x2 - a.z) - f8.z;
-                // A^-1 packed at 12..17, C^T rows at 18..20 and 21..23, cx at 30
-                const float z0 = f3.x * e0;
-                const float z1 = f3.y * e0 + f3.z * e1;
-                const float z2 = f3.w * e0 + f4.x * e1 + f4.y * e2;
-                const float lw = fmaf(-0.5f, z0 * z0 + z1 * z1 + z2 * z2, f7.z) * kL2e;
+                const float4 g0 = rk[0], g1 = rk[1], g2 = rk[2], g3 = rk[3], g4 = rk[4];
+                const float e0 = (x0 - g0.x) - g1.x, e1 = (x1 - g0.y) - g1.y, e2 = (x2 - g0.z) - g1.z;
+                const float z0 = g1.w * e0;
+                const float z1 = g2.x * e0 + g2.y * e1;
+                const float z2 = g2.z * e0 + g2.w * e1 + g3.x * e2;
+                const float lw = fmaf(-0.5f, z0 * z0 + z1 * z1 + z2 * z2, g0.w) * kL2e;
                 cw[k * CS] = lw;
-                cmu[k * CS] = make_float2(f4.z * z0 + f4.w * z1 + f5.x * z2, f5.y * z0 + f5.z * z1 + f5.w * z2);
+                cmu[k * CS] = make_float2(g3.y * z0 + g3.z * z1 + g3.w * z2, g4.x * z0 + g4.y * z1 + g4.z * z2);
                 mx = fmaxf(mx, lw);
             }
             // normalisation: w'_k = 2^(lw - max), se = sum w'_k
@@ -212,26 +213,25 @@ __global__ void __launch_bounds__(kQWarps * 32, kQCtas)
                 if (kk < 0) kk = last >= 0 ? last : 0;
                 const float2 sel = cmu[kk * CS];
                 // Gaussian draw in the chart (step ii), exp map (step iii)
+                // the chart group, float4 5-8: (t, b.x), (b.y, b.z, mu_w.x, mu_w.y),
+                // (mu_w.z, D^-1), (cn, D)
                 const float4* rk = rec + kk * Q4;
-                const float4 t4 = rk[0];   // mu_x, t.x
-                const float4 t5 = rk[1];   // t.y t.z b.x b.y
-                const float4 t6 = rk[2];   // b.z mu_w
-                const float4 dd = rk[6];   // D (d00 d10 d11), D^-1 00
+                const float4 h5 = rk[5], h6 = rk[6], h7 = rk[7], h8 = rk[8];
                 const float rad = sqrtf(-2.f * logf(1.f - u1));
                 float sn, cs;
                 sincospif(2.f * u2, &sn, &cs);
                 const float g0 = rad * cs, g1 = rad * sn;
-                const float n0 = sel.x + dd.x * g0;
-                const float n1 = sel.y + dd.y * g0 + dd.z * g1;
+                const float n0 = sel.x + h8.y * g0;
+                const float n1 = sel.y + h8.z * g0 + h8.w * g1;
                 const float rn = sqrtf(n0 * n0 + n1 * n1);
                 valid = (rn < kPiF) && ok && last >= 0;
                 float sr, cr;
                 sincosf(rn, &sr, &cr);
                 const float sc = rn < 1e-3f ? 1.f - rn * rn * (1.f / 6.f) : __fdividef(sr, rn);
                 const float c0 = n0 * sc, c1 = n1 * sc;
-                w0 = c0 * t4.w + c1 * t5.z + cr * t6.y;
-                w1 = c0 * t5.x + c1 * t5.w + cr * t6.z;
-                w2 = c0 * t5.y + c1 * t6.x + cr * t6.w;
+                w0 = c0 * h5.x + c1 * h5.w + cr * h6.z;
+                w1 = c0 * h5.y + c1 * h6.x + cr * h6.w;
+                w2 = c0 * h5.z + c1 * h6.y + cr * h7.x;
             } else {
                 w0 = dir_in[3 * i];
                 w1 = dir_in[3 * i + 1];
@@ -244,22 +244,22 @@ __global__ void __launch_bounds__(kQWarps * 32, kQCtas)
 #pragma unroll 4
             for (int k = 0; k < K; ++k) {
                 const float4* rk = rec + k * Q4;
-                const float4 a = rk[0], b = rk[1], c = rk[2], f6 = rk[6], f7 = rk[7];
+                const float4 h5 = rk[5], h6 = rk[6], h7 = rk[7], h8 = rk[8];   // the chart group
                 const float wk = cw[k * CS];
                 const float2 mk = cmu[k * CS];
-                // t = (a.w, b.x, b.y), b = (b.z, b.w, c.x), mu = (c.y, c.z, c.w)
-                const float u = a.w * w0 + b.x * w1 + b.y * w2;
-                const float v = b.z * w0 + b.w * w1 + c.x * w2;
-                const float cz = c.y * w0 + c.z * w1 + c.w * w2;
+                // t = (h5.x, h5.y, h5.z), b = (h5.w, h6.x, h6.y), mu = (h6.z, h6.w, h7.x)
+                const float u = h5.x * w0 + h5.y * w1 + h5.z * w2;
+                const float v = h5.w * w0 + h6.x * w1 + h6.y * w2;
+                const float cz = h6.z * w0 + h6.w * w1 + h7.x * w2;
                 const float s2v = u * u + v * v;
                 // antipode of the mean (and within 1e-19 of it): outside the chart
                 const bool cut = !(s2v >= 1.17549435e-38f) && cz < 0.f;
                 const float gg = cut ? 1.f : g_of_cos(cz, tc::rsqrt_approx(s2v));
                 const float d0 = gg * u - mk.x, d1 = gg * v - mk.y;
-                // D^-1 (f6.w, f7.x, f7.y), cn at 31
-                const float y0 = f6.w * d0;
-                const float y1 = f7.x * d0 + f7.y * d1;
-                const float pk_ = wk * tc::ex2_approx(fmaf(-0.5f, y0 * y0 + y1 * y1, f7.w) * kL2e) * gg;
+                // D^-1 (h7.y, h7.z, h7.w), cn = h8.x
+                const float y0 = h7.y * d0;
+                const float y1 = h7.z * d0 + h7.w * d1;
+                const float pk_ = wk * tc::ex2_approx(fmaf(-0.5f, y0 * y0 + y1 * y1, h8.x) * kL2e) * gg;
                 p += cut ? 0.f : pk_;
             }
             p = se > 0.f ? __fdividef(p, se) : 0.f;
@@ -329,20 +329,20 @@ __device__ __forceinline__ void warp_by_components(const float* __restrict__ qta
             } else {
 #pragma unroll
                 for (int q = 0; q < kQ; ++q) P[q] = 0.f;
-                P[11] = 1.f;
-                P[24] = P[26] = P[27] = P[29] = 1.f;
-                P[30] = -INFINITY;
+                P[28] = 1.f;
+                P[33] = P[35] = P[29] = P[31] = 1.f;
+                P[3] = -INFINITY;
             }
         }
         // ---- conditioning on position: z = A^-1 (x - mu^x)
-        const float e0 = (qx0 - P[0]) - P[32], e1 = (qx1 - P[1]) - P[33],
-                    e2 = (qx2 - P[2]) - P[34];
-        const float z0 = P[12] * e0;
-        const float z1 = P[13] * e0 + P[14] * e1;
-        const float z2 = P[15] * e0 + P[16] * e1 + P[17] * e2;
-        const float lw = P[30] - 0.5f * (z0 * z0 + z1 * z1 + z2 * z2);
-        const float m0 = P[18] * z0 + P[19] * z1 + P[20] * z2;   // C^T z
-        const float m1 = P[21] * z0 + P[22] * z1 + P[23] * z2;
+        const float e0 = (qx0 - P[0]) - P[4], e1 = (qx1 - P[1]) - P[5],
+                    e2 = (qx2 - P[2]) - P[6];
+        const float z0 = P[7] * e0;
+        const float z1 = P[8] * e0 + P[9] * e1;
+        const float z2 = P[10] * e0 + P[11] * e1 + P[12] * e2;
+        const float lw = P[3] - 0.5f * (z0 * z0 + z1 * z1 + z2 * z2);
+        const float m0 = P[13] * z0 + P[14] * z1 + P[15] * z2;   // C^T z
+        const float m1 = P[16] * z0 + P[17] * z1 + P[18] * z2;
         // normalise pi'_k over the KP component lanes (log-sum-exp)
         float mx = lw;
 #pragma unroll
@@ -360,9 +360,9 @@ __device__ __forceinline__ void warp_by_components(const float* __restrict__ qta
                 cond_pi[o] = ok ? cpi : 0.f;
                 cond_m[2 * o] = m0;
                 cond_m[2 * o + 1] = m1;
-                cond_L[3 * o] = P[24];
-                cond_L[3 * o + 1] = P[25];
-                cond_L[3 * o + 2] = P[26];
+                cond_L[3 * o] = P[33];
+                cond_L[3 * o + 1] = P[34];
+                cond_L[3 * o + 2] = P[35];
             }
             continue;
         }
@@ -392,17 +392,17 @@ __device__ __forceinline__ void warp_by_components(const float* __restrict__ qta
                 float sn, cs;
                 sincospif(2.f * b2, &sn, &cs);
                 const float g0 = rad * cs, g1 = rad * sn;
-                const float n0 = m0 + P[24] * g0;
-                const float n1 = m1 + P[25] * g0 + P[26] * g1;
+                const float n0 = m0 + P[33] * g0;
+                const float n1 = m1 + P[34] * g0 + P[35] * g1;
                 const float rn = sqrtf(n0 * n0 + n1 * n1);
                 vv = rn < kPiF ? 1.f : 0.f;
                 float sr, cr;
                 sincosf(rn, &sr, &cr);
                 const float sc = rn < 1e-3f ? 1.f - rn * rn * (1.f / 6.f) : __fdividef(sr, rn);
                 const float c0 = n0 * sc, c1 = n1 * sc;
-                s0 = c0 * P[3] + c1 * P[6] + cr * P[9];
-                s1 = c0 * P[4] + c1 * P[7] + cr * P[10];
-                s2 = c0 * P[5] + c1 * P[8] + cr * P[11];
+                s0 = c0 * P[20] + c1 * P[23] + cr * P[26];
+                s1 = c0 * P[21] + c1 * P[24] + cr * P[27];
+                s2 = c0 * P[22] + c1 * P[25] + cr * P[28];
             }
             const int from = base_lane + kk;
             w0 = __shfl_sync(FULL, s0, from);
@@ -411,16 +411,16 @@ __device__ __forceinline__ void warp_by_components(const float* __restrict__ qta
             valid = __shfl_sync(FULL, vv, from) > 0.5f && ok && pos != 0u;
         }
         // ---- solid-angle pdf of the conditioned mixture at w (Eq. solidangle-pdf)
-        const float u = P[3] * w0 + P[4] * w1 + P[5] * w2;
-        const float v = P[6] * w0 + P[7] * w1 + P[8] * w2;
-        const float cz = P[9] * w0 + P[10] * w1 + P[11] * w2;
+        const float u = P[20] * w0 + P[21] * w1 + P[22] * w2;
+        const float v = P[23] * w0 + P[24] * w1 + P[25] * w2;
+        const float cz = P[26] * w0 + P[27] * w1 + P[28] * w2;
         const float s2v = u * u + v * v;
         const bool cut = s2v == 0.f && cz < 0.f;          // antipode: outside the chart
         const float gg = cut ? 1.f : g_of_cos(cz, rsqrtf(s2v));   // theta / sin(theta) = 1/sinc
         const float d0 = gg * u - m0, d1 = gg * v - m1;
-        const float y0 = P[27] * d0;
-        const float y1 = P[28] * d0 + P[29] * d1;
-        float pk_ = cpi * __expf(P[31] - 0.5f * (y0 * y0 + y1 * y1)) * gg;
+        const float y0 = P[29] * d0;
+        const float y1 = P[30] * d0 + P[31] * d1;
+        float pk_ = cpi * __expf(P[32] - 0.5f * (y0 * y0 + y1 * y1)) * gg;
         if (cut || k >= K) pk_ = 0.f;
         float p = pk_;
 #pragma unroll
