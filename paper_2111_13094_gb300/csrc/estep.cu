@@ -255,23 +255,34 @@ __global__ void __launch_bounds__(kEW * 32, kECtas)
                 float ya[5], yb[5];
                 const float la = logp2(xa, wa, ya), lb = logp2(xb, wb, yb);
                 float refa = 0.f, refb = 0.f;       // shift on top of the region bound
-                if (SOLID) {
-                    refa = la, refb = lb;
+                if (SOLID) {                         // the two maxima, reduce-scatter as the sums below
+                    const bool up = (k & (KP / 2)) != 0;
+                    float keep = up ? lb : la;
+                    keep = fmaxf(keep, __shfl_xor_sync(FULL, up ? la : lb, KP / 2));
 #pragma unroll
-                    for (int o = KP / 2; o > 0; o >>= 1) {
-                        refa = fmaxf(refa, __shfl_xor_sync(FULL, refa, o));
-                        refb = fmaxf(refb, __shfl_xor_sync(FULL, refb, o));
-                    }
+                    for (int o = KP / 4; o > 0; o >>= 1) keep = fmaxf(keep, __shfl_xor_sync(FULL, keep, o));
+                    const float other = __shfl_xor_sync(FULL, keep, KP / 2);
+                    refa = up ? other : keep;
+                    refb = up ? keep : other;
                     refa = refa == -INFINITY ? 0.f : refa;
                     refb = refb == -INFINITY ? 0.f : refb;
                 }
                 const float ea = tc::ex2_approx(la - refa);
                 const float eb = tc::ex2_approx(lb - refb);
-                float sa = ea, sb = eb;
+                // the two sums by one reduce-scatter: at the first level the lower
+                // half of the sample's lanes keeps sample a, the upper half b; each
+                // half then reduces one value; a last exchange returns both
+                // (five shuffles instead of eight)
+                float sa, sb;
+                {
+                    const bool up = (k & (KP / 2)) != 0;
+                    float keep = up ? eb : ea;
+                    keep += __shfl_xor_sync(FULL, up ? ea : eb, KP / 2);
 #pragma unroll
-                for (int o = KP / 2; o > 0; o >>= 1) {
-                    sa += __shfl_xor_sync(FULL, sa, o);
-                    sb += __shfl_xor_sync(FULL, sb, o);
+                    for (int o = KP / 4; o > 0; o >>= 1) keep += __shfl_xor_sync(FULL, keep, o);
+                    const float other = __shfl_xor_sync(FULL, keep, KP / 2);
+                    sa = up ? other : keep;
+                    sb = up ? keep : other;
                 }
                 // the component-0 lane of each sample slot records the sums
                 // (predicated stores: no branch in the pair loop)
