@@ -284,10 +284,13 @@ __global__ void __launch_bounds__(kEW * 32, kECtas)
                     sa = up ? other : keep;
                     sb = up ? keep : other;
                 }
-                // the component-0 lane of each sample slot records the sums
-                // (predicated stores: no branch in the pair loop)
-                st_shared_pred(k == 0, &s_lse[warp][ja], sa, SOLID ? lmax + refa * kLn2F : lmax);
-                st_shared_pred(k == 0, &s_lse[warp][jb], sb, SOLID ? lmax + refb * kLn2F : lmax);
+                // component lane 0 records sample a's sum, lane KP/2 sample b's (one
+                // predicated store: no branch in the pair loop)
+                {
+                    const bool lo = k == 0;
+                    st_shared_pred(lo || k == KP / 2, &s_lse[warp][lo ? ja : jb], lo ? sa : sb,
+                                   SOLID ? lmax + (lo ? refa : refb) * kLn2F : lmax);
+                }
                 const float ia = tc::rcp_approx(sa), ib = tc::rcp_approx(sb);
                 const float ra = sa >= kSumMin ? xa.w * ea * ia : 0.f;
                 const float rb = sb >= kSumMin ? xb.w * eb * ib : 0.f;
