@@ -71,7 +71,7 @@ BYTES_PER_QUERY = 29
 # capture of a 512-region launch of the same kernel (traffic grows with the
 # samples processed, so a full launch moves this times N); None for kernels
 # without a capture of their current version
-DRAM_BYTES_PER_SAMPLE = {"k_estep<16>": 28.96}
+DRAM_BYTES_PER_SAMPLE = {"k_estep<16>": 29.10}
 PREC = {"fp32": 0, "3xbf16": 1, "tf32": 2, "3xtf32": 3, "6xbf16": 4}
 STATE_FIELDS = ("pi", "mu_x", "mu_w", "L", "S0", "S2", "Wbar", "n_seen", "step_j", "status")
 
