@@ -92,8 +92,16 @@ def _dev(*a):
     return [torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in a]
 
 
+def _sorted(qx, reg):
+    """The queries ordered by region (stable): warps then hold one or two
+    regions and take the thread-per-query path (K <= 16)."""
+    o = np.argsort(reg, kind="stable")
+    return np.ascontiguousarray(qx[o]), np.ascontiguousarray(reg[o])
+
+
+@pytest.mark.parametrize("order", ["given", "sorted"])
 @pytest.mark.parametrize("K,J", [(2, 1), (16, 3), (32, 4)])
-def test_product_sample_matches_oracle(K, J):
+def test_product_sample_matches_oracle(K, J, order):
     dims = (4, 4, 2)
     ost = _mixtures(21, dims, K)
     cfg = api.config(K)
@@ -101,6 +109,8 @@ def test_product_sample_matches_oracle(K, J):
     Q = {2: 4000, 16: 2500, 32: 1500}[K]
     qx = syn.query_points(22, Q)
     reg = syn.grid_region(qx, dims)
+    if order == "sorted":
+        qx, reg = _sorted(qx, reg)
     bw, bmu, bL = syn.bsdf_lobes(23, Q, J)
     u = np.random.default_rng(24).random((Q, 3), dtype=np.float32)
     tq, tr, tw, tm, tl, tu = _dev(qx, reg, bw, bmu, bL, u)
@@ -134,7 +144,8 @@ def test_product_sample_matches_oracle(K, J):
     assert np.all(p[~vv] == 0)
 
 
-def test_product_pdf_entry_matches_oracle():
+@pytest.mark.parametrize("order", ["given", "sorted"])
+def test_product_pdf_entry_matches_oracle(order):
     K, J = 16, 3
     dims = (2, 2, 2)
     ost = _mixtures(25, dims, K)
@@ -143,6 +154,8 @@ def test_product_pdf_entry_matches_oracle():
     Q = 4000
     qx = syn.query_points(26, Q)
     reg = syn.grid_region(qx, dims)
+    if order == "sorted":
+        qx, reg = _sorted(qx, reg)
     bw, bmu, bL = syn.bsdf_lobes(27, Q, J)
     rng = np.random.default_rng(28)
     dirs = rng.normal(size=(Q, 3))
@@ -162,7 +175,8 @@ def test_product_pdf_entry_matches_oracle():
     assert np.abs(p - po).max() < 1e-4 * po.max()
 
 
-def test_product_philox_and_grid_paths_are_exact():
+@pytest.mark.parametrize("order", ["given", "sorted"])
+def test_product_philox_and_grid_paths_are_exact(order):
     K, J = 16, 2
     dims = (4, 4, 4)
     ost = _mixtures(29, dims, K)
@@ -171,6 +185,8 @@ def test_product_philox_and_grid_paths_are_exact():
     Q = 20000
     qx = syn.query_points(30, Q)
     reg = syn.grid_region(qx, dims)
+    if order == "sorted":
+        qx, reg = _sorted(qx, reg)
     bw, bmu, bL = syn.bsdf_lobes(31, Q, J)
     u = orc.uniforms(99, Q)
     tq, tr, tw, tm, tl, tu = _dev(qx, reg, bw, bmu, bL, u)
