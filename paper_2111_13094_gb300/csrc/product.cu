@@ -49,9 +49,9 @@ __device__ inline Pair make_pair(const float* P, float cm0, float cm1, float lcp
     o.p10 = o.ln = 0.f;
     o.lw = -INFINITY;
     // the lobe's mean in the mu_k chart
-    const float u = P[20] * mu2[0] + P[21] * mu2[1] + P[22] * mu2[2];
-    const float v = P[23] * mu2[0] + P[24] * mu2[1] + P[25] * mu2[2];
-    const float c = P[26] * mu2[0] + P[27] * mu2[1] + P[28] * mu2[2];
+    const float u = P[qrec::T] * mu2[0] + P[qrec::T + 1] * mu2[1] + P[qrec::T + 2] * mu2[2];
+    const float v = P[qrec::B] * mu2[0] + P[qrec::B + 1] * mu2[1] + P[qrec::B + 2] * mu2[2];
+    const float c = P[qrec::MUW] * mu2[0] + P[qrec::MUW + 1] * mu2[1] + P[qrec::MUW + 2] * mu2[2];
     const float s2 = u * u + v * v;
     const float rs = rsqrtf(s2);
     const float s = s2 > 0.f ? s2 * rs : 0.f;
@@ -68,9 +68,9 @@ __device__ inline Pair make_pair(const float* P, float cm0, float cm1, float lcp
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
         const float e0 = q == 0 ? t2[0] : b2[0], e1 = q == 0 ? t2[1] : b2[1], e2 = q == 0 ? t2[2] : b2[2];
-        const float ta = P[20] * e0 + P[21] * e1 + P[22] * e2;
-        const float tb = P[23] * e0 + P[24] * e1 + P[25] * e2;
-        const float tc = P[26] * e0 + P[27] * e1 + P[28] * e2;
+        const float ta = P[qrec::T] * e0 + P[qrec::T + 1] * e1 + P[qrec::T + 2] * e2;
+        const float tb = P[qrec::B] * e0 + P[qrec::B + 1] * e1 + P[qrec::B + 2] * e2;
+        const float tc = P[qrec::MUW] * e0 + P[qrec::MUW + 1] * e1 + P[qrec::MUW + 2] * e2;
         J[0][q] = g * ta + u * tc * h;
         J[1][q] = g * tb + v * tc * h;
     }
@@ -78,7 +78,8 @@ __device__ inline Pair make_pair(const float* P, float cm0, float cm1, float lcp
     const float M00 = J[0][0] * L2[0] + J[0][1] * L2[1], M01 = J[0][1] * L2[2];
     const float M10 = J[1][0] * L2[0] + J[1][1] * L2[1], M11 = J[1][1] * L2[2];
     const float b00 = M00 * M00 + M01 * M01, b01 = M00 * M10 + M01 * M11, b11 = M10 * M10 + M11 * M11;
-    const float a00 = P[33] * P[33], a01 = P[33] * P[34], a11 = P[34] * P[34] + P[35] * P[35];
+    const float d00 = P[qrec::D], d10 = P[qrec::D + 1], d11 = P[qrec::D + 2];
+    const float a00 = d00 * d00, a01 = d00 * d10, a11 = d10 * d10 + d11 * d11;
     // S = S1 + S2' and its inverse
     const float S00 = a00 + b00, S01 = a01 + b01, S11 = a11 + b11;
     const float det = S00 * S11 - S01 * S01;
@@ -194,19 +195,21 @@ __global__ void __launch_bounds__(256, 3)
                 } else {
 #pragma unroll
                     for (int q = 0; q < kQ; ++q) P[q] = 0.f;
-                    P[28] = 1.f;
-                    P[33] = P[35] = P[29] = P[31] = 1.f;
-                    P[3] = -INFINITY;
+                    P[qrec::MUW + 2] = 1.f;
+                    P[qrec::D] = P[qrec::D + 2] = P[qrec::DINV] = P[qrec::DINV + 2] = 1.f;
+                    P[qrec::CX] = -INFINITY;
                 }
             }
             // ---- conditioning on position (as in k_query)
-            const float e0 = (qx0 - P[0]) - P[4], e1 = (qx1 - P[1]) - P[5], e2 = (qx2 - P[2]) - P[6];
-            const float z0 = P[7] * e0;
-            const float z1 = P[8] * e0 + P[9] * e1;
-            const float z2 = P[10] * e0 + P[11] * e1 + P[12] * e2;
-            const float lw = P[3] - 0.5f * (z0 * z0 + z1 * z1 + z2 * z2);
-            const float m0 = P[13] * z0 + P[14] * z1 + P[15] * z2;
-            const float m1 = P[16] * z0 + P[17] * z1 + P[18] * z2;
+            const float e0 = (qx0 - P[qrec::MUX]) - P[qrec::REM];
+            const float e1 = (qx1 - P[qrec::MUX + 1]) - P[qrec::REM + 1];
+            const float e2 = (qx2 - P[qrec::MUX + 2]) - P[qrec::REM + 2];
+            const float z0 = P[qrec::AINV] * e0;
+            const float z1 = P[qrec::AINV + 1] * e0 + P[qrec::AINV + 2] * e1;
+            const float z2 = P[qrec::AINV + 3] * e0 + P[qrec::AINV + 4] * e1 + P[qrec::AINV + 5] * e2;
+            const float lw = P[qrec::CX] - 0.5f * (z0 * z0 + z1 * z1 + z2 * z2);
+            const float m0 = P[qrec::CT] * z0 + P[qrec::CT + 1] * z1 + P[qrec::CT + 2] * z2;
+            const float m1 = P[qrec::CT + 3] * z0 + P[qrec::CT + 4] * z1 + P[qrec::CT + 5] * z2;
             float mx = lw;
 #pragma unroll
             for (int o = KP / 2; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(FULL, mx, o));
@@ -299,9 +302,9 @@ __global__ void __launch_bounds__(256, 3)
                     sincosf(rn, &sr, &cr);
                     const float sc = rn < 1e-3f ? 1.f - rn * rn * (1.f / 6.f) : __fdividef(sr, rn);
                     const float c0 = n0 * sc, c1 = n1 * sc;
-                    s0 = c0 * P[20] + c1 * P[23] + cr * P[26];
-                    s1 = c0 * P[21] + c1 * P[24] + cr * P[27];
-                    s2 = c0 * P[22] + c1 * P[25] + cr * P[28];
+                    s0 = c0 * P[qrec::T] + c1 * P[qrec::B] + cr * P[qrec::MUW];
+                    s1 = c0 * P[qrec::T + 1] + c1 * P[qrec::B + 1] + cr * P[qrec::MUW + 1];
+                    s2 = c0 * P[qrec::T + 2] + c1 * P[qrec::B + 2] + cr * P[qrec::MUW + 2];
                 }
                 const int from = base_lane + kk;
                 w0 = __shfl_sync(FULL, s0, from);
@@ -310,9 +313,9 @@ __global__ void __launch_bounds__(256, 3)
                 valid = __shfl_sync(FULL, vv, from) > 0.5f && ok && pos != 0u;
             }
             // ---- pdf of the product mixture at w: every pair's chart density / sinc
-            const float u = P[20] * w0 + P[21] * wv1 + P[22] * wv2;
-            const float v = P[23] * w0 + P[24] * wv1 + P[25] * wv2;
-            const float cz = P[26] * w0 + P[27] * wv1 + P[28] * wv2;
+            const float u = P[qrec::T] * w0 + P[qrec::T + 1] * wv1 + P[qrec::T + 2] * wv2;
+            const float v = P[qrec::B] * w0 + P[qrec::B + 1] * wv1 + P[qrec::B + 2] * wv2;
+            const float cz = P[qrec::MUW] * w0 + P[qrec::MUW + 1] * wv1 + P[qrec::MUW + 2] * wv2;
             const float s2v = u * u + v * v;
             const bool cut = s2v == 0.f && cz < 0.f;          // antipode: outside the chart
             const float gg = cut ? 1.f : g_of_cos(cz, rsqrtf(s2v));

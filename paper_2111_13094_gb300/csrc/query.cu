@@ -35,9 +35,10 @@ namespace sdmm {
 // when the region changes) and the threads of that region read them from
 // there, one pass per region.  A warp whose queries span more regions
 // (queries in any order) processes them with one lane per component instead
-// (warp_by_components), which reads each query's records once, coalesced.  With `perm`, the warp's j-th query is perm[j] and
-// outputs go to the slot's record (the library's binning of queries given in
-// any order), else to the query's own index.
+// (warp_by_components), which reads each query's records once, coalesced.
+// With `perm`, the warp's j-th query is perm[j] and outputs go to the slot's
+// record (the library's binning of queries given in any order), else to the
+// query's own index.
 constexpr int kQWarps = 4;
 
 template <int KP, int OP>
@@ -329,20 +330,20 @@ __device__ __forceinline__ void warp_by_components(const float* __restrict__ qta
             } else {
 #pragma unroll
                 for (int q = 0; q < kQ; ++q) P[q] = 0.f;
-                P[28] = 1.f;
-                P[33] = P[35] = P[29] = P[31] = 1.f;
-                P[3] = -INFINITY;
+                P[qrec::MUW + 2] = 1.f;
+                P[qrec::D] = P[qrec::D + 2] = P[qrec::DINV] = P[qrec::DINV + 2] = 1.f;
+                P[qrec::CX] = -INFINITY;
             }
         }
         // ---- conditioning on position: z = A^-1 (x - mu^x)
-        const float e0 = (qx0 - P[0]) - P[4], e1 = (qx1 - P[1]) - P[5],
-                    e2 = (qx2 - P[2]) - P[6];
-        const float z0 = P[7] * e0;
-        const float z1 = P[8] * e0 + P[9] * e1;
-        const float z2 = P[10] * e0 + P[11] * e1 + P[12] * e2;
-        const float lw = P[3] - 0.5f * (z0 * z0 + z1 * z1 + z2 * z2);
-        const float m0 = P[13] * z0 + P[14] * z1 + P[15] * z2;   // C^T z
-        const float m1 = P[16] * z0 + P[17] * z1 + P[18] * z2;
+        const float e0 = (qx0 - P[qrec::MUX]) - P[qrec::REM], e1 = (qx1 - P[qrec::MUX + 1]) - P[qrec::REM + 1],
+                    e2 = (qx2 - P[qrec::MUX + 2]) - P[qrec::REM + 2];
+        const float z0 = P[qrec::AINV] * e0;
+        const float z1 = P[qrec::AINV + 1] * e0 + P[qrec::AINV + 2] * e1;
+        const float z2 = P[qrec::AINV + 3] * e0 + P[qrec::AINV + 4] * e1 + P[qrec::AINV + 5] * e2;
+        const float lw = P[qrec::CX] - 0.5f * (z0 * z0 + z1 * z1 + z2 * z2);
+        const float m0 = P[qrec::CT] * z0 + P[qrec::CT + 1] * z1 + P[qrec::CT + 2] * z2;   // C^T z
+        const float m1 = P[qrec::CT + 3] * z0 + P[qrec::CT + 4] * z1 + P[qrec::CT + 5] * z2;
         // normalise pi'_k over the KP component lanes (log-sum-exp)
         float mx = lw;
 #pragma unroll
@@ -360,9 +361,9 @@ __device__ __forceinline__ void warp_by_components(const float* __restrict__ qta
                 cond_pi[o] = ok ? cpi : 0.f;
                 cond_m[2 * o] = m0;
                 cond_m[2 * o + 1] = m1;
-                cond_L[3 * o] = P[33];
-                cond_L[3 * o + 1] = P[34];
-                cond_L[3 * o + 2] = P[35];
+                cond_L[3 * o] = P[qrec::D];
+                cond_L[3 * o + 1] = P[qrec::D + 1];
+                cond_L[3 * o + 2] = P[qrec::D + 2];
             }
             continue;
         }
@@ -392,17 +393,17 @@ __device__ __forceinline__ void warp_by_components(const float* __restrict__ qta
                 float sn, cs;
                 sincospif(2.f * b2, &sn, &cs);
                 const float g0 = rad * cs, g1 = rad * sn;
-                const float n0 = m0 + P[33] * g0;
-                const float n1 = m1 + P[34] * g0 + P[35] * g1;
+                const float n0 = m0 + P[qrec::D] * g0;
+                const float n1 = m1 + P[qrec::D + 1] * g0 + P[qrec::D + 2] * g1;
                 const float rn = sqrtf(n0 * n0 + n1 * n1);
                 vv = rn < kPiF ? 1.f : 0.f;
                 float sr, cr;
                 sincosf(rn, &sr, &cr);
                 const float sc = rn < 1e-3f ? 1.f - rn * rn * (1.f / 6.f) : __fdividef(sr, rn);
                 const float c0 = n0 * sc, c1 = n1 * sc;
-                s0 = c0 * P[20] + c1 * P[23] + cr * P[26];
-                s1 = c0 * P[21] + c1 * P[24] + cr * P[27];
-                s2 = c0 * P[22] + c1 * P[25] + cr * P[28];
+                s0 = c0 * P[qrec::T] + c1 * P[qrec::B] + cr * P[qrec::MUW];
+                s1 = c0 * P[qrec::T + 1] + c1 * P[qrec::B + 1] + cr * P[qrec::MUW + 1];
+                s2 = c0 * P[qrec::T + 2] + c1 * P[qrec::B + 2] + cr * P[qrec::MUW + 2];
             }
             const int from = base_lane + kk;
             w0 = __shfl_sync(FULL, s0, from);
@@ -411,16 +412,16 @@ __device__ __forceinline__ void warp_by_components(const float* __restrict__ qta
             valid = __shfl_sync(FULL, vv, from) > 0.5f && ok && pos != 0u;
         }
         // ---- solid-angle pdf of the conditioned mixture at w (Eq. solidangle-pdf)
-        const float u = P[20] * w0 + P[21] * w1 + P[22] * w2;
-        const float v = P[23] * w0 + P[24] * w1 + P[25] * w2;
-        const float cz = P[26] * w0 + P[27] * w1 + P[28] * w2;
+        const float u = P[qrec::T] * w0 + P[qrec::T + 1] * w1 + P[qrec::T + 2] * w2;
+        const float v = P[qrec::B] * w0 + P[qrec::B + 1] * w1 + P[qrec::B + 2] * w2;
+        const float cz = P[qrec::MUW] * w0 + P[qrec::MUW + 1] * w1 + P[qrec::MUW + 2] * w2;
         const float s2v = u * u + v * v;
         const bool cut = s2v == 0.f && cz < 0.f;          // antipode: outside the chart
         const float gg = cut ? 1.f : g_of_cos(cz, rsqrtf(s2v));   // theta / sin(theta) = 1/sinc
         const float d0 = gg * u - m0, d1 = gg * v - m1;
-        const float y0 = P[29] * d0;
-        const float y1 = P[30] * d0 + P[31] * d1;
-        float pk_ = cpi * __expf(P[32] - 0.5f * (y0 * y0 + y1 * y1)) * gg;
+        const float y0 = P[qrec::DINV] * d0;
+        const float y1 = P[qrec::DINV + 1] * d0 + P[qrec::DINV + 2] * d1;
+        float pk_ = cpi * __expf(P[qrec::CN] - 0.5f * (y0 * y0 + y1 * y1)) * gg;
         if (cut || k >= K) pk_ = 0.f;
         float p = pk_;
 #pragma unroll
