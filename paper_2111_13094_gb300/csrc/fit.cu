@@ -387,12 +387,21 @@ __global__ void __launch_bounds__(kWarps * 32, 2)
 
 // ---------------------------------------------------------------------------
 // Sum of a region's unit partials in FP64, in unit order (deterministic).
+// The units' FP32 partials of one region summed in a fixed order: four
+// consecutive units in FP32 (pairwise), the groups in FP64.  FP64 work on
+// GB300's narrow FP64 pipe is what bounds the M-step; a unit partial carries
+// the rounding of its own FP32 accumulation over up to thousands of samples,
+// which the three FP32 additions of a group do not exceed.
 __device__ inline void reduce_partials(const float* __restrict__ partial, int ps, int64_t c0,
                                        int64_t c1, int nv, double* __restrict__ out, int t0 = threadIdx.x,
                                        int nt = blockDim.x) {
     for (int v = t0; v < nv; v += nt) {
+        const float* __restrict__ p = partial + v;
         double s = 0.0;
-        for (int64_t c = c0; c < c1; ++c) s += (double)partial[c * ps + v];
+        int64_t c = c0;
+        for (; c + 4 <= c1; c += 4)
+            s += (double)((p[c * ps] + p[(c + 1) * ps]) + (p[(c + 2) * ps] + p[(c + 3) * ps]));
+        for (; c < c1; ++c) s += (double)p[c * ps];
         out[v] = s;
     }
 }
