@@ -381,3 +381,21 @@ def test_underflowing_samples_take_the_exact_log_sum_exp(K):
     # from their means; the M-step's covariance is then the difference of two
     # large uncentred FP32 moments (L within 5e-3), outside the 1e-3 contract
     # for this stress case; the log-sum-exp under test is exact above
+
+
+def test_empty_batch_skips_every_region():
+    """A batch without samples (every region empty): every region is
+    reported skipped and its parameters are left as they were."""
+    K, R = 16, 5
+    b = _small_batch(51, K, [300] * R)
+    ost = oracle_init(51, b, K)
+    gcfg = api.config(K)
+    st = gpu_state(ost, gcfg)
+    before = host(st)
+    samples = torch.zeros(7, 0, dtype=torch.float32, device="cuda")
+    batch = api.SampleBatch(samples, torch.zeros(R + 1, dtype=torch.int64, device="cuda"))
+    api.fit_regions(gcfg, batch, 2, st, api.workspace(gcfg, R, 0))
+    g = host(st)
+    assert list(g.status) == [1] * R
+    for f in ("pi", "mu_x", "mu_w", "L", "S0", "S2"):
+        assert np.array_equal(getattr(g, f), getattr(before, f)), f

@@ -242,3 +242,40 @@ def test_binned_entry_points_match_the_oracle(K):
     if K <= 16:                                       # the binned path needs its workspace
         with pytest.raises(api.SdmmError):
             api.sample(cfg, st, tq, seed=77, region=tr, ws=ws[: ws.numel() // 2])
+
+
+@pytest.mark.parametrize("K", [2, 16])
+def test_empty_and_ragged_query_batches(K):
+    """No queries (every entry point returns empty outputs); 37 queries of one
+    region (one warp plus a ragged tail, all through the thread-per-query
+    path) and the same 37 queries through the library's binning, where the
+    bin is padded to two warps: both agree with the oracle."""
+    dims = (2, 2, 2)
+    ost = _mixtures(41, dims, K)
+    cfg = api.config(K)
+    st = gpu_state(ost, cfg)
+    grid = api.Grid((0, 0, 0), (1, 1, 1), dims)
+    e = torch.empty(0, 3, device="cuda")
+    ws0 = api.query_workspace(st.R, 0)
+    for kw in (dict(grid=grid), dict(grid=grid, ws=ws0)):
+        d, p, v = api.sample(cfg, st, e, seed=1, **kw)
+        assert d.shape == (0, 3) and p.numel() == 0 and v.numel() == 0
+        assert api.pdf(cfg, st, e, e, **kw).numel() == 0
+    Q = 37
+    rng = np.random.default_rng(42)
+    qx = (0.5 * rng.random((Q, 3)) + np.array([0.5, 0.0, 0.5])).astype(np.float32)   # all in cell (1, 0, 1)
+    reg = syn.grid_region(qx, dims)
+    assert np.all(reg == reg[0])
+    u = orc.uniforms(43, Q)
+    o = orc.sample(K, ost.pi, ost.mu_x, ost.mu_w, ost.L, qx, reg, u)
+    same = o["margin"] > 1e-5
+    tq = torch.from_numpy(qx).cuda()
+    ws = api.query_workspace(st.R, Q)
+    for kw in (dict(region=torch.from_numpy(reg).cuda()), dict(grid=grid, ws=ws)):
+        d, p, v = (t.cpu().numpy() for t in api.sample(cfg, st, tq, seed=43, **kw))
+        assert np.array_equal(v[same], o["valid"][same])
+        ok = same & (o["valid"] == 1)
+        assert _angle(d[ok].astype(np.float64), o["dir"][ok]).max() < 1e-4
+        vv = v == 1
+        po = orc.pdf(K, ost.pi, ost.mu_x, ost.mu_w, ost.L, qx[vv], reg[vv], d[vv].astype(np.float64))
+        assert_pdf_close(p[vv], po, ost, K, qx[vv], reg[vv], d[vv].astype(np.float64))
