@@ -667,9 +667,9 @@ def kdtree_leg(api, torch, dev, batch, N, peaks):
            "bin_samples_per_s": N / (tb * 1e-3), "refine_samples_per_s": N / (tr * 1e-3),
            "bin_roofline": {"bound": "hbm", "achieved": bin_gbs, "peak": hbm, "unit": "GB/s",
                             "frac": bin_gbs / hbm, "bytes_per_sample": 56.0},
-           "note": "host wall time of the synchronous calls (binning: leaf lookup, stable radix sort by "
-                   "leaf, one gather; refinement: rounds of stable partitions, one 4-byte read-back per "
-                   "tree level)"}
+           "note": "host wall time of the synchronous calls (binning: leaf lookup, one stable counting "
+                   "pass by leaf that moves the streams (up to 1024 leaves); refinement: rounds of stable "
+                   "partitions, one 4-byte read-back per tree level)"}
     del tree, kb, kr, kp
     return res
 

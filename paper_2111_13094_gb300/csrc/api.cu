@@ -1037,7 +1037,7 @@ KdLayout kd_layout(const sdmm_kdtree* t, int64_t N) {
     L.tile_prefix = take(sizeof(int64_t) * T);
     L.seg_tile0 = take(sizeof(int32_t) * (S + 1));
     L.counters = take(sizeof(int32_t) * 4);
-    L.rx_hist = take(sizeof(uint32_t) * 256 * (size_t)rx_tiles(N));
+    L.rx_hist = take(sizeof(uint32_t) * (size_t)rx_hist_entries(N));
     L.rx_bsum = take(sizeof(uint32_t) * ((size_t)rx_scan_blocks(N) + 1));
     L.total = o;
     return L;

@@ -797,8 +797,80 @@ __global__ void k_gather_idx(int64_t N, const uint32_t* __restrict__ idx, BatchD
     for (int q = 0; q < 7; ++q) const_cast<float*>(out.p[q])[i] = in.p[q][j];
 }
 
+// One counting pass for trees of at most 1024 leaves (10-bit keys): tiles of
+// 8192 keys, so the digit counts take as much room as the 8-bit passes'
+// (1024 x N / 8192 = 256 x N / 2048), and the scatter moves the seven sample
+// streams themselves (read in order, written to their leaf's run) instead of
+// an index that a gather would follow at random afterwards.
+constexpr int kCsBits = 10, kCsDigits = 1 << kCsBits, kCsPer = 32, kCsTile = kRxThreads * kCsPer;
+
+__global__ void __launch_bounds__(kRxThreads) k_cs_hist(const uint32_t* __restrict__ key, int64_t N, int T,
+                                                      uint32_t* __restrict__ hist) {
+    __shared__ uint32_t h[kCsDigits];
+    for (int d = threadIdx.x; d < kCsDigits; d += kRxThreads) h[d] = 0u;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kCsTile;
+    for (int q = 0; q < kCsPer; ++q) {
+        const int64_t i = base + q * kRxThreads + threadIdx.x;
+        if (i < N) atomicAdd(&h[key[i] & (kCsDigits - 1)], 1u);
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < kCsDigits; d += kRxThreads) hist[(int64_t)d * T + blockIdx.x] = h[d];
+}
+
+// stable scatter of the keys and the seven streams: the tile's keys in 32
+// ordered sub-rounds of 256; within a sub-round, rank among equal keys by
+// warp, then lane (warp counts kept only for the keys present)
+__global__ void __launch_bounds__(kRxThreads) k_cs_scatter(const uint32_t* __restrict__ key_in,
+                                                         uint32_t* __restrict__ key_out, int64_t N, int T,
+                                                         const uint32_t* __restrict__ off, BatchDesc in,
+                                                         BatchDesc out) {
+    constexpr int W = kRxThreads / 32;
+    __shared__ uint32_t s_carry[kCsDigits];
+    __shared__ uint32_t s_wc[W][kCsDigits];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tile = blockIdx.x;
+    for (int d = tid; d < kCsDigits; d += kRxThreads) {
+        s_carry[d] = off[(int64_t)d * T + tile];
+#pragma unroll
+        for (int w = 0; w < W; ++w) s_wc[w][d] = 0u;
+    }
+    __syncthreads();
+    const int64_t base = (int64_t)tile * kCsTile;
+    for (int r = 0; r < kCsPer; ++r) {
+        const int64_t i = base + r * kRxThreads + tid;
+        const bool valid = i < N;
+        const uint32_t k = valid ? key_in[i] : 0u;
+        const uint32_t d = valid ? (k & (kCsDigits - 1)) : (uint32_t)kCsDigits;   // invalid lanes match only each other
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const int rank = __popc(peers & ((1u << lane) - 1u));
+        const bool lead = valid && rank == 0;
+        if (lead) s_wc[warp][d] = (uint32_t)__popc(peers);
+        __syncthreads();
+        if (valid) {
+            uint32_t pre = 0u;
+            for (int w = 0; w < warp; ++w) pre += s_wc[w][d];
+            const uint32_t dst = s_carry[d] + pre + (uint32_t)rank;
+            key_out[dst] = k;
+#pragma unroll
+            for (int q = 0; q < 7; ++q) const_cast<float*>(out.p[q])[dst] = in.p[q][i];
+        }
+        __syncthreads();
+        if (lead) {
+            atomicAdd(&s_carry[d], (uint32_t)__popc(peers));
+            s_wc[warp][d] = 0u;
+        }
+        __syncthreads();
+    }
+}
+
 int64_t rx_tiles(int64_t N) { return (N + kRxTile - 1) / kRxTile; }
-int64_t rx_scan_blocks(int64_t N) { return (256 * rx_tiles(N) + kRxScan - 1) / kRxScan; }
+// digit-count entries of the larger of the two schemes (8-bit passes; the
+// one 10-bit pass, whose tile count rounds up separately)
+int64_t rx_hist_entries(int64_t N) {
+    return std::max<int64_t>(256 * rx_tiles(N), (int64_t)kCsDigits * ((N + kCsTile - 1) / kCsTile));
+}
+int64_t rx_scan_blocks(int64_t N) { return (rx_hist_entries(N) + kRxScan - 1) / kRxScan; }
 
 cudaError_t launch_kd_bin(cudaStream_t st, const KdWork& w, const int32_t* axis, const double* split,
                           const int32_t* left, const int32_t* leaf, int32_t n_nodes, int32_t n_leaves, int64_t N,
@@ -812,10 +884,22 @@ cudaError_t launch_kd_bin(cudaStream_t st, const KdWork& w, const int32_t* axis,
                                                                pz, key[0], idx[0]);
         int bits = 0;
         while (bits < 32 && (int64_t(1) << bits) < (int64_t)n_leaves) ++bits;
+        if (bits <= kCsBits) {                    // one counting pass moving the streams
+            const int T = (int)((N + kCsTile - 1) / kCsTile);
+            const int64_t M = (int64_t)kCsDigits * T;
+            const int nb = (int)((M + kRxScan - 1) / kRxScan);
+            k_cs_hist<<<T, kRxThreads, 0, st>>>(key[0], N, T, w.rx_hist);
+            k_rx_scan_sums<<<nb, 1024, 0, st>>>(w.rx_hist, M, w.rx_bsum);
+            k_rx_scan_top<<<1, 1024, 0, st>>>(w.rx_bsum, nb);
+            k_rx_scan_down<<<nb, 1024, 0, st>>>(w.rx_hist, M, w.rx_bsum);
+            k_cs_scatter<<<T, kRxThreads, 0, st>>>(key[0], key[1], N, T, w.rx_hist, in, out);
+            k_bin_offsets<<<(unsigned)((N + 1 + 255) / 256), 256, 0, st>>>(key[1], N, n_leaves, offsets);
+            return cudaGetLastError();
+        }
         const int passes = std::max(1, (bits + 7) / 8);
         const int T = (int)rx_tiles(N);
         const int64_t M = 256 * (int64_t)T;
-        const int nb = (int)rx_scan_blocks(N);
+        const int nb = (int)((M + kRxScan - 1) / kRxScan);
         for (int p = 0; p < passes; ++p) {
             const int src = p & 1, dst = src ^ 1;
             k_rx_hist<<<T, kRxThreads, 0, st>>>(key[src], N, 8 * p, T, w.rx_hist);

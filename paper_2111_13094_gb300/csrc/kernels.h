@@ -126,6 +126,7 @@ cudaError_t kd_rounds(cudaStream_t st, const KdWork& w, int64_t c, int32_t* tree
                       const float4** rec_final,
                       int64_t** seg_off_final, int64_t** seg_parent_final, int32_t* S_final, int* overflow);
 int64_t rx_tiles(int64_t N);
+int64_t rx_hist_entries(int64_t N);
 int64_t rx_scan_blocks(int64_t N);
 cudaError_t launch_kd_bin(cudaStream_t st, const KdWork& w, const int32_t* axis, const double* split,
                           const int32_t* left, const int32_t* leaf, int32_t n_nodes, int32_t n_leaves, int64_t N,

@@ -40,11 +40,16 @@ def test_grid_lookup_matches_oracle(levels):
     assert np.array_equal(got, kd.lookup(ot, pts))
 
 
-def test_binning_matches_oracle():
-    s = _scene(1, 60000)
-    t = api.KdTree(4096, 4096).grid(3)
+@pytest.mark.parametrize("N,levels", [(60000, 3), (8193, 3), (100, 1), (60000, 4), (9000, 4)])
+def test_binning_matches_oracle(N, levels):
+    """Up to 1024 leaves (levels <= 3: 8^levels) the binning is one counting
+    pass that moves the streams; beyond (levels = 4: 4096 leaves) two 8-bit
+    passes on (leaf, index) and a gather.  Both keep each leaf's samples in
+    their input order; N spans whole and ragged tiles."""
+    s = _scene(1, N)
+    t = api.KdTree(1 << 14, 1 << 13).grid(levels)
     b = t.bin(torch.from_numpy(s).cuda())
-    out, off, _ = kd.bin_samples(kd.grid(3), s)
+    out, off, _ = kd.bin_samples(kd.grid(levels), s)
     assert np.array_equal(b.offsets.cpu().numpy(), off)
     assert np.array_equal(b.samples.cpu().numpy(), out)
 
