@@ -939,6 +939,88 @@ def config_ablations(api, torch, dev, stream, want_cpu, R=1024, M=16384, K=16, r
     return out
 
 
+def config_batching(api, torch, dev, stream, seed=0, R=512, K=16, reps=5):
+    """The batched form against plain per-region fitting (the paper fits each
+    kD-tree leaf on its own): one stepwise round of R regions of the batched
+    workload's recipe, as one sdmm_fit_regions call (persistent work queue over
+    all regions) and as R calls of one region each, on the same work units
+    (chunk fixed), so both compute the same FP32 sums: the parameters must
+    agree bit for bit, i.e. at equal log-likelihood error."""
+    import ctypes
+
+    from paper_2111_13094_gb300 import _lib
+    from paper_2111_13094_gb300 import synthetic as syn
+    lib = _lib.load()
+    truth = syn.batched_truth(seed + 5, R, K=K)
+    counts = syn.region_counts(seed + 5, R)
+    b = syn.batched_round(seed + 5, R, counts, 0, truth)
+    cfg = api.config(K, chunk=CHUNK)
+    batch = api.SampleBatch(torch.from_numpy(np.ascontiguousarray(b.samples)).to(dev),
+                            torch.from_numpy(b.offsets).to(dev))
+    st = api.MixtureState(R, K, device=dev)
+    api.init_regions(cfg, batch, torch.from_numpy(np.asarray(b.extent, np.float64)).to(dev),
+                     torch.from_numpy(syn.init_uniforms(seed + 5, R, K // 8)).to(dev), st)
+    snap = {f: getattr(st, f).clone() for f in STATE_FIELDS + ("etab", "qtab")}
+    ws = api.workspace(cfg, R, b.N, device=dev)
+    Mmax = int(np.max(counts))
+    ws1 = api.workspace(cfg, 1, Mmax, device=dev)
+    one_off = [torch.tensor([0, int(m)], dtype=torch.int64, device=dev) for m in counts]
+    s = batch.samples
+    row = s.stride(0) * s.element_size()
+    off = b.offsets
+
+    def region_state(r):
+        ptrs = []
+        for f in api.MixtureState.FIELDS:
+            t = getattr(st, f)
+            ptrs.append(t.data_ptr() + r * (t.numel() // R) * t.element_size())
+        return _lib.State(*ptrs)
+
+    def batched():
+        api.fit_regions(cfg, batch, 1, st, ws, stream=stream)
+
+    sm = [_lib.Samples(*[s.data_ptr() + q * row + int(off[r]) * s.element_size() for q in range(7)],
+                       one_off[r].data_ptr(), 1, int(counts[r])) for r in range(R)]
+    sts = [region_state(r) for r in range(R)]
+    hs = ctypes.c_void_p(stream.cuda_stream)
+
+    def per_region():
+        for r in range(R):
+            _lib.check(lib.sdmm_fit_regions(ctypes.byref(cfg), ctypes.byref(sm[r]), 1, None, ctypes.byref(sts[r]),
+                                            None, ctypes.c_void_p(ws1.data_ptr()), ws1.numel(), hs),
+                       "sdmm_fit_regions")
+
+    def restore():
+        for f, v in snap.items():
+            getattr(st, f).copy_(v)
+
+    res = {"config": f"one stepwise round of {R} regions (counts log-uniform in [256, 65536], "
+                     f"{int(counts.sum())} samples), K = {K}, work units of {CHUNK} samples in both forms"}
+    out = {}
+    for name, fn in (("batched", batched), ("per_region", per_region)):
+        times = []
+        for rep in range(reps + 1):
+            restore()
+            torch.cuda.synchronize()
+            e0, e1 = _events()
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if rep > 0:
+                times.append(e0.elapsed_time(e1))
+        res[f"{name}_ms"] = float(np.mean(times))
+        out[name] = {f: getattr(st, f).clone() for f in ("pi", "mu_x", "mu_w", "L", "status")}
+    res["speedup"] = res["per_region_ms"] / res["batched_ms"]
+    res["bit_identical"] = all(torch.equal(out["batched"][f], out["per_region"][f]) for f in out["batched"])
+    res["value_batched"] = float(counts.sum()) / (res["batched_ms"] * 1e-3)
+    res["value_per_region"] = float(counts.sum()) / (res["per_region_ms"] * 1e-3)
+    res["unit"] = UNIT
+    del ws, ws1, st, batch
+    torch.cuda.empty_cache()
+    return res
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -1081,7 +1163,8 @@ def run_gpu(args):
         configs = {"single_region": config_single_region(api, torch, dev, stream, want_cpu),
                    "precision_sweep": config_precision_sweep(api, torch, dev, stream, want_cpu),
                    "objective": config_objective(api, torch, dev, stream, want_cpu),
-                   "ablations": config_ablations(api, torch, dev, stream, want_cpu)}
+                   "ablations": config_ablations(api, torch, dev, stream, want_cpu),
+                   "batching": config_batching(api, torch, dev, stream)}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
