@@ -624,14 +624,18 @@ static sdmm_status objective_common(const sdmm_config* cfg, const sdmm_samples* 
     if (nsm <= 0) return fail(SDMM_ERR_CUDA, "no CUDA device");
     const WsPtrs w = ws_ptrs(workspace, L);
     const int KP = pow2_ceil(cfg->K);
+    // the specialised E-step's whitened statistics serve the adjoint too
+    // (converted per component in the reduction); the generic kernel
+    // accumulates the adjoint's own for K <= 2
+    const int ystats = estep_fast_supported(KP);
     SDMM_CUDA(launch_set_desc(stream, w.hdr, make_desc(s, prior_scale, nullptr)), "set_desc");
     SDMM_CUDA(launch_build_chunks(stream, w.hdr, w.cb, w.cr, nullptr, L.chunk, 1, L.max_chunks), "build_chunks");
-    SDMM_CUDA(launch_accumulate(stream, dF ? MODE_GRAD : MODE_FIT, KP, nsm * default_ctas(cfg), w.hdr,
-                                w.cb, w.cr, st->etab, cfg->K, L.chunk, cfg->estep_density, w.partial,
+    SDMM_CUDA(launch_accumulate(stream, (dF && !ystats) ? MODE_GRAD : MODE_FIT, KP, nsm * default_ctas(cfg),
+                                w.hdr, w.cb, w.cr, st->etab, cfg->K, L.chunk, cfg->estep_density, w.partial,
                                 L.ps, 0, nullptr, cfg->dir_coords == SDMM_DIR_EUCLIDEAN, 1),
               "accumulate");
     SDMM_CUDA(launch_reduce_objective(stream, s->R, w.hdr, w.cb, w.partial, L.ps, *cfg, *st, F_out, dF,
-                                      gd, gL, ga),
+                                      gd, gL, ga, ystats),
               "reduce_objective");
     return SDMM_OK;
 }

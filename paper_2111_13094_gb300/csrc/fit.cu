@@ -800,10 +800,33 @@ __global__ void __launch_bounds__(G == 1 ? 128 : 32, G == 1 ? 1 : 16) k_reduce_m
 
 // ---------------------------------------------------------------------------
 // MAP objective (and, with dF != nullptr, its adjoint) from the partials.
+// The adjoint's statistics [w r, w r z, w r z y^T (lower)] (z = L^-T y,
+// y = L^-1 d) from the whitened ones of the specialised E-step,
+// [w r, w r y', w r y' y'^T] with y' = c y (c = sqrt(log2(e) / 2)): z is
+// L^-T y per component, so its sums are L^-T times the sums of y.  FP64.
+__device__ inline void whitened_to_adjoint(const double* __restrict__ Li, double* __restrict__ sk) {
+    const double ic = 1.0 / (double)0.849321800288019f, ic2 = ic * ic;
+    double Y[5][5], z1[5], zy[15];
+    for (int a = 0; a < 5; ++a)
+        for (int b = 0; b <= a; ++b) Y[a][b] = Y[b][a] = sk[6 + pk(a, b)];
+    for (int i = 0; i < 5; ++i) {
+        double v = 0.0;
+        for (int m = i; m < 5; ++m) v += Li[pk(m, i)] * sk[1 + m];
+        z1[i] = v * ic;
+        for (int j = 0; j <= i; ++j) {
+            double u = 0.0;
+            for (int m = i; m < 5; ++m) u += Li[pk(m, i)] * Y[m][j];
+            zy[pk(i, j)] = u * ic2;
+        }
+    }
+    for (int i = 0; i < 5; ++i) sk[1 + i] = z1[i];
+    for (int p = 0; p < 15; ++p) sk[6 + p] = zy[p];
+}
+
 __global__ void __launch_bounds__(128) k_reduce_objective(
     const WsHeader* __restrict__ ws, const int64_t* __restrict__ chunk_base,
     const float* __restrict__ partial, int ps, sdmm_config cfg, sdmm_state st, double* F_out,
-    const double* __restrict__ dF, float* g_delta, float* g_L, float* g_logit) {
+    const double* __restrict__ dF, float* g_delta, float* g_L, float* g_logit, int ystats) {
     const int64_t r = blockIdx.x;
     const int K = cfg.K;
     const int tid = threadIdx.x;
@@ -839,7 +862,8 @@ __global__ void __launch_bounds__(128) k_reduce_objective(
         s_Fk[tid] = beta * q * log(pi) - 0.5 * beta * a * logdet - 0.5 * beta * trBS;
         if (dF != nullptr) {
             const double sc = dF[r];
-            const double* sk = s_st + tid * kStat;
+            double* sk = s_st + tid * kStat;
+            if (ystats) whitened_to_adjoint(Li, sk);
             const double invW = W > 0.0 ? 1.0 / W : 0.0;
             for (int c = 0; c < 5; ++c) g_delta[rk * 5 + c] = (float)(sc * sk[1 + c] * invW);
             for (int i = 0; i < 5; ++i)
@@ -1176,8 +1200,8 @@ cudaError_t launch_reduce_mstep(cudaStream_t s, int64_t R, WsHeader* ws, const i
 cudaError_t launch_reduce_objective(cudaStream_t s, int64_t R, const WsHeader* ws,
                                     const int64_t* cb, const float* partial, int ps,
                                     const sdmm_config& cfg, const sdmm_state& st, double* F,
-                                    const double* dF, float* gd, float* gL, float* ga) {
-    k_reduce_objective<<<(unsigned)R, 128, 0, s>>>(ws, cb, partial, ps, cfg, st, F, dF, gd, gL, ga);
+                                    const double* dF, float* gd, float* gL, float* ga, int ystats) {
+    k_reduce_objective<<<(unsigned)R, 128, 0, s>>>(ws, cb, partial, ps, cfg, st, F, dF, gd, gL, ga, ystats);
     return cudaGetLastError();
 }
 

@@ -54,7 +54,7 @@ cudaError_t launch_tc_estep(cudaStream_t s, int K, int prec, int grid, WsHeader*
 cudaError_t launch_reduce_objective(cudaStream_t s, int64_t R, const WsHeader* ws,
                                     const int64_t* cb, const float* partial, int ps,
                                     const sdmm_config& cfg, const sdmm_state& st, double* F,
-                                    const double* dF, float* gd, float* gL, float* ga);
+                                    const double* dF, float* gd, float* gL, float* ga, int ystats);
 cudaError_t launch_init(cudaStream_t s, int64_t R, const sdmm_config& cfg, const BatchDesc& d,
                         const double* extent, const double* uniforms, const sdmm_state& st);
 cudaError_t launch_prepare(cudaStream_t s, int K, int64_t R, const sdmm_state& st,
