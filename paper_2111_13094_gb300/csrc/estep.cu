@@ -55,11 +55,17 @@ __device__ __forceinline__ void st_shared_pred(bool pred, float2* p, float a, fl
 // (direction coordinates without the log map, g = 1); SOLID: the solid-angle
 // density p^t / sinc of the E-step, whose log Jacobian lifts a component above
 // the region bound, so every sample takes the exact per-sample maximum.
-template <int KP, bool OFFS, bool EUCL, bool SOLID>
+// TWO: the second pass of the accurate covariance update (Sec. 3.2 Eq.
+// tangent-space-sigma-update): the responsibilities of the current
+// parameters, the sample measured in the chart of each component's new mean
+// (chart2 records: new mean, its rows t', b', mu'), and only the second
+// moments w r d' d'^T accumulated, 15 per component, in the chart.
+template <int KP, bool OFFS, bool EUCL, bool SOLID, bool TWO = false>
 __global__ void __launch_bounds__(kEW * 32, kECtas)
     k_estep(WsHeader* __restrict__ ws, const int64_t* __restrict__ chunk_base,
             const int32_t* __restrict__ chunk_region, const float* __restrict__ etab, int K, int chunk,
-            float* __restrict__ partial, int ps, int write_ll) {
+            float* __restrict__ partial, int ps, int write_ll, const float* __restrict__ chart2) {
+    static_assert(!(TWO && (OFFS || EUCL)), "the second pass runs in tangent charts at the means");
     static_assert(KP >= 4 && KP <= 32, "two samples per lane need 2 * 32 / KP <= 32");
     constexpr int SPI = 32 / KP;
     constexpr int RED = KP * kStat + 4;
@@ -97,6 +103,7 @@ __global__ void __launch_bounds__(kEW * 32, kECtas)
     for (int q = 0; q < 15; ++q) li[q] = 0.f;
     float c2 = -INFINITY, lmax = 0.f;
     float xr0 = 0.f, xr1 = 0.f, xr2 = 0.f;
+    float n2[9] = {}, mo2[3] = {};   // TWO: the new chart's rows and mean (from the reference point); unused otherwise
     int prev_r = -1;
 
     // log2 of the chart density of one sample at this lane's component,
@@ -125,6 +132,22 @@ __global__ void __launch_bounds__(kEW * 32, kECtas)
         if (EUCL) return l2;
         const bool cut = !(s2 >= 1.17549435e-38f) && cz < 0.f;   // to within 1e-19 rad
         return cut ? -INFINITY : l2;
+    };
+
+    // TWO: the sample in the chart of this lane's component's new mean,
+    // d' = (x - mu'^x, log_{mu'}(w)), into y; true at the new chart's cut locus
+    auto new_chart = [&](const float4 sa, const float4 sb, float y[5]) -> bool {
+        const float u = n2[0] * sb.x + n2[1] * sb.y + n2[2] * sb.z;
+        const float v = n2[3] * sb.x + n2[4] * sb.y + n2[5] * sb.z;
+        const float cz = n2[6] * sb.x + n2[7] * sb.y + n2[8] * sb.z;
+        const float s2 = u * u + v * v;
+        const float gg = g_of_cos_fit(cz, fminf(tc::rsqrt_approx(s2), 1e18f));
+        y[0] = sa.x - mo2[0];
+        y[1] = sa.y - mo2[1];
+        y[2] = sa.z - mo2[2];
+        y[3] = gg * u;
+        y[4] = gg * v;
+        return !(s2 >= 1.17549435e-38f) && cz < 0.f;
     };
 
     for (;;) {
@@ -173,6 +196,23 @@ __global__ void __launch_bounds__(kEW * 32, kECtas)
                     mo[a] = acc_m;
                 }
                 c5 = p[27];
+                if (TWO) {
+                    float q2[kChart];
+                    const float4* src2 = reinterpret_cast<const float4*>(chart2 + ((int64_t)r * K + k) * kChart);
+#pragma unroll
+                    for (int q = 0; q < kChart / 4; ++q) {
+                        const float4 v = __ldg(src2 + q);
+                        q2[4 * q + 0] = v.x;
+                        q2[4 * q + 1] = v.y;
+                        q2[4 * q + 2] = v.z;
+                        q2[4 * q + 3] = v.w;
+                    }
+#pragma unroll
+                    for (int q = 0; q < 9; ++q) n2[q] = q2[3 + q];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) mo2[c] = ((c == 0 ? q2[0] : c == 1 ? q2[1] : q2[2]) -
+                                                          (c == 0 ? xr0 : c == 1 ? xr1 : xr2)) + q2[12 + c];
+                }
             } else {                         // padding lane: density 0
 #pragma unroll
                 for (int q = 0; q < 9; ++q) rt[q] = 0.f;
@@ -181,6 +221,13 @@ __global__ void __launch_bounds__(kEW * 32, kECtas)
                 for (int q = 0; q < 5; ++q) mo[q] = 0.f;
 #pragma unroll
                 for (int q = 0; q < 15; ++q) li[q] = 0.f;
+                if (TWO) {
+#pragma unroll
+                    for (int q = 0; q < 9; ++q) n2[q] = 0.f;
+                    n2[8] = 1.f;
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) mo2[q] = 0.f;
+                }
             }
             lmax = c5;
 #pragma unroll
@@ -292,8 +339,12 @@ __global__ void __launch_bounds__(kEW * 32, kECtas)
                                    SOLID ? lmax + (lo ? refa : refb) * kLn2F : lmax);
                 }
                 const float ia = tc::rcp_approx(sa), ib = tc::rcp_approx(sb);
-                const float ra = sa >= kSumMin ? xa.w * ea * ia : 0.f;
-                const float rb = sb >= kSumMin ? xb.w * eb * ib : 0.f;
+                float ra = sa >= kSumMin ? xa.w * ea * ia : 0.f;
+                float rb = sb >= kSumMin ? xb.w * eb * ib : 0.f;
+                if (TWO) {
+                    if (new_chart(xa, wa, ya)) ra = 0.f;
+                    if (new_chart(xb, wb, yb)) rb = 0.f;
+                }
                 accumulate(ra, ya);
                 accumulate(rb, yb);
             }
@@ -318,7 +369,8 @@ __global__ void __launch_bounds__(kEW * 32, kECtas)
 #pragma unroll
                 for (int o = KP / 2; o > 0; o >>= 1) se += __shfl_xor_sync(FULL, se, o);
                 if (k == 0 && act) s_lse[warp][j] = make_float2(se, lmax + ref * kLn2F);
-                const float rr = (act && se >= kSumMin) ? __fdividef(xa.w * e, se) : 0.f;
+                float rr = (act && se >= kSumMin) ? __fdividef(xa.w * e, se) : 0.f;
+                if (TWO && new_chart(xa, wa, ya)) rr = 0.f;
                 accumulate(rr, ya);
             }
             __syncwarp();
@@ -364,12 +416,23 @@ __global__ void __launch_bounds__(kEW * 32, kECtas)
             red[warp][K * kStat + 1] = wll;
         }
         __syncthreads();
-        const int nv = K * kStat + 2;
-        for (int v = threadIdx.x; v < nv; v += kEW * 32) {
-            float s = 0.f;
+        if (TWO) {   // the second pass's layout: 15 second moments per component
+            const int nv = K * 15;
+            for (int v = threadIdx.x; v < nv; v += kEW * 32) {
+                const int src = (v / 15) * kStat + 6 + v % 15;
+                float s = 0.f;
 #pragma unroll
-            for (int w = 0; w < kEW; ++w) s += red[w][v];
-            partial[(int64_t)c * ps + v] = s;
+                for (int w = 0; w < kEW; ++w) s += red[w][src];
+                partial[(int64_t)c * ps + v] = s;
+            }
+        } else {
+            const int nv = K * kStat + 2;
+            for (int v = threadIdx.x; v < nv; v += kEW * 32) {
+                float s = 0.f;
+#pragma unroll
+                for (int w = 0; w < kEW; ++w) s += red[w][v];
+                partial[(int64_t)c * ps + v] = s;
+            }
         }
     }
 }
@@ -378,7 +441,7 @@ bool estep_fast_supported(int KP) { return KP >= 4 && KP <= 32; }
 
 cudaError_t launch_estep_fast(cudaStream_t s, int KP, int grid, WsHeader* ws, const int64_t* cb,
                               const int32_t* cr, const float* etab, int K, int chunk, float* partial,
-                              int ps, int write_ll, int variant) {
+                              int ps, int write_ll, int variant, const float* chart2) {
     // persistent grid of every resident CTA (the work queue balances the
     // units); the caller's grid, sized for the 8-warp kernels, is not used
     (void)grid;
@@ -387,23 +450,17 @@ cudaError_t launch_estep_fast(cudaStream_t s, int KP, int grid, WsHeader* ws, co
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
     grid = nsm * kECtas;
+#define SDMM_ESTEP_V(P, O, E, S, T)                                                                    \
+    k_estep<P, O, E, S, T><<<grid, kEW * 32, 0, s>>>(ws, cb, cr, etab, K, chunk, partial, ps, write_ll, chart2)
 #define SDMM_ESTEP(P)                                                                                  \
     case P:                                                                                            \
-        if (variant == ESTEP_EUCLID)                                                                   \
-            k_estep<P, true, true, false><<<grid, kEW * 32, 0, s>>>(ws, cb, cr, etab, K, chunk, partial, ps, \
-                                                                    write_ll);                         \
-        else if (variant == ESTEP_SOLID)                                                               \
-            k_estep<P, false, false, true><<<grid, kEW * 32, 0, s>>>(ws, cb, cr, etab, K, chunk, partial, ps, \
-                                                                     write_ll);                        \
-        else if (variant == ESTEP_SOLID_OFFSETS)                                                       \
-            k_estep<P, true, false, true><<<grid, kEW * 32, 0, s>>>(ws, cb, cr, etab, K, chunk, partial, ps,  \
-                                                                    write_ll);                         \
-        else if (variant == ESTEP_OFFSETS)                                                             \
-            k_estep<P, true, false, false><<<grid, kEW * 32, 0, s>>>(ws, cb, cr, etab, K, chunk, partial, ps, \
-                                                                     write_ll);                        \
-        else                                                                                           \
-            k_estep<P, false, false, false><<<grid, kEW * 32, 0, s>>>(ws, cb, cr, etab, K, chunk, partial,   \
-                                                                      ps, write_ll);                   \
+        if (variant == ESTEP_EUCLID) SDMM_ESTEP_V(P, true, true, false, false);                        \
+        else if (variant == ESTEP_SOLID) SDMM_ESTEP_V(P, false, false, true, false);                   \
+        else if (variant == ESTEP_SOLID_OFFSETS) SDMM_ESTEP_V(P, true, false, true, false);            \
+        else if (variant == ESTEP_OFFSETS) SDMM_ESTEP_V(P, true, false, false, false);                 \
+        else if (variant == ESTEP_TWO) SDMM_ESTEP_V(P, false, false, false, true);                     \
+        else if (variant == ESTEP_TWO_SOLID) SDMM_ESTEP_V(P, false, false, true, true);                \
+        else SDMM_ESTEP_V(P, false, false, false, false);                                              \
         break;
     switch (KP) {
         SDMM_ESTEP(4)
@@ -413,6 +470,7 @@ cudaError_t launch_estep_fast(cudaStream_t s, int KP, int grid, WsHeader* ws, co
         default: return cudaErrorInvalidValue;
     }
 #undef SDMM_ESTEP
+#undef SDMM_ESTEP_V
     return cudaGetLastError();
 }
 

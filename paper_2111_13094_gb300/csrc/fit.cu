@@ -1152,6 +1152,9 @@ cudaError_t launch_accumulate(cudaStream_t s, int mode, int KP, int grid, WsHead
     if (mode == MODE_FIT)
         return launch_acc_mode<MODE_FIT>(KP, dim3(grid), s, ws, cb, cr, etab, K, chunk, density,
                                          partial, ps, write_ll, nullptr, euclid);
+    if (mode == MODE_TWO && estep_fast_supported(KP))
+        return launch_estep_fast(s, KP, grid, ws, cb, cr, etab, K, chunk, partial, ps, 0,
+                                 density == SDMM_DENSITY_SOLID_ANGLE ? ESTEP_TWO_SOLID : ESTEP_TWO, chart2);
     if (mode == MODE_TWO)
         return launch_acc_mode<MODE_TWO>(KP, dim3(grid), s, ws, cb, cr, etab, K, chunk, density,
                                          partial, ps, 0, chart2, 0);

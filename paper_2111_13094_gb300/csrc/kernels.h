@@ -27,11 +27,12 @@ cudaError_t launch_accumulate(cudaStream_t s, int mode, int KP, int grid, WsHead
                               int chunk, int density, float* partial, int ps, int write_ll,
                               const float* chart2 = nullptr, int euclid = 0, int chart_offsets = 0);
 // specialised E-step of the fit and the objective's forward pass, KP in 4..32
-enum { ESTEP_CHART = 0, ESTEP_OFFSETS = 1, ESTEP_EUCLID = 2, ESTEP_SOLID = 3, ESTEP_SOLID_OFFSETS = 4 };
+enum { ESTEP_CHART = 0, ESTEP_OFFSETS = 1, ESTEP_EUCLID = 2, ESTEP_SOLID = 3, ESTEP_SOLID_OFFSETS = 4,
+       ESTEP_TWO = 5, ESTEP_TWO_SOLID = 6 };
 bool estep_fast_supported(int KP);
 cudaError_t launch_estep_fast(cudaStream_t s, int KP, int grid, WsHeader* ws, const int64_t* cb,
                               const int32_t* cr, const float* etab, int K, int chunk, float* partial,
-                              int ps, int write_ll, int variant);
+                              int ps, int write_ll, int variant, const float* chart2 = nullptr);
 // ystats: the E-step partials are in whitened coordinates (k_estep); the
 // reductions take them back to the chart
 cudaError_t launch_new_charts(cudaStream_t s, int64_t R, WsHeader* ws, const int64_t* cb,
