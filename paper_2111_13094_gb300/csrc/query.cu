@@ -76,6 +76,7 @@ __global__ void __launch_bounds__(kQWarps * 32, kQCtas)
     float2* const cmu = &s_cmu[0][threadIdx.x];                // and cmu[k * CS]
     constexpr int CS = kQWarps * 32;
     int staged = -1;
+    float rbound = 0.f;                                        // the staged region's bound
     const int64_t wstride = (int64_t)gridDim.x * kQWarps * 32;
     for (int64_t base = ((int64_t)blockIdx.x * kQWarps + warp) * 32; base < Q; base += wstride) {
         const int64_t j = base + lane;
@@ -147,9 +148,20 @@ __global__ void __launch_bounds__(kQWarps * 32, kQCtas)
             const int rp = pass == 0 ? r0 : r1;
             if (pass == 1 && r1 == r0) break;
             if (rp != staged) {
+                // and the region bound B = log2(e) max_k cx_k: no conditioned
+                // weight pi_k N(x) of the region exceeds 2^B (times the common
+                // constant), so 2^(lw - B) needs no per-query maximum
                 __syncwarp();
                 const float4* src = q4 + (int64_t)rp * n4;
-                for (int e = lane; e < n4; e += 32) s_rec[warp][e] = __ldg(src + e);
+                float cmax = -INFINITY;
+                for (int e = lane; e < n4; e += 32) {
+                    const float4 v = __ldg(src + e);
+                    s_rec[warp][e] = v;
+                    if (e % Q4 == 0) cmax = fmaxf(cmax, v.w);   // cx of component e / Q4
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) cmax = fmaxf(cmax, __shfl_xor_sync(FULL, cmax, o));
+                rbound = cmax > -INFINITY ? cmax * kL2e : 0.f;
                 __syncwarp();
                 staged = rp;
             }
@@ -157,8 +169,9 @@ __global__ void __launch_bounds__(kQWarps * 32, kQCtas)
             const float4* rec = &s_rec[warp][0];
 
             // ---- pass 1: conditioning on the position (Sec. 3.2), every component:
-            // lw = log2 of pi'_k up to a common constant, m = C^T z
-            float mx = -INFINITY;
+            // w'_k = 2^(lw - B) with lw = log2 of pi'_k up to a common constant,
+            // m = C^T z, se = sum w'_k
+            float se = 0.f;
 #pragma unroll 4
             for (int k = 0; k < K; ++k) {
                 // the record's conditioning group, float4 0-4: (mu_x, cx), (remainder,
@@ -169,18 +182,36 @@ __global__ void __launch_bounds__(kQWarps * 32, kQCtas)
                 const float z0 = g1.w * e0;
                 const float z1 = g2.x * e0 + g2.y * e1;
                 const float z2 = g2.z * e0 + g2.w * e1 + g3.x * e2;
-                const float lw = fmaf(-0.5f, z0 * z0 + z1 * z1 + z2 * z2, g0.w) * kL2e;
-                cw[k * CS] = lw;
-                cmu[k * CS] = make_float2(g3.y * z0 + g3.z * z1 + g3.w * z2, g4.x * z0 + g4.y * z1 + g4.z * z2);
-                mx = fmaxf(mx, lw);
-            }
-            // normalisation: w'_k = 2^(lw - max), se = sum w'_k
-            float se = 0.f;
-#pragma unroll 4
-            for (int k = 0; k < K; ++k) {
-                const float w = mx > -INFINITY ? tc::ex2_approx(cw[k * CS] - mx) : 0.f;
+                const float w = tc::ex2_approx(
+                    fmaf(-0.5f * kL2e, z0 * z0 + z1 * z1 + z2 * z2, fmaf(g0.w, kL2e, -rbound)));
                 cw[k * CS] = w;
+                cmu[k * CS] = make_float2(g3.y * z0 + g3.z * z1 + g3.w * z2, g4.x * z0 + g4.y * z1 + g4.z * z2);
                 se += w;
+            }
+            if (!(se >= 0x1p-100f)) {
+                // every weight more than 2^100 below the bound (a position far
+                // from all components), where the shifted weights lose
+                // precision or flush to zero: w'_k = 2^(lw - max) instead
+                float mx = -INFINITY;
+#pragma unroll 1
+                for (int k = 0; k < K; ++k) {
+                    const float4* rk = rec + k * Q4;
+                    const float4 g0 = rk[0], g1 = rk[1], g2 = rk[2], g3 = rk[3];
+                    const float e0 = (x0 - g0.x) - g1.x, e1 = (x1 - g0.y) - g1.y, e2 = (x2 - g0.z) - g1.z;
+                    const float z0 = g1.w * e0;
+                    const float z1 = g2.x * e0 + g2.y * e1;
+                    const float z2 = g2.z * e0 + g2.w * e1 + g3.x * e2;
+                    const float lw = fmaf(-0.5f * kL2e, z0 * z0 + z1 * z1 + z2 * z2, g0.w * kL2e);
+                    cw[k * CS] = lw;
+                    mx = fmaxf(mx, lw);
+                }
+                se = 0.f;
+#pragma unroll 1
+                for (int k = 0; k < K; ++k) {
+                    const float w = mx > -INFINITY ? tc::ex2_approx(cw[k * CS] - mx) : 0.f;
+                    cw[k * CS] = w;
+                    se += w;
+                }
             }
 
             float w0, w1, w2;
@@ -199,19 +230,21 @@ __global__ void __launch_bounds__(kQWarps * 32, kQCtas)
                     u2 = u24(o.z);
                 }
                 // component by inverse CDF on u0 (Sec. 3.1 "Sampling", step i): the
-                // first k with u0 se < cumsum; rounding past the end takes the last
-                // component of positive weight
+                // first k with u0 se < cumsum, i.e. the number of partial sums
+                // <= u0 se (they do not decrease); rounding past the end takes the
+                // last component of positive weight
                 const float thr = u0 * se;
                 float cum = 0.f;
-                int kk = -1, last = -1;
+                int kk = 0;
 #pragma unroll 4
                 for (int k = 0; k < K; ++k) {
-                    const float w = cw[k * CS];
-                    cum += w;
-                    last = w > 0.f ? k : last;
-                    kk = (kk < 0 && thr < cum) ? k : kk;
+                    cum += cw[k * CS];
+                    kk += cum <= thr ? 1 : 0;
                 }
-                if (kk < 0) kk = last >= 0 ? last : 0;
+                if (kk >= K) {
+                    kk = K - 1;
+                    while (kk > 0 && !(cw[kk * CS] > 0.f)) --kk;
+                }
                 const float2 sel = cmu[kk * CS];
                 // Gaussian draw in the chart (step ii), exp map (step iii)
                 // the chart group, float4 5-8: (t, b.x), (b.y, b.z, mu_w.x, mu_w.y),
@@ -225,7 +258,7 @@ __global__ void __launch_bounds__(kQWarps * 32, kQCtas)
                 const float n0 = sel.x + h8.y * g0;
                 const float n1 = sel.y + h8.z * g0 + h8.w * g1;
                 const float rn = sqrtf(n0 * n0 + n1 * n1);
-                valid = (rn < kPiF) && ok && last >= 0;
+                valid = (rn < kPiF) && ok && se > 0.f;
                 float sr, cr;
                 sincosf(rn, &sr, &cr);
                 const float sc = rn < 1e-3f ? 1.f - rn * rn * (1.f / 6.f) : __fdividef(sr, rn);
