@@ -62,6 +62,8 @@ __global__ void __launch_bounds__(kQWarps * 32, kQCtas)
     static_assert(OP == OP_SAMPLE || OP == OP_PDF, "sampling and pdf only");
     constexpr unsigned FULL = 0xffffffffu;
     constexpr float kL2e = 1.44269504088896341f;
+    constexpr float kC = 0.849321800288019f;                   // sqrt(log2(e) / 2)
+    constexpr float kIC = 1.177410022515475f;                  // 1 / kC
     constexpr int Q4 = kQ / 4;                                 // float4 per record
     __shared__ float4 s_rec[kQWarps][KM * Q4];                 // per warp: one region's records
     // per thread and component: the weight w'_k and the conditional mean m_k,
@@ -76,9 +78,14 @@ __global__ void __launch_bounds__(kQWarps * 32, kQCtas)
     float2* const cmu = &s_cmu[0][threadIdx.x];                // and cmu[k * CS]
     constexpr int CS = kQWarps * 32;
     int staged = -1;
-    float rbound = 0.f;                                        // the staged region's bound
-    const int64_t wstride = (int64_t)gridDim.x * kQWarps * 32;
-    for (int64_t base = ((int64_t)blockIdx.x * kQWarps + warp) * 32; base < Q; base += wstride) {
+    // each warp takes a contiguous run of batches of 32 slots, so that sorted
+    // queries stage a region's records once per region, not once per batch
+    const int64_t nbat = (Q + 31) / 32, nwarps = (int64_t)gridDim.x * kQWarps;
+    const int64_t per = (nbat + nwarps - 1) / nwarps;
+    const int64_t b0 = ((int64_t)blockIdx.x * kQWarps + warp) * per;
+    const int64_t b1 = b0 + per < nbat ? b0 + per : nbat;
+    for (int64_t bat = b0; bat < b1; ++bat) {
+        const int64_t base = bat * 32;
         const int64_t j = base + lane;
         bool in = j < Q;
         int64_t i = j;
@@ -148,20 +155,37 @@ __global__ void __launch_bounds__(kQWarps * 32, kQCtas)
             const int rp = pass == 0 ? r0 : r1;
             if (pass == 1 && r1 == r0) break;
             if (rp != staged) {
-                // and the region bound B = log2(e) max_k cx_k: no conditioned
-                // weight pi_k N(x) of the region exceeds 2^B (times the common
-                // constant), so 2^(lw - B) needs no per-query maximum
+                // the region's records, rescaled for the base-2 exponents of
+                // both passes: A^-1 and D^-1 times c = sqrt(log2(e) / 2), so that
+                // |z|^2 and |y|^2 are already those exponents; C^T times 1 / c
+                // (the conditional mean C^T z unchanged); cn times log2(e); cx
+                // times log2(e) less the region bound B = log2(e) max_k cx_k:
+                // no conditioned weight of the region exceeds 2^B (times the
+                // common constant), so 2^(lw - B) needs no per-query maximum
                 __syncwarp();
                 const float4* src = q4 + (int64_t)rp * n4;
                 float cmax = -INFINITY;
                 for (int e = lane; e < n4; e += 32) {
-                    const float4 v = __ldg(src + e);
+                    float4 v = __ldg(src + e);
+                    switch (e % Q4) {
+                        case 0: cmax = fmaxf(cmax, v.w); break;                          // (mu_x, cx)
+                        case 1: v.w *= kC; break;                                         // (rem, A^-1 0)
+                        case 2: v.x *= kC; v.y *= kC; v.z *= kC; v.w *= kC; break;        // A^-1 1..4
+                        case 3: v.x *= kC; v.y *= kIC; v.z *= kIC; v.w *= kIC; break;     // (A^-1 5, C^T 0)
+                        case 4: v.x *= kIC; v.y *= kIC; v.z *= kIC; break;                // (C^T 1, 0)
+                        case 7: v.y *= kC; v.z *= kC; v.w *= kC; break;                   // (mu_w.z, D^-1)
+                        case 8: v.x *= kL2e; break;                                       // (cn, D)
+                        default: break;
+                    }
                     s_rec[warp][e] = v;
-                    if (e % Q4 == 0) cmax = fmaxf(cmax, v.w);   // cx of component e / Q4
                 }
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) cmax = fmaxf(cmax, __shfl_xor_sync(FULL, cmax, o));
-                rbound = cmax > -INFINITY ? cmax * kL2e : 0.f;
+                const float rbound = cmax > -INFINITY ? cmax * kL2e : 0.f;
+                for (int e = lane; e < n4; e += 32) {    // the lane's own entries
+                    float* cx = &s_rec[warp][e].w;
+                    if (e % Q4 == 0) *cx = fmaf(*cx, kL2e, -rbound);
+                }
                 __syncwarp();
                 staged = rp;
             }
@@ -174,16 +198,16 @@ __global__ void __launch_bounds__(kQWarps * 32, kQCtas)
             float se = 0.f;
 #pragma unroll 4
             for (int k = 0; k < K; ++k) {
-                // the record's conditioning group, float4 0-4: (mu_x, cx), (remainder,
-                // A^-1 0), A^-1 1..4, (A^-1 5, C^T row 0), (C^T row 1, 0)
+                // the record's conditioning group as staged, float4 0-4: (mu_x, cx - B),
+                // (remainder, c A^-1 0), c A^-1 1..4, (c A^-1 5, C^T row 0 / c),
+                // (C^T row 1 / c, 0)
                 const float4* rk = rec + k * Q4;
                 const float4 g0 = rk[0], g1 = rk[1], g2 = rk[2], g3 = rk[3], g4 = rk[4];
                 const float e0 = (x0 - g0.x) - g1.x, e1 = (x1 - g0.y) - g1.y, e2 = (x2 - g0.z) - g1.z;
                 const float z0 = g1.w * e0;
                 const float z1 = g2.x * e0 + g2.y * e1;
                 const float z2 = g2.z * e0 + g2.w * e1 + g3.x * e2;
-                const float w = tc::ex2_approx(
-                    fmaf(-0.5f * kL2e, z0 * z0 + z1 * z1 + z2 * z2, fmaf(g0.w, kL2e, -rbound)));
+                const float w = tc::ex2_approx(fmaf(-z2, z2, fmaf(-z1, z1, fmaf(-z0, z0, g0.w))));
                 cw[k * CS] = w;
                 cmu[k * CS] = make_float2(g3.y * z0 + g3.z * z1 + g3.w * z2, g4.x * z0 + g4.y * z1 + g4.z * z2);
                 se += w;
@@ -201,7 +225,7 @@ __global__ void __launch_bounds__(kQWarps * 32, kQCtas)
                     const float z0 = g1.w * e0;
                     const float z1 = g2.x * e0 + g2.y * e1;
                     const float z2 = g2.z * e0 + g2.w * e1 + g3.x * e2;
-                    const float lw = fmaf(-0.5f * kL2e, z0 * z0 + z1 * z1 + z2 * z2, g0.w * kL2e);
+                    const float lw = fmaf(-z2, z2, fmaf(-z1, z1, fmaf(-z0, z0, g0.w)));
                     cw[k * CS] = lw;
                     mx = fmaxf(mx, lw);
                 }
@@ -290,10 +314,10 @@ __global__ void __launch_bounds__(kQWarps * 32, kQCtas)
                 const bool cut = !(s2v >= 1.17549435e-38f) && cz < 0.f;
                 const float gg = cut ? 1.f : g_of_cos(cz, tc::rsqrt_approx(s2v));
                 const float d0 = gg * u - mk.x, d1 = gg * v - mk.y;
-                // D^-1 (h7.y, h7.z, h7.w), cn = h8.x
+                // c D^-1 (h7.y, h7.z, h7.w), log2(e) cn = h8.x as staged
                 const float y0 = h7.y * d0;
                 const float y1 = h7.z * d0 + h7.w * d1;
-                const float pk_ = wk * tc::ex2_approx(fmaf(-0.5f, y0 * y0 + y1 * y1, h8.x) * kL2e) * gg;
+                const float pk_ = wk * tc::ex2_approx(fmaf(-y1, y1, fmaf(-y0, y0, h8.x))) * gg;
                 p += cut ? 0.f : pk_;
             }
             p = se > 0.f ? __fdividef(p, se) : 0.f;
