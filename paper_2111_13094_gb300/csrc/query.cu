@@ -71,6 +71,21 @@ __global__ void __launch_bounds__(kQWarps * 32, kQCtas)
     // wavefront (interleaved with the means they were four)
     __shared__ float s_cw[KM][kQWarps * 32];
     __shared__ float2 s_cmu[KM][kQWarps * 32];
+    // per float4 of a record, the factors of its staged copy: A^-1 and D^-1
+    // times c = sqrt(log2(e) / 2), C^T times 1 / c, cn times log2(e)
+    __shared__ float4 s_scale[Q4];
+    if (threadIdx.x < Q4) {
+        const int m = threadIdx.x;
+        float4 f = make_float4(1.f, 1.f, 1.f, 1.f);
+        if (m == 1) f.w = kC;                                              // (rem, A^-1 0)
+        if (m == 2) f = make_float4(kC, kC, kC, kC);                       // A^-1 1..4
+        if (m == 3) f = make_float4(kC, kIC, kIC, kIC);                    // (A^-1 5, C^T 0)
+        if (m == 4) f = make_float4(kIC, kIC, kIC, 1.f);                   // (C^T 1, 0)
+        if (m == 7) f = make_float4(1.f, kC, kC, kC);                      // (mu_w.z, D^-1)
+        if (m == 8) f.x = kL2e;                                            // (cn, D)
+        s_scale[m] = f;
+    }
+    __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const float4* __restrict__ q4 = reinterpret_cast<const float4*>(qtab);
     const int n4 = K * Q4;                                     // float4 of one region's records
@@ -166,25 +181,23 @@ __global__ void __launch_bounds__(kQWarps * 32, kQCtas)
                 const float4* src = q4 + (int64_t)rp * n4;
                 float cmax = -INFINITY;
                 for (int e = lane; e < n4; e += 32) {
+                    const int m = e % Q4;
                     float4 v = __ldg(src + e);
-                    switch (e % Q4) {
-                        case 0: cmax = fmaxf(cmax, v.w); break;                          // (mu_x, cx)
-                        case 1: v.w *= kC; break;                                         // (rem, A^-1 0)
-                        case 2: v.x *= kC; v.y *= kC; v.z *= kC; v.w *= kC; break;        // A^-1 1..4
-                        case 3: v.x *= kC; v.y *= kIC; v.z *= kIC; v.w *= kIC; break;     // (A^-1 5, C^T 0)
-                        case 4: v.x *= kIC; v.y *= kIC; v.z *= kIC; break;                // (C^T 1, 0)
-                        case 7: v.y *= kC; v.z *= kC; v.w *= kC; break;                   // (mu_w.z, D^-1)
-                        case 8: v.x *= kL2e; break;                                       // (cn, D)
-                        default: break;
-                    }
+                    const float4 f = s_scale[m];
+                    cmax = m == 0 ? fmaxf(cmax, v.w) : cmax;
+                    v.x *= f.x;
+                    v.y *= f.y;
+                    v.z *= f.z;
+                    v.w *= f.w;
                     s_rec[warp][e] = v;
                 }
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) cmax = fmaxf(cmax, __shfl_xor_sync(FULL, cmax, o));
                 const float rbound = cmax > -INFINITY ? cmax * kL2e : 0.f;
-                for (int e = lane; e < n4; e += 32) {    // the lane's own entries
-                    float* cx = &s_rec[warp][e].w;
-                    if (e % Q4 == 0) *cx = fmaf(*cx, kL2e, -rbound);
+                __syncwarp();
+                for (int c = lane; c < K; c += 32) {     // cx - B of component c
+                    float* cx = &s_rec[warp][c * Q4].w;
+                    *cx = fmaf(*cx, kL2e, -rbound);
                 }
                 __syncwarp();
                 staged = rp;
