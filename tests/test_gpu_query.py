@@ -8,7 +8,7 @@ import torch
 from scipy import stats
 
 import oracle as orc
-from gpu_util import PDF_RTOL, assert_pdf_close, gpu_state
+from gpu_util import EPS32, PDF_RTOL, assert_pdf_close, gpu_state, pdf_kappa
 from paper_2111_13094_gb300 import api
 from paper_2111_13094_gb300 import synthetic as syn
 
@@ -279,3 +279,87 @@ def test_empty_and_ragged_query_batches(K):
         vv = v == 1
         po = orc.pdf(K, ost.pi, ost.mu_x, ost.mu_w, ost.L, qx[vv], reg[vv], d[vv].astype(np.float64))
         assert_pdf_close(p[vv], po, ost, K, qx[vv], reg[vv], d[vv].astype(np.float64))
+
+
+def _far_mixture(seed, K):
+    """One region's K components with narrow positions (std 1e-3 to 4e-3) and
+    weak position-direction coupling, so that a position tenths away from
+    every mean is tens to hundreds of standard deviations out while the
+    conditional mean m = L21 z stays well inside the chart."""
+    pi, mu_x, mu_w, L = syn.random_mixtures(seed, (1, 1, 1), K)
+    for i in range(5):
+        for j in range(min(i + 1, 3)):
+            L[..., i * (i + 1) // 2 + j] *= 0.02 if i < 3 else 0.002
+    ost = orc.State(1, K)
+    ost.set_params(pi, mu_x, mu_w, L)
+    return ost
+
+
+def _spatial_terms(ost, K, qx):
+    """Per query and component, in FP64: |z_k|^2 with z_k = A_k^-1 (x - mu_k),
+    and log2 of pi_k N_3(x; mu_k, A_k A_k^T) less the region's bound (its
+    largest log2 of pi_k / ((2 pi)^(3/2) det A_k))."""
+    Lp = ost.L.reshape(K, 15)
+    mu = ost.mu_x.reshape(K, 3)
+    pi = ost.pi.reshape(K)
+    z2 = np.empty((qx.shape[0], K))
+    cx = np.empty(K)
+    for k in range(K):
+        A = np.zeros((3, 3))
+        for i in range(3):
+            for j in range(i + 1):
+                A[i, j] = Lp[k, i * (i + 1) // 2 + j]
+        z = np.linalg.solve(A, (qx.astype(np.float64) - mu[k]).T)
+        z2[:, k] = (z * z).sum(axis=0)
+        cx[k] = np.log(pi[k]) - np.log(np.diag(A)).sum() - 1.5 * np.log(2 * np.pi)
+    lw2 = (cx[None, :] - 0.5 * z2 - cx.max()) / np.log(2.0)
+    return z2, lw2
+
+
+@pytest.mark.parametrize("K", [3, 16])
+def test_far_positions_take_the_exact_maximum(K):
+    """Positions far from every component of their region: every conditioned
+    weight pi_k N_3(x) lies more than 2^110 below the region's bound, so the
+    weights shifted by the bound underflow and the kernel redoes them with the
+    exact per-query maximum (a broken redo gives pdf 0 and valid 0 for all).
+    Validity and directions match the oracle where its component choice has a
+    margin of 1e-2 (the FP32 weights of near-tied components differ from the
+    FP64 ones by about eps |z|^2); each pdf, of the sample entry and of the pdf
+    entry at the same direction, is within 32 eps times its condition number,
+    here the direction part plus the largest |z_k|^2 of the components that
+    carry 1e-3 of the conditioned weight (the rounding of their spatial
+    Mahalanobis terms)."""
+    ost = _far_mixture(61, K)
+    qx = syn.query_points(62, 6000)
+    z2, lw2 = _spatial_terms(ost, K, qx)
+    far = lw2.max(axis=1) < -110.0
+    assert far.mean() > 0.9
+    qx = np.ascontiguousarray(qx[far])
+    z2, lw2 = z2[far], lw2[far]
+    Q = qx.shape[0]
+    reg = np.zeros(Q, np.int32)
+    cfg = api.config(K)
+    st = gpu_state(ost, cfg)
+    tq, tr = torch.from_numpy(qx).cuda(), torch.from_numpy(reg).cuda()
+    dt, pt, vt = api.sample(cfg, st, tq, region=tr, seed=63)
+    pe = api.pdf(cfg, st, tq, dt, region=tr).cpu().numpy()
+    d, p, v = dt.cpu().numpy(), pt.cpu().numpy(), vt.cpu().numpy()
+    o = orc.sample(K, ost.pi, ost.mu_x, ost.mu_w, ost.L, qx, reg, orc.uniforms(63, Q))
+    same = o["margin"] > 1e-2
+    assert same.mean() > 0.9
+    assert np.array_equal(v[same], o["valid"][same])
+    assert v.mean() > 0.5
+    ok = same & (o["valid"] == 1)
+    assert _angle(d[ok].astype(np.float64), o["dir"][ok]).max() < 1e-4
+    vv = np.flatnonzero(v == 1)
+    po = orc.pdf(K, ost.pi, ost.mu_x, ost.mu_w, ost.L, qx[vv], reg[vv], d[vv].astype(np.float64))
+    w = np.exp2(lw2[vv] - lw2[vv].max(axis=1, keepdims=True))
+    w /= w.sum(axis=1, keepdims=True)
+    zc2 = np.where(w >= 1e-3, z2[vv], 0.0).max(axis=1)
+    for pg in (p[vv], pe[vv]):
+        rel = np.abs(pg - po) / po
+        assert np.all(np.isfinite(rel))
+        print(K, "far-position pdf rel quantiles", np.quantile(rel, [0.5, 0.99, 1.0]))
+        for q in np.flatnonzero(rel >= PDF_RTOL):
+            kap = pdf_kappa(ost, K, qx[vv[q]], 0, d[vv[q]].astype(np.float64))
+            assert rel[q] < 32 * EPS32 * (kap + zc2[q]), (q, rel[q], kap, zc2[q])
