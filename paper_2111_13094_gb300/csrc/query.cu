@@ -19,26 +19,26 @@ namespace sdmm {
 // Guided sampling and pdf with one thread per query (K <= KM components).
 // The thread conditions every component of its region on the position in a
 // first pass (weight and conditional mean of each component kept in shared
-// memory, one 16-byte slot per component and thread), picks the component
-// and draws the direction, then evaluates the solid-angle pdf of the
-// conditioned mixture at that direction in a second pass.  No lane waits on
-// another: the component choice, the Gaussian draw and the exp map run once
-// per query instead of in one lane of a component group.
+// memory, in a per-thread slot of two arrays), picks the component and draws
+// the direction, then evaluates the solid-angle pdf of the conditioned mixture
+// at that direction in a second pass.  No lane waits on another: the component
+// choice, the Gaussian draw and the exp map run once per query instead of in
+// one lane of a component group.
 //
 // With `perm` (the library's binning) query perm[j] is processed at slot j
 // (perm[j] < 0: an empty padding slot) and its outputs go to the slot's record
 // sorted_out[j]: (direction, pdf, or -1 if not valid) for sampling, (pdf, ...)
 // for the pdf; k_qbin_unpermute then moves them to the query's own index.
-// A warp takes 32 queries at a time.  When they fall in at most two regions,
-// those of its first and last query (queries sorted by region), it copies a
-// region's K records into shared memory with coalesced 16-byte loads (only
-// when the region changes) and the threads of that region read them from
-// there, one pass per region.  A warp whose queries span more regions
-// (queries in any order) processes them with one lane per component instead
+// Without it, outputs go to the query's own index.
+// Each warp of the persistent grid takes a contiguous run of batches of 32
+// slots.  When a batch's queries fall in at most two regions, those of its
+// first and last query (queries sorted by region), the warp copies a region's
+// K records into shared memory with coalesced 16-byte loads, rescaled for the
+// base-2 exponents (only when the region changes, so once per region for
+// sorted queries), and the threads of that region read them from there, one
+// pass per region.  A batch whose queries span more regions (queries in any
+// order) is processed with one lane per component instead
 // (warp_by_components), which reads each query's records once, coalesced.
-// With `perm`, the warp's j-th query is perm[j] and outputs go to the slot's
-// record (the library's binning of queries given in any order), else to the
-// query's own index.
 constexpr int kQWarps = 4;
 
 template <int KP, int OP>
